@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the SL-MPP7 Vlasov-Poisson hot path on one GB300 (per rank).
+
+Default workload: the 3D3V Plummer sphere (32^3 x 64^3 cells, 8.6e9 cells,
+34 GB of FP32 f), MP7 + PP, isolated Poisson, drift-kick-drift.  One step =
+one DKD Strang step: 9 sweeps (3 half drifts, 3 kicks, 3 half drifts), the
+velocity moment and the Poisson solve.  Metric: phase-space cell-updates per
+second (cells x sweeps / time), whole job (all ranks).
+
+JSON fields beyond the base contract:
+  roofline      HBM roofline of the dominant kernel (the sweep): 8 algorithmic
+                bytes per FP32 cell-update (read f once, write once) / mean
+                sweep-kernel time measured with CUDA events on the library's
+                stream, against the measured HBM copy bandwidth.
+  sweeps        cell-updates/s and GB/s of every sweep kind.
+  cpu_baseline  the FP64 CPU oracle on this host's cores, on a reduced grid.
+  e2e           the same metric through the C ABI with f in pinned host
+                memory, the host->device and device->host copies of f inside
+                the timed region.
+
+--impl reference times the CPU oracle (the only reference implementation this
+method has here) on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="plummer",
+                   choices=["plummer", "landau_nonlinear", "two_stream", "landau_linear"])
+    p.add_argument("--nx", type=int, default=None, help="override spatial cells per axis")
+    p.add_argument("--nv", type=int, default=None, help="override velocity cells per axis")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--sweep-reps", type=int, default=3)
+    return p.parse_args()
+
+
+def workload(args):
+    from paper_1702_08521_gb300 import inputs
+    if args.workload == "plummer":
+        cfg = inputs.plummer(args.nx or 32, args.nv or 64)
+    elif args.workload == "landau_nonlinear":
+        cfg = inputs.landau_nonlinear(args.nx or 256, args.nv or 1024)
+    elif args.workload == "two_stream":
+        cfg = inputs.two_stream(args.nx or 256, args.nv or 1024)
+    else:
+        cfg = inputs.landau_linear()
+    return cfg
+
+
+def sweeps_per_step(cfg) -> int:
+    d = cfg["grid"]["dims"]
+    return 3 * d if cfg["split"] == 1 else 3 * d  # DKD: 2 d drifts + d kicks; KDK: d + 2 d
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def sweep_traffic():
+    """Per-cell DRAM bytes of the sweep kernel from the committed ncu summary,
+    valid only while the sweep source is unchanged since the capture."""
+    src = os.path.join(ROOT, "paper_1702_08521_gb300", "csrc", "vp_sweep.cu")
+    summ = os.path.join(ROOT, "profiles", "sweep_traffic.txt")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for line in open(summ):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("sweep_source_sha256_16") == h:
+            return float(kv["dram_bytes_per_cell"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_oracle_rate(cfg_small, seconds: float = 12.0):
+    """FP64 CPU oracle, all host cores: cell-updates/s over the step's sweep
+    kinds on a reduced grid (bounded sample)."""
+    import numpy as np
+    import oracle as O
+    ncores = os.cpu_count() or 1
+    O.set_threads(ncores)
+    g = O.grid(**cfg_small["grid"])
+    kind, params = cfg_small["ic"]
+    f = O.init_f(g, kind, params)
+    _, _, acc = O.field(g, f)
+    acc = np.ascontiguousarray(acc)
+    dims = cfg_small["grid"]["dims"]
+    dt = cfg_small["dt"]
+    ncell = g.NX * g.NV
+    updates = 0
+    t0 = time.perf_counter()
+    while True:
+        for d in range(dims - 1, -1, -1):
+            O.drift_sweep(g, f, d, 0.5 * dt)
+        for d in range(dims):
+            O.kick_sweep(g, f, d, dt, acc[d])
+        for d in range(dims - 1, -1, -1):
+            O.drift_sweep(g, f, d, 0.5 * dt)
+        updates += ncell * 3 * dims
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return updates / el, O.get_threads(), ncell
+
+
+def small_cfg(cfg):
+    from paper_1702_08521_gb300 import inputs
+    if cfg["grid"]["dims"] == 3:
+        return inputs.plummer(12, 24), "plummer 12^3 x 24^3 FP64 (2.4e7 cells), DKD sweep sequence"
+    return cfg, f"{cfg['name']} FP64, KDK sweep sequence"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = workload(args)
+    small, desc = small_cfg(cfg)
+    per_step = []
+    for _ in range(args.warmup + args.steps):
+        r, cores, _ = cpu_oracle_rate(small, seconds=2.0)
+        per_step.append(r)
+    rate = statistics.mean(per_step[args.warmup:])
+    cells = 1
+    for n in cfg["grid"]["nx"] + cfg["grid"]["nv"]:
+        cells *= n
+    ms = cells * sweeps_per_step(cfg) / rate * 1e3
+    out = {"metric": "advection cell-updates/s", "value": rate, "unit": "cell-updates/s",
+           "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["name"], "sample": desc},
+           "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1702_08521_gb300 import vlasov as V
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    cfg = workload(args)
+    prec = V.VP_F32 if cfg["precision"] == "f32" else V.VP_F64
+    esize = 4 if prec == V.VP_F32 else 8
+    stream = torch.cuda.Stream(device=dev)
+    sim = V.Simulation(cfg["grid"], precision=prec, stream=stream)
+    kind, params = cfg["ic"]
+    V.vp_init_f(sim.ctx, kind, params)
+    sim.field()
+    ncell = V.vp_num_cells(sim.ctx)
+    nsw = sweeps_per_step(cfg)
+    dt, split = cfg["dt"], cfg["split"]
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (captures the step graph)
+    sim.step(dt, args.warmup, split=split)
+    barrier()
+    l0 = V.vp_launch_count(sim.ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        barrier()
+        ev0.record(stream)
+        sim.step(dt, args.steps, split=split)
+        ev1.record(stream)
+        barrier()
+    launches = V.vp_launch_count(sim.ctx) - l0
+    t = ev0.elapsed_time(ev1) / 1e3
+    tt = torch.tensor([t], device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    tmax = float(tt.item())
+    value = world * ncell * nsw * args.steps / tmax
+
+    # per-sweep-kind timing of the sweep kernel (CUDA events on the library stream)
+    dims = cfg["grid"]["dims"]
+    kinds = [("drift", d) for d in range(dims)] + [("kick", d) for d in range(dims)]
+    per_kind = {}
+    all_ms = []
+    for name, d in kinds:
+        ts = []
+        for _ in range(args.sweep_reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if name == "drift":
+                V.vp_drift_sweep(sim.ctx, d, 0.5 * dt)
+            else:
+                V.vp_kick_sweep(sim.ctx, d, dt, sim.accel[d * sim.NX:])
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.mean(ts[1:])
+        all_ms.extend(ts[1:])
+        per_kind[f"{name}_{'xv'[name == 'kick']}{d + 1}"] = {
+            "ms": round(ms, 4), "cell_updates_per_s": ncell / (ms / 1e3),
+            "gbs": 2 * esize * ncell / (ms / 1e3) / 1e9}
+    mean_ms = statistics.mean(all_ms)
+    peak, peak_kind = peaks()
+    achieved = 2 * esize * ncell / (mean_ms / 1e3) / 1e9
+    traffic_cell = sweep_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": (traffic_cell * ncell if traffic_cell is not None else None),
+                "kernel": "k_sweep_cols/k_sweep_rows (one sweep, all kinds averaged)",
+                "algorithmic_bytes_per_launch": 2 * esize * ncell,
+                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+    # end to end through the C ABI with host buffers: H2D f, one step, D2H f
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        nbytes = ncell * esize
+        try:
+            host = torch.empty(ncell, dtype=sim.f.dtype, pin_memory=True)
+            V.vp_download_f(sim.ctx, host, nbytes)
+            stream.synchronize()
+            reps = max(1, min(3, args.steps))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                V.vp_upload_f(sim.ctx, host, nbytes)
+                sim.step(dt, 1, split=split)
+                V.vp_download_f(sim.ctx, host, nbytes)
+            b.record(stream)
+            b.synchronize()
+            te = a.elapsed_time(b) / 1e3 / reps
+            e2e = {"value": ncell * nsw / te, "unit": "cell-updates/s",
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                   "ms_per_step": te * 1e3}
+            del host
+        except RuntimeError as ex:
+            e2e = {"value": None, "unit": "cell-updates/s", "error": str(ex)[:200]}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        small, desc = small_cfg(cfg)
+        rate, cores, _ = cpu_oracle_rate(small)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": desc + ", ~12 s of sweeps"}
+
+    if rank == 0:
+        out = {"metric": "advection cell-updates/s", "value": value, "unit": "cell-updates/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": cfg["precision"], "data": "synthetic",
+               "config": {"workload": cfg["name"], "cells": ncell, "sweeps_per_step": nsw,
+                          "scheme": f"SL-MPP{cfg['grid']['order']}", "split": "DKD" if split else "KDK",
+                          "dt": dt, "l2": "inputs larger than L2 (f is %.1f GB)" % (ncell * esize / 1e9),
+                          "parallelism": f"replicas x{world}"},
+               "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
+               "sweeps": per_kind, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(out))
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

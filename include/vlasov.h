@@ -1,0 +1,197 @@
+/*
+ * vlasov.h -- C ABI of the GB300 (sm_103a) SL-MPP5/7 Vlasov-Poisson library.
+ *
+ * The method is that of Tanaka, Yoshikawa, Minoshima & Yoshida (2017),
+ * "Multidimensional Vlasov-Poisson simulations with high-order monotonicity-
+ * and positivity-preserving schemes": a Strang-split sequence of 1D
+ * semi-Lagrangian advections of the phase-space distribution f, each one a
+ * conservative flux update (Sec. 2.1.2) whose fluxes pass through the MP
+ * constraint (Appendix A) and the positivity-preserving flux limiter
+ * (Sec. 2.1.1), with the acceleration from an FFT Poisson solve (Sec. 2.2).
+ *
+ * Conventions shared by every call:
+ *   - Return value: VP_OK (0) or a negative VP_E* code; vp_last_error()
+ *     returns a one-line description of the last failure on that context.
+ *   - Asynchrony: work is enqueued on the CUDA stream given to vp_create and
+ *     returns without waiting, except where a call says it synchronises.
+ *   - Memory: the distribution function f and every array passed as a
+ *     "_dev" pointer are device memory owned by the caller (the library never
+ *     frees them).  The library owns only small internal tables and FFT
+ *     buffers (allocated at vp_create, freed at vp_destroy).
+ *   - Layout of f: row-major [x_1 .. x_D][v_1 .. v_D], velocity innermost,
+ *     i.e. every spatial cell holds its whole velocity grid contiguously
+ *     (Sec. 2.3).  Element type float (VP_F32) or double (VP_F64).
+ *   - Spatial arrays (rho, phi, one acceleration component): NX = prod nx
+ *     doubles, row-major [x_1 .. x_D].  An acceleration field is D such
+ *     arrays back to back (axis-major, D * NX doubles).
+ *   - Cells are uniform; cell i of an axis covers [lo + i h, lo + (i+1) h].
+ */
+#ifndef VLASOV_H
+#define VLASOV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define VP_OK 0
+#define VP_EINVAL (-1)      /* bad argument (message in vp_last_error) */
+#define VP_ECUDA (-2)       /* a CUDA call failed */
+#define VP_ENOMEM (-3)      /* a library-internal allocation failed */
+#define VP_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define VP_ENONFINITE (-5)  /* diagnostics found NaN or Inf in f */
+#define VP_ENOTSUP (-6)     /* configuration not supported */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define VP_F32 0
+#define VP_F64 1
+#define VP_BC_PERIODIC 0
+#define VP_BC_OUTFLOW 1 /* zero ghost cells: nothing flows in */
+#define VP_POIS_PERIODIC 0
+#define VP_POIS_ISOLATED 1
+#define VP_SPLIT_KDK 0
+#define VP_SPLIT_DKD 1
+#define VP_IC_LANDAU 0
+#define VP_IC_TWOSTREAM 1
+#define VP_IC_PLUMMER 2
+#define VP_IC_ADVECT 3
+#define VP_NDIAG 9
+
+/* ---- grid and scheme --------------------------------------------------- */
+typedef struct {
+    int dx, dv;            /* spatial / velocity dimensions; dx == dv in 1..3 */
+    int nx[3], nv[3];      /* cells per axis (entries beyond dx/dv ignored) */
+    double xlo[3], xhi[3]; /* spatial box per axis */
+    double vlo[3], vhi[3]; /* velocity box per axis */
+    int xbc;               /* VP_BC_PERIODIC or VP_BC_OUTFLOW (spatial axes);
+                              velocity axes are always zero-inflow */
+    int order;             /* 5: CSL5 flux (Eqs. 29-34); 7: CSL7 (Eqs. 36-43) */
+    int mp;                /* 1: MP constraint (Appendix A) on, 0: off */
+    int pp;                /* 1: PP flux limiter (Eqs. 15-23) on, 0: off */
+    double alpha;          /* MP parameter (4 in the paper) */
+    int precision;         /* VP_F32 or VP_F64: storage and arithmetic of f */
+    int poisson;           /* VP_POIS_PERIODIC or VP_POIS_ISOLATED (3D, cubic cells) */
+    int pois_order;        /* 2, 4 or 6: Green function and FDA order (App. C) */
+    double coupling;       /* S in lap(phi) = S (rho - rho_bg): 4 pi G for
+                              gravity (Eq. 3), -1 for electrons (Eq. 74) */
+    double rho_bg;         /* neutralising background density */
+} vp_grid;
+
+/* diagnostics of one state, all double precision */
+typedef struct {
+    double mass;     /* sum f dX dV */
+    double ke;       /* 1/2 sum f |v|^2 dX dV */
+    double fe;       /* 1/2 sum_x |a|^2 dX  (field energy) */
+    double pe;       /* 1/2 sum_x (rho - rho_bg) phi dX  (potential energy) */
+    double min_f;    /* minimum of f */
+    double max_f;    /* maximum of f */
+    double mode_amp; /* (2/NX) |sum_x a_1(x) exp(-2 pi i m j_1 / n_1)|, m = `mode` */
+    double l1;       /* sum |f| dX dV */
+    double l2;       /* sum f^2 dX dV */
+} vp_diag;
+
+typedef struct vp_ctx vp_ctx; /* opaque: grid, stream, tables, FFT plans */
+
+/*
+ * vp_create -- validate the grid (Sec. 2: uniform Cartesian phase-space
+ * mesh) and build a context bound to `cuda_stream` (a cudaStream_t; NULL
+ * for the legacy default stream) on the current device.  Precomputes the
+ * CSL weight polynomials, the Green function of the Poisson solver (Eqs.
+ * 50-54) and allocates the library's small FFT/scratch buffers.
+ * *out receives the context; on failure *out is NULL.
+ */
+int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out);
+
+/* Free the context and its internal buffers (not f).  NULL is accepted. */
+void vp_destroy(vp_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  Never NULL. */
+const char *vp_last_error(const vp_ctx *ctx);
+
+/* Number of cells of f (NX * NV) and bytes per element (4 or 8). */
+long long vp_num_cells(const vp_ctx *ctx);
+int vp_elem_size(const vp_ctx *ctx);
+
+/*
+ * vp_bind_f -- attach the caller-owned device array holding f
+ * (vp_num_cells elements of the grid's precision, 16-byte aligned).  All
+ * later calls read and write it in place.
+ */
+int vp_bind_f(vp_ctx *ctx, void *f_dev);
+
+/*
+ * vp_init_f -- fill f with an analytic initial condition sampled at cell
+ * centres (point values):
+ *   VP_IC_LANDAU    params {alpha, k1, k2, k3, sigma, amp}:
+ *                   amp (1 + alpha sum_d cos k_d x_d) prod_d N(v_d; 0, sigma^2)
+ *                   (Eq. 75; Eq. 69 for the gravitating slab)
+ *   VP_IC_TWOSTREAM params {alpha, k}: v_1^2 exp(-|v|^2/2)/(2 pi)^{D/2} (1 + alpha cos k x_1)
+ *   VP_IC_PLUMMER   params {G, M, a}: isotropic Plummer distribution function
+ *   VP_IC_ADVECT    params {shape}: Test-1 profiles in x (Eqs. 60, 62, 63, 65-67)
+ */
+int vp_init_f(vp_ctx *ctx, int kind, const double *params, int nparams);
+
+/* Host <-> device copies of f on the context stream (host memory should be
+ * pinned for asynchrony); `bytes` must equal vp_num_cells * vp_elem_size. */
+int vp_upload_f(vp_ctx *ctx, const void *host, size_t bytes);
+int vp_download_f(vp_ctx *ctx, void *host, size_t bytes);
+
+/*
+ * vp_drift_sweep -- advance f by the 1D advection along spatial axis `dim`
+ * (0-based) at speed v_dim for a time dt (Eq. 4): every line along x_dim is
+ * shifted by s = v dt / dx_dim cells, split as s = N + zeta with N the
+ * nearest integer (an exact copy) and |zeta| <= 1/2 the CFL number of one
+ * SL-MPP update (Eq. 49).  In place.
+ */
+int vp_drift_sweep(vp_ctx *ctx, int dim, double dt);
+
+/*
+ * vp_kick_sweep -- same along velocity axis `dim` with the acceleration
+ * accel_dev[x] (NX doubles, device) of each spatial cell (Eq. 5), shift
+ * s = a dt / dv_dim; zero inflow at the velocity boundaries.  In place.
+ */
+int vp_kick_sweep(vp_ctx *ctx, int dim, double dt, const double *accel_dev);
+
+/* rho_dev[x] = sum_v f dV (Eq. 3 on the mesh), NX doubles, computed from the
+ * float/double f with double-precision accumulation. */
+int vp_density_moment(vp_ctx *ctx, double *rho_dev);
+
+/*
+ * vp_poisson_solve -- lap(phi) = S (rho - rho_bg) by FFT convolution
+ * (Sec. 2.2): periodic with the 2nd/4th/6th-order Green function (Eqs.
+ * 51-53, k = 0 mode zero) or isolated by doubling-up with G(r) = -(S/4pi)
+ * dV / r (Eq. 54); then accel = -grad phi by the 2/4/6-point FDA (Eqs.
+ * C9-C11).  rho_dev: NX doubles in; phi_dev: NX doubles out (may be NULL);
+ * accel_dev: dx * NX doubles out.
+ */
+int vp_poisson_solve(vp_ctx *ctx, const double *rho_dev, double *phi_dev, double *accel_dev);
+
+/*
+ * vp_diagnostics -- compute the density, field and the vp_diag quantities of
+ * the current f (mode index `mode` for mode_amp) and copy them to *out.
+ * Synchronises the stream.  Returns VP_ENONFINITE if f holds NaN or Inf.
+ */
+int vp_diagnostics(vp_ctx *ctx, int mode, vp_diag *out);
+
+/*
+ * vp_step -- nsteps Strang-split steps (Sec. 2.4, Eq. 55).  KDK: kicks
+ * v_1..v_D by dt/2 with accel, drifts x_D..x_1 by dt, density + Poisson ->
+ * accel, kicks by dt/2.  DKD: drifts by dt/2, density + Poisson -> accel,
+ * kicks by dt, drifts by dt/2.  accel_dev (dx * NX doubles, device) holds on
+ * entry the field used by KDK's first half kick and on exit the last field
+ * solved.  If diag_dev is not NULL it receives nsteps * VP_NDIAG doubles
+ * (vp_diag order) describing f after each step.  Captured once into a CUDA
+ * graph per (dt, split, diag) and replayed.
+ */
+int vp_step(vp_ctx *ctx, double dt, int split, int nsteps, double *accel_dev, int mode,
+            double *diag_dev);
+
+/* Kernel launches the library issued on this context since creation. */
+long long vp_launch_count(const vp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

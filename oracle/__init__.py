@@ -44,7 +44,7 @@ def build(force: bool = False) -> str:
                                              os.path.getmtime(os.path.join(_HERE, "vp_oracle.h")))):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:

@@ -1,0 +1,100 @@
+// vp_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "vlasov.h"
+
+// Per line class (one velocity index for a drift, one spatial cell for a
+// kick): the integer shift n, the direction sigma = sign(zeta), the CFL number
+// nu = |zeta| and the CSL weights w_k(nu) on the upwind-ordered stencil
+// u[-3..3] (u[0] = upwind cell of the interface).  For CSL5 w[0] = w[6] = 0.
+template <typename T>
+struct __align__(16) LineShift {
+    T w[7];
+    T nu;
+    int n;
+    int sigma;
+};
+
+// Geometry of one sweep: f viewed as [outer][L][inner].
+struct SweepGeo {
+    long long outer, inner;
+    int L;
+    int periodic;
+    // class of a line: cls_from_inner ? (c / cdiv) % cmod : o / cdiv
+    int cls_from_inner;
+    long long cdiv, cmod;
+    // column-kernel tile (W columns x full line), row-kernel lines per CTA
+    int W, nseg, R;
+};
+
+struct LimParams {
+    double alpha;
+    int mp, pp;
+};
+
+// CSL weight polynomials: w_k(nu) = sum_j c[j][k] nu^j.
+struct WPoly {
+    double c[7][7];
+    int nterm;  // 5 or 7 polynomial terms
+};
+
+struct vp_graph_cache {
+    cudaGraphExec_t exec;
+    double dt;
+    int split;
+    void *f;
+    double *acc;
+    long long per_step;  // kernels in one captured step
+    int valid;
+};
+
+struct vp_ctx {
+    vp_grid g;
+    cudaStream_t stream;
+    int device, sm_count;
+    long long NX, NV, ncell;
+    int esize;
+    void *f;
+    WPoly wp;
+    // library-owned device buffers
+    void *d_shift;
+    long long shift_cap;
+    double *d_rho, *d_phi, *d_acc;      // diagnostics scratch
+    double *d_rho_s, *d_phi_s;          // step scratch
+    double2 *d_fft;
+    double *d_green;                    // periodic: S / lambda(k)
+    double2 *d_ghat;                    // isolated: DFT of the padded Green function
+    long long MT;
+    int m[3];
+    double *d_part;                     // diagnostics partial sums [NX * 6]
+    double *d_diag;                     // VP_NDIAG doubles
+    int *d_flag;                        // non-finite flag
+    long long launches;
+    vp_graph_cache graph;
+    char err[256];
+};
+
+// error helpers
+int vp_fail(vp_ctx *c, int code, const char *fmt, ...);
+#define VP_CUDA_TRY(ctx, call)                                                         \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return vp_fail((ctx), VP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+// launchers implemented in the kernel files; all enqueue on ctx->stream
+int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double *accel);
+int vp_launch_sweep(vp_ctx *c, int kick, int dim);
+int vp_launch_moment(vp_ctx *c, double *rho);
+int vp_launch_poisson(vp_ctx *c, const double *rho, double *phi, double *acc);
+int vp_launch_diag(vp_ctx *c, int mode, double *out_dev);
+int vp_launch_init(vp_ctx *c, int kind, const double *p, int np);
+int vp_field_setup(vp_ctx *c);          // Green function tables (at create)
+int vp_sweep_setup(vp_ctx *c);          // kernel attributes (at create)

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C ABI in include/vlasov.h (csrc/libvlasov.so).
+
+Functions keep the C names (``vp_create``, ``vp_drift_sweep``, ...) and only
+marshal arguments: torch tensors are passed as raw device pointers, a torch
+CUDA stream as its ``cudaStream_t``.  Every step of the method runs in the
+CUDA library; there is no Python or CPU fallback.  If the library cannot be
+loaded, the first call raises ``RuntimeError``.
+
+``Simulation`` is a small convenience owner of a context plus the tensors it
+needs (f, acceleration), built on the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+VP_OK, VP_EINVAL, VP_ECUDA, VP_ENOMEM, VP_ETIMEOUT, VP_ENONFINITE, VP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+VP_F32, VP_F64 = 0, 1
+VP_BC_PERIODIC, VP_BC_OUTFLOW = 0, 1
+VP_POIS_PERIODIC, VP_POIS_ISOLATED = 0, 1
+VP_SPLIT_KDK, VP_SPLIT_DKD = 0, 1
+VP_IC_LANDAU, VP_IC_TWOSTREAM, VP_IC_PLUMMER, VP_IC_ADVECT = 0, 1, 2, 3
+VP_NDIAG = 9
+DIAG_NAMES = ("mass", "ke", "fe", "pe", "min_f", "max_f", "mode_amp", "l1", "l2")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vlasov error {code}: {msg}")
+        self.code = code
+
+
+class vp_grid(ctypes.Structure):
+    _fields_ = [
+        ("dx", ctypes.c_int), ("dv", ctypes.c_int),
+        ("nx", ctypes.c_int * 3), ("nv", ctypes.c_int * 3),
+        ("xlo", ctypes.c_double * 3), ("xhi", ctypes.c_double * 3),
+        ("vlo", ctypes.c_double * 3), ("vhi", ctypes.c_double * 3),
+        ("xbc", ctypes.c_int), ("order", ctypes.c_int), ("mp", ctypes.c_int),
+        ("pp", ctypes.c_int), ("alpha", ctypes.c_double), ("precision", ctypes.c_int),
+        ("poisson", ctypes.c_int), ("pois_order", ctypes.c_int),
+        ("coupling", ctypes.c_double), ("rho_bg", ctypes.c_double),
+    ]
+
+
+class vp_diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in DIAG_NAMES]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libvlasov.so (building it first if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            try:
+                path = _build.build()
+            except RuntimeError as e:
+                if not os.path.exists(path):
+                    raise RuntimeError(f"libvlasov.so is missing and could not be built: {e}") from e
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        GP = ctypes.POINTER(vp_grid)
+        sig = {
+            "vp_create": (I, [GP, P, ctypes.POINTER(P)]),
+            "vp_destroy": (None, [P]),
+            "vp_last_error": (ctypes.c_char_p, [P]),
+            "vp_num_cells": (LL, [P]),
+            "vp_elem_size": (I, [P]),
+            "vp_launch_count": (LL, [P]),
+            "vp_bind_f": (I, [P, P]),
+            "vp_init_f": (I, [P, I, P, I]),
+            "vp_upload_f": (I, [P, P, ctypes.c_size_t]),
+            "vp_download_f": (I, [P, P, ctypes.c_size_t]),
+            "vp_drift_sweep": (I, [P, I, D]),
+            "vp_kick_sweep": (I, [P, I, D, P]),
+            "vp_density_moment": (I, [P, P]),
+            "vp_poisson_solve": (I, [P, P, P, P]),
+            "vp_diagnostics": (I, [P, I, ctypes.POINTER(vp_diag)]),
+            "vp_step": (I, [P, D, I, I, P, I, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    """Device (or host) pointer of a tensor / integer address / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != VP_OK:
+        msg = load().vp_last_error(ctx).decode() if ctx else ""
+        raise VpError(rc, msg)
+
+
+def make_grid(dims: int, nx, nv, xlo, xhi, vlo, vhi, *, xbc: int = VP_BC_PERIODIC,
+              order: int = 7, mp: int = 1, pp: int = 1, alpha: float = 4.0,
+              precision: int = VP_F32, poisson: int = VP_POIS_PERIODIC, pois_order: int = 6,
+              coupling: float = -1.0, rho_bg: float = 1.0, **_ignored) -> vp_grid:
+    g = vp_grid()
+    g.dx = g.dv = dims
+    for d in range(dims):
+        g.nx[d], g.nv[d] = int(nx[d]), int(nv[d])
+        g.xlo[d], g.xhi[d] = float(xlo[d]), float(xhi[d])
+        g.vlo[d], g.vhi[d] = float(vlo[d]), float(vhi[d])
+    g.xbc, g.order, g.mp, g.pp, g.alpha = xbc, order, mp, pp, float(alpha)
+    g.precision, g.poisson, g.pois_order = precision, poisson, pois_order
+    g.coupling, g.rho_bg = float(coupling), float(rho_bg)
+    return g
+
+
+# ---- the C calls, same names ---------------------------------------------------
+
+def vp_create(grid: vp_grid, stream=None) -> ctypes.c_void_p:
+    """stream: a torch.cuda.Stream, an integer cudaStream_t or None (default stream)."""
+    lib = load()
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    out = ctypes.c_void_p()
+    rc = lib.vp_create(ctypes.byref(grid), ctypes.c_void_p(h), ctypes.byref(out))
+    if rc != VP_OK:
+        raise VpError(rc, "vp_create failed (see stderr)")
+    return out
+
+
+def vp_destroy(ctx) -> None:
+    load().vp_destroy(ctx)
+
+
+def vp_last_error(ctx) -> str:
+    return load().vp_last_error(ctx).decode()
+
+
+def vp_num_cells(ctx) -> int:
+    return int(load().vp_num_cells(ctx))
+
+
+def vp_elem_size(ctx) -> int:
+    return int(load().vp_elem_size(ctx))
+
+
+def vp_launch_count(ctx) -> int:
+    return int(load().vp_launch_count(ctx))
+
+
+def vp_bind_f(ctx, f) -> None:
+    _check(ctx, load().vp_bind_f(ctx, _ptr(f)))
+
+
+def vp_init_f(ctx, kind: int, params) -> None:
+    arr = (ctypes.c_double * len(params))(*[float(p) for p in params])
+    _check(ctx, load().vp_init_f(ctx, kind, ctypes.cast(arr, ctypes.c_void_p), len(params)))
+
+
+def vp_upload_f(ctx, host, nbytes: int) -> None:
+    _check(ctx, load().vp_upload_f(ctx, _ptr(host), nbytes))
+
+
+def vp_download_f(ctx, host, nbytes: int) -> None:
+    _check(ctx, load().vp_download_f(ctx, _ptr(host), nbytes))
+
+
+def vp_drift_sweep(ctx, dim: int, dt: float) -> None:
+    _check(ctx, load().vp_drift_sweep(ctx, dim, dt))
+
+
+def vp_kick_sweep(ctx, dim: int, dt: float, accel) -> None:
+    _check(ctx, load().vp_kick_sweep(ctx, dim, dt, _ptr(accel)))
+
+
+def vp_density_moment(ctx, rho) -> None:
+    _check(ctx, load().vp_density_moment(ctx, _ptr(rho)))
+
+
+def vp_poisson_solve(ctx, rho, phi, accel) -> None:
+    _check(ctx, load().vp_poisson_solve(ctx, _ptr(rho), _ptr(phi), _ptr(accel)))
+
+
+def vp_diagnostics(ctx, mode: int = 1) -> dict:
+    d = vp_diag()
+    _check(ctx, load().vp_diagnostics(ctx, mode, ctypes.byref(d)))
+    return {n: getattr(d, n) for n in DIAG_NAMES}
+
+
+def vp_step(ctx, dt: float, split: int, nsteps: int, accel, mode: int = 1, diag=None) -> None:
+    _check(ctx, load().vp_step(ctx, dt, split, nsteps, _ptr(accel), mode, _ptr(diag)))
+
+
+# ---- convenience owner -----------------------------------------------------------
+
+class Simulation:
+    """A context plus its device tensors (torch is used for memory and streams)."""
+
+    def __init__(self, grid: dict, precision: int = VP_F32, stream=None, device: str = "cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the Vlasov library needs a CUDA device")
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.grid = make_grid(**{**grid, "precision": precision})
+        self.ctx = vp_create(self.grid, self.stream)
+        self.dims = grid["dims"]
+        self.shape = tuple(grid["nx"]) + tuple(grid["nv"])
+        self.NX = 1
+        for n in grid["nx"]:
+            self.NX *= int(n)
+        dtype = torch.float32 if precision == VP_F32 else torch.float64
+        self.f = torch.empty(vp_num_cells(self.ctx), dtype=dtype, device=device)
+        self.accel = torch.zeros(self.dims * self.NX, dtype=torch.float64, device=device)
+        self.rho = torch.zeros(self.NX, dtype=torch.float64, device=device)
+        self.phi = torch.zeros(self.NX, dtype=torch.float64, device=device)
+        vp_bind_f(self.ctx, self.f)
+
+    def init(self, kind: int, params) -> None:
+        vp_init_f(self.ctx, kind, params)
+
+    def upload(self, f_host) -> None:
+        """Copy a host array / tensor into f (blocking)."""
+        t = self.torch.as_tensor(f_host).to(self.f.dtype).contiguous()
+        with self.torch.cuda.stream(self.stream):
+            self.f.copy_(t.reshape(-1), non_blocking=False)
+        self.stream.synchronize()
+
+    def field(self) -> None:
+        vp_density_moment(self.ctx, self.rho)
+        vp_poisson_solve(self.ctx, self.rho, self.phi, self.accel)
+
+    def step(self, dt: float, nsteps: int, split: int = VP_SPLIT_KDK, mode: int = 1, diag=None):
+        vp_step(self.ctx, dt, split, nsteps, self.accel, mode, diag)
+
+    def diagnostics(self, mode: int = 1) -> dict:
+        return vp_diagnostics(self.ctx, mode)
+
+    def sync(self) -> None:
+        self.stream.synchronize()
+
+    def close(self) -> None:
+        if self.ctx:
+            vp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
