@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sweep-reps", type=int, default=3)
+    p.add_argument("--sweep-impl", type=int, default=0, choices=[0, 1, 2],
+                   help="0 auto, 1 staged-load kernels, 2 TMA pipeline")
+    p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
 
@@ -238,6 +241,10 @@ def main():
     esize = 4 if prec == V.VP_F32 else 8
     stream = torch.cuda.Stream(device=dev)
     sim = V.Simulation(cfg["grid"], precision=prec, stream=stream)
+    if args.sweep_impl:
+        V.vp_set_option(sim.ctx, V.VP_OPT_SWEEP_IMPL, args.sweep_impl)
+    if args.no_autotune:
+        V.vp_set_option(sim.ctx, V.VP_OPT_AUTOTUNE, 0)
     kind, params = cfg["ic"]
     V.vp_init_f(sim.ctx, kind, params)
     sim.field()
@@ -292,6 +299,10 @@ def main():
             "ms": round(ms, 4), "cell_updates_per_s": ncell / (ms / 1e3),
             "gbs": 2 * esize * ncell / (ms / 1e3) / 1e9}
     mean_ms = statistics.mean(all_ms)
+    tuning = {}
+    for name, d in kinds:
+        tu = V.vp_get_tuning(sim.ctx, 1 if name == "kick" else 0, d)
+        tuning[f"{name}_{'xv'[name == 'kick']}{d + 1}"] = tu
     peak, peak_kind = peaks()
     achieved = 2 * esize * ncell / (mean_ms / 1e3) / 1e9
     traffic_cell = sweep_traffic()
@@ -344,7 +355,7 @@ def main():
                           "dt": dt, "l2": "inputs larger than L2 (f is %.1f GB)" % (ncell * esize / 1e9),
                           "parallelism": f"replicas x{world}"},
                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
-               "sweeps": per_kind, "e2e": e2e, "cpu_baseline": cpu}
+               "sweeps": per_kind, "tuning": tuning, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out))
     sim.close()
     if world > 1:

@@ -191,6 +191,31 @@ int vp_step(vp_ctx *ctx, double dt, int split, int nsteps, double *accel_dev, in
 /* Kernel launches the library issued on this context since creation. */
 long long vp_launch_count(const vp_ctx *ctx);
 
+/*
+ * vp_sync -- wait for the context stream and check the device status word
+ * that bounded device-side waits (TMA completion barriers) write when they
+ * give up.  Returns VP_ETIMEOUT (and clears the word) if one did.
+ */
+int vp_sync(vp_ctx *ctx);
+
+/*
+ * vp_set_option -- implementation choices (no effect on results):
+ *   VP_OPT_SWEEP_IMPL: 0 automatic, 1 staged-load kernels only, 2 prefer the
+ *                      TMA-pipelined strided-axis kernel;
+ *   VP_OPT_AUTOTUNE:   1 (default) times candidate tile shapes of each sweep
+ *                      geometry on its first use (with a zero shift, which
+ *                      leaves f unchanged) and keeps the fastest; 0 uses
+ *                      fixed defaults.
+ * Changing an option forgets tuned shapes and the captured step graph.
+ */
+#define VP_OPT_SWEEP_IMPL 1
+#define VP_OPT_AUTOTUNE 2
+int vp_set_option(vp_ctx *ctx, int option, long long value);
+
+/* Tile shape in use for sweep (kick, dim): out4 = {impl, W or R, segments,
+ * CTAs per SM (0 = occupancy maximum)}; impl 0 means not tuned yet. */
+int vp_get_tuning(const vp_ctx *ctx, int kick, int dim, int *out4);
+
 #ifdef __cplusplus
 }
 #endif

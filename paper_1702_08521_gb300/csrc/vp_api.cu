@@ -150,11 +150,24 @@ void free_buffers(vp_ctx *c) {
     cudaFree(c->d_part);
     cudaFree(c->d_diag);
     cudaFree(c->d_flag);
+    cudaFree(c->d_status);
     if (c->graph.valid) cudaGraphExecDestroy(c->graph.exec);
 }
 
+bool capturing(const vp_ctx *c) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // legacy stream while another stream captures: do not sync
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
 int sweep_all(vp_ctx *c, int kick, int dim, double dt, const double *accel) {
-    int rc = vp_launch_shift_table(c, kick, dim, dt, accel);
+    int rc;
+    if (c->opt_autotune && !c->tune[kick][dim].valid && !capturing(c))
+        if ((rc = vp_tune_sweep(c, kick, dim))) return rc;
+    rc = vp_launch_shift_table(c, kick, dim, dt, accel);
     if (rc) return rc;
     return vp_launch_sweep(c, kick, dim);
 }
@@ -242,7 +255,14 @@ int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out) {
     ALLOC(c->d_part, sizeof(double) * c->NX * 6);
     ALLOC(c->d_diag, sizeof(double) * VP_NDIAG);
     ALLOC(c->d_flag, sizeof(int));
+    ALLOC(c->d_status, sizeof(int));
 #undef ALLOC
+    c->opt_autotune = 1;
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+        free_buffers(c);
+        delete c;
+        return VP_ECUDA;
+    }
     if ((rc = vp_sweep_setup(c)) || (rc = vp_field_setup(c))) {
         fprintf(stderr, "vp_create: %s\n", c->err);
         free_buffers(c);
@@ -343,6 +363,47 @@ int vp_poisson_solve(vp_ctx *c, const double *rho_dev, double *phi_dev, double *
     return vp_launch_poisson(c, rho_dev, phi_dev ? phi_dev : c->d_phi, accel_dev);
 }
 
+int vp_set_option(vp_ctx *c, int option, long long value) {
+    if (!c) return VP_EINVAL;
+    if (option == VP_OPT_SWEEP_IMPL) {
+        if (value < 0 || value > 2) return vp_fail(c, VP_EINVAL, "sweep implementation must be 0, 1 or 2");
+        c->opt_impl = (int)value;
+    } else if (option == VP_OPT_AUTOTUNE) {
+        c->opt_autotune = value != 0;
+    } else {
+        return vp_fail(c, VP_EINVAL, "unknown option %d", option);
+    }
+    for (int k = 0; k < 2; ++k)
+        for (int d = 0; d < 3; ++d) c->tune[k][d].valid = 0;
+    if (c->graph.valid) {
+        cudaGraphExecDestroy(c->graph.exec);
+        c->graph.valid = 0;
+    }
+    return VP_OK;
+}
+
+int vp_get_tuning(const vp_ctx *c, int kick, int dim, int *out4) {
+    if (!c || !out4 || kick < 0 || kick > 1 || dim < 0 || dim > 2) return VP_EINVAL;
+    const SweepTune &t = c->tune[kick][dim];
+    out4[0] = t.valid ? t.impl : 0;
+    out4[1] = t.W;
+    out4[2] = t.nseg;
+    out4[3] = t.ctas_per_sm;
+    return VP_OK;
+}
+
+int vp_sync(vp_ctx *c) {
+    if (!c) return VP_EINVAL;
+    VP_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int st = 0;
+    VP_CUDA_TRY(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        cudaMemset(c->d_status, 0, sizeof(int));
+        return vp_fail(c, VP_ETIMEOUT, "a device-side wait gave up (status %d)", st);
+    }
+    return VP_OK;
+}
+
 int vp_diagnostics(vp_ctx *c, int mode, vp_diag *out) {
     int rc = check_ctx(c, true);
     if (rc) return rc;
@@ -353,7 +414,7 @@ int vp_diagnostics(vp_ctx *c, int mode, vp_diag *out) {
     int flag = 0;
     VP_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_diag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     VP_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    VP_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if ((rc = vp_sync(c))) return rc;
     memcpy(out, h, sizeof(h));
     if (flag) return vp_fail(c, VP_ENONFINITE, "f holds NaN or Inf");
     return VP_OK;
@@ -369,6 +430,12 @@ int vp_step(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, int 
     // graph path needs a capturable (non-legacy) stream
     const bool use_graph = c->stream != nullptr && c->stream != cudaStreamLegacy;
     vp_graph_cache &gc = c->graph;
+    if (c->opt_autotune && !capturing(c)) {
+        for (int d = 0; d < c->g.dx; ++d)
+            if ((rc = vp_tune_sweep(c, 0, d))) return rc;
+        for (int d = 0; d < c->g.dv; ++d)
+            if ((rc = vp_tune_sweep(c, 1, d))) return rc;
+    }
     if (use_graph && !(gc.valid && gc.dt == dt && gc.split == split && gc.f == c->f && gc.acc == accel_dev)) {
         if (gc.valid) {
             cudaGraphExecDestroy(gc.exec);

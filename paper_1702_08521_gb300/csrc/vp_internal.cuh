@@ -33,6 +33,13 @@ struct SweepGeo {
     int W, nseg, R;
 };
 
+// tile configuration of one sweep geometry (chosen by the autotuner)
+struct SweepTune {
+    int valid;
+    int impl;   // 1: staged loads (k_sweep_cols / k_sweep_rows), 2: TMA pipeline
+    int W, nseg, ctas_per_sm;
+};
+
 struct LimParams {
     double alpha;
     int mp, pp;
@@ -76,6 +83,10 @@ struct vp_ctx {
     double *d_diag;                     // VP_NDIAG doubles
     int *d_flag;                        // non-finite flag
     long long launches;
+    int *d_status;                      // device-side error word (bounded waits)
+    int opt_impl;                       // 0 auto, 1 staged, 2 TMA
+    int opt_autotune;                   // 1: time candidate tiles on first use
+    SweepTune tune[2][3];               // [kick][dim]
     vp_graph_cache graph;
     char err[256];
 };
@@ -92,6 +103,7 @@ int vp_fail(vp_ctx *c, int code, const char *fmt, ...);
 // launchers implemented in the kernel files; all enqueue on ctx->stream
 int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double *accel);
 int vp_launch_sweep(vp_ctx *c, int kick, int dim);
+int vp_tune_sweep(vp_ctx *c, int kick, int dim);  // outside stream capture only
 int vp_launch_moment(vp_ctx *c, double *rho);
 int vp_launch_poisson(vp_ctx *c, const double *rho, double *phi, double *acc);
 int vp_launch_diag(vp_ctx *c, int mode, double *out_dev);

@@ -11,12 +11,20 @@
 //   * k_sweep_rows: inner == 1 (the contiguous last velocity axis).  A CTA
 //     owns R consecutive lines, one contiguous block of memory, staged with
 //     an odd row pitch so that 32 lanes walking 32 lines hit 32 banks.
+//   * k_sweep_cols_tma: the strided-axis sweep as a persistent kernel fed by
+//     TMA: one elected thread streams [L x W] tiles global -> shared with
+//     cp.async.bulk.tensor (two input stages, mbarrier completion), all
+//     threads compute into a shared output tile, which TMA stores back while
+//     the next tile is computed.  No per-thread global loads or stores.
 // Each thread walks a segment of one line in the upwind direction with a
 // sliding register window, so each interface flux is computed once and the
 // incoming flux of a cell is the outgoing flux of its upwind neighbour.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 
 #include "vp_internal.cuh"
+#include "vp_tma.cuh"
 
 namespace {
 
@@ -272,6 +280,78 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     }
 }
 
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ CUtensorMap tmap,
+                                                        const LineShift<T> *__restrict__ tab,
+                                                        SweepGeo geo, LimParams lp,
+                                                        int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int W = geo.W, L = geo.L;
+    const int tile = L * W;
+    T *in_buf = reinterpret_cast<T *>(smraw);  // [2][L][W]
+    T *out_buf = in_buf + 2 * tile;            // [2][L][W]
+    const long long tpo = (geo.inner + W - 1) / W;
+    const long long ntiles = geo.outer * tpo;
+    const uint32_t bytes = (uint32_t)(tile * sizeof(T));
+    if (threadIdx.x == 0) {
+        vp_tma::mbar_init(&bar[0], 1);
+        vp_tma::mbar_init(&bar[1], 1);
+        vp_tma::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            const long long t = blockIdx.x + (long long)s * gridDim.x;
+            if (t < ntiles) {
+                vp_tma::mbar_expect_tx(&bar[s], bytes);
+                vp_tma::load_3d(in_buf + s * tile, &tmap, &bar[s], (int)((t % tpo) * W), 0, (int)(t / tpo));
+            }
+        }
+    }
+    const int cc = threadIdx.x % W;
+    const int seg = threadIdx.x / W;
+    const int r0 = (int)((long long)seg * L / geo.nseg);
+    const int r1 = (int)((long long)(seg + 1) * L / geo.nseg);
+    int k = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        T *in = in_buf + s * tile;
+        T *out = out_buf + s * tile;
+        if (!vp_tma::mbar_wait(&bar[s], (uint32_t)((k >> 1) & 1))) {
+            // the tile never arrived: report, drain our stores, leave
+            if (threadIdx.x == 0) {
+                atomicExch(status, VP_ETIMEOUT);
+                vp_tma::mbar_wait(&bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1), 1u << 20);
+                vp_tma::wait_all<0>();
+            }
+            return;
+        }
+        const long long o = t / tpo;
+        const long long c0 = (t % tpo) * W;
+        const int wc = (int)((geo.inner - c0) < W ? (geo.inner - c0) : W);
+        if (cc < wc && seg < geo.nseg) {
+            const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
+            sweep_segment<T, ORDER>(in + cc, W, L, geo.periodic, sh, r0, r1, out + cc, W,
+                                    (T)lp.alpha, lp.mp, lp.pp);
+        }
+        vp_tma::fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            vp_tma::store_3d(&tmap, out, (int)c0, 0, (int)o);
+            vp_tma::commit();
+            const long long tn = t + 2LL * gridDim.x;
+            if (tn < ntiles) {
+                vp_tma::mbar_expect_tx(&bar[s], bytes);
+                vp_tma::load_3d(in, &tmap, &bar[s], (int)((tn % tpo) * W), 0, (int)(tn / tpo));
+            }
+            vp_tma::wait_read<1>();  // the other output tile is free again
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) vp_tma::wait_all<0>();
+}
+
 // Shift decomposition of every line class, in double precision so that the
 // integer part is exact: s = c dt / h, n = nearest integer (halves away from
 // zero), zeta = s - n, nu = |zeta|; the weights are the CSL polynomials at nu.
@@ -310,6 +390,8 @@ void set_attrs() {
                          200 * 1024);
     cudaFuncSetAttribute(k_sweep_rows<T, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    cudaFuncSetAttribute(k_sweep_cols_tma<T, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
 }
 
 // geometry of the sweep along axis `dim` (kick: velocity axis, else spatial)
@@ -343,53 +425,217 @@ SweepGeo make_geo(const vp_ctx *c, int kick, int dim) {
     return geo;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
 template <typename T>
-int launch_sweep_t(vp_ctx *c, int kick, int dim) {
-    SweepGeo geo = make_geo(c, kick, dim);
+bool tma_eligible(const vp_ctx *c, const SweepGeo &geo, int W) {
+    constexpr int VEC = 16 / sizeof(T);
+    return geo.inner > 1 && geo.inner % VEC == 0 && W % VEC == 0 && geo.inner < (1LL << 31) &&
+           geo.outer < (1LL << 31) && geo.L <= 256 && W <= 256 &&
+           (size_t)4 * geo.L * W * sizeof(T) <= 200 * 1024 && tensor_map_encoder() != nullptr &&
+           (reinterpret_cast<uintptr_t>(c->f) & 15) == 0;
+}
+
+template <typename T>
+int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     const LineShift<T> *tab = static_cast<const LineShift<T> *>(c->d_shift);
-    LimParams lp{c->g.alpha, c->g.mp, c->g.pp};
+    const LimParams lp{c->g.alpha, c->g.mp, c->g.pp};
     T *f = static_cast<T *>(c->f);
     const int L = geo.L;
-    const int order = c->g.order;
-    if (geo.inner > 1) {
-        int W = (int)(8192 / sizeof(T) * 4 / L);  // ~32 KB tile for float
-        W = W > 128 ? 128 : W;
-        W = W < 32 ? 32 : W;
-        if (geo.inner < W) W = (int)geo.inner;
-        int nseg = L / 8;
-        const int maxseg = 256 / W > 0 ? 256 / W : 1;
-        nseg = nseg > maxseg ? maxseg : nseg;
-        nseg = nseg < 1 ? 1 : nseg;
-        geo.W = W;
-        geo.nseg = nseg;
-        const long long tiles = geo.outer * ((geo.inner + W - 1) / W);
+    int W = tu.W;
+    if (geo.inner < W) W = (int)geo.inner;
+    geo.W = W;
+    geo.nseg = tu.nseg;
+    const int threads = ((W * tu.nseg + 31) / 32) * 32;
+    const long long tiles = geo.outer * ((geo.inner + W - 1) / W);
+    const bool seven = c->g.order == 7;
+    if (tu.impl == 2 && tma_eligible<T>(c, geo, W)) {
+        CUtensorMap map;
+        const cuuint64_t dims[3] = {(cuuint64_t)geo.inner, (cuuint64_t)L, (cuuint64_t)geo.outer};
+        const cuuint64_t strides[2] = {(cuuint64_t)geo.inner * sizeof(T),
+                                       (cuuint64_t)geo.inner * L * sizeof(T)};
+        const cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)L, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = tensor_map_encoder()(&map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                          3, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return vp_fail(c, VP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        const size_t smem = (size_t)4 * L * W * sizeof(T);
+        int per_sm = tu.ctas_per_sm;
+        if (per_sm <= 0) {
+            if (seven)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_cols_tma<T, 7>, threads, smem);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_cols_tma<T, 5>, threads, smem);
+            per_sm = per_sm < 1 ? 1 : per_sm;
+        }
+        long long grid = (long long)per_sm * c->sm_count;
+        grid = grid > tiles ? tiles : grid;
+        if (seven)
+            k_sweep_cols_tma<T, 7><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status);
+        else
+            k_sweep_cols_tma<T, 5><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status);
+    } else {
         const size_t smem = (size_t)L * W * sizeof(T);
         if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
-        const int threads = ((W * nseg + 31) / 32) * 32;
-        if (order == 7)
+        if (seven)
             k_sweep_cols<T, 7><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
         else
             k_sweep_cols<T, 5><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+    }
+    c->launches++;
+    VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+template <typename T>
+int launch_rows(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
+    const LineShift<T> *tab = static_cast<const LineShift<T> *>(c->d_shift);
+    const LimParams lp{c->g.alpha, c->g.mp, c->g.pp};
+    T *f = static_cast<T *>(c->f);
+    const int L = geo.L;
+    int R = tu.W;
+    if (geo.outer < R) R = (int)geo.outer;
+    geo.R = R;
+    geo.nseg = tu.nseg;
+    const long long blocks = (geo.outer + R - 1) / R;
+    const size_t smem = (size_t)R * (L | 1) * sizeof(T);
+    if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
+    const int threads = ((R * tu.nseg + 31) / 32) * 32;
+    if (c->g.order == 7)
+        k_sweep_rows<T, 7><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
+    else
+        k_sweep_rows<T, 5><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
+    c->launches++;
+    VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+// default tile choice when the autotuner has not run
+template <typename T>
+SweepTune default_tune(const vp_ctx *c, const SweepGeo &geo) {
+    SweepTune tu{};
+    tu.valid = 1;
+    const int L = geo.L;
+    if (geo.inner > 1) {
+        int W = (int)(32768 / sizeof(T) / L);  // ~32 KB staged tile
+        W = W > 128 ? 128 : (W < 32 ? 32 : W);
+        W &= ~3;
+        int nseg = L / 8;
+        const int maxseg = 256 / W > 0 ? 256 / W : 1;
+        nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
+        tu.W = W;
+        tu.nseg = nseg;
+        const int want = c->opt_impl ? c->opt_impl : 2;
+        tu.impl = (want == 2 && tma_eligible<T>(c, geo, W < geo.inner ? W : (int)geo.inner)) ? 2 : 1;
     } else {
         int R = 4096 / L;
         R = R < 32 ? 32 : (R > 128 ? 128 : R);
-        if (geo.outer < R) R = (int)geo.outer;
         int nseg = L / 16;
         const int maxseg = 256 / R > 0 ? 256 / R : 1;
-        nseg = nseg > maxseg ? maxseg : nseg;
-        nseg = nseg < 1 ? 1 : nseg;
-        geo.R = R;
-        geo.nseg = nseg;
-        const long long blocks = (geo.outer + R - 1) / R;
-        const size_t smem = (size_t)R * (L | 1) * sizeof(T);
-        if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
-        const int threads = ((R * nseg + 31) / 32) * 32;
-        if (order == 7)
-            k_sweep_rows<T, 7><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
-        else
-            k_sweep_rows<T, 5><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
+        nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
+        tu.W = R;
+        tu.nseg = nseg;
+        tu.impl = 1;
     }
-    c->launches++;
+    return tu;
+}
+
+template <typename T>
+int launch_sweep_t(vp_ctx *c, int kick, int dim) {
+    const SweepGeo geo = make_geo(c, kick, dim);
+    SweepTune tu = c->tune[kick][dim];
+    if (!tu.valid || (c->opt_impl && geo.inner > 1 && tu.impl != c->opt_impl)) tu = default_tune<T>(c, geo);
+    if (c->opt_impl == 1) tu.impl = 1;
+    if (geo.inner > 1) return launch_cols<T>(c, geo, tu);
+    return launch_rows<T>(c, geo, tu);
+}
+
+// Autotuner: time candidate tile shapes of one sweep geometry on the bound
+// f with a zero shift (n = 0, nu = 0 leaves f bit-for-bit unchanged) and keep
+// the fastest.  Runs once per (kind, axis), never inside a stream capture.
+template <typename T>
+int tune_t(vp_ctx *c, int kick, int dim) {
+    const SweepGeo geo = make_geo(c, kick, dim);
+    SweepTune best = default_tune<T>(c, geo);
+    if (kick) VP_CUDA_TRY(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * c->NX, c->stream));
+    int rc = vp_launch_shift_table(c, kick, dim, 0.0, kick ? c->d_acc : nullptr);
+    if (rc) return rc;
+    SweepTune cand[32];
+    int nc = 0;
+    if (geo.inner > 1) {
+        const int impls[2] = {2, 1};
+        for (int ii = 0; ii < 2; ++ii) {
+            if (c->opt_impl && impls[ii] != c->opt_impl) continue;
+            for (int W = 32; W <= 128; W *= 2)
+                for (int nseg = 1; nseg <= 8; nseg *= 2) {
+                    const int th = W * nseg;
+                    if (th < 64 || th > 512 || nseg > geo.L) continue;
+                    const int Weff = geo.inner < W ? (int)geo.inner : W;
+                    if (impls[ii] == 2 && !tma_eligible<T>(c, geo, Weff)) continue;
+                    if (impls[ii] == 1 && (size_t)geo.L * W * sizeof(T) > 200 * 1024) continue;
+                    if (nc < 32) cand[nc++] = SweepTune{1, impls[ii], W, nseg, 0};
+                }
+        }
+    } else {
+        for (int R = 32; R <= 128; R *= 2)
+            for (int nseg = 1; nseg <= 8; nseg *= 2) {
+                const int th = R * nseg;
+                if (th < 64 || th > 512 || nseg > geo.L) continue;
+                if ((size_t)R * (geo.L | 1) * sizeof(T) > 200 * 1024) continue;
+                if (nc < 32) cand[nc++] = SweepTune{1, 1, R, nseg, 0};
+            }
+    }
+    if (nc == 0) {
+        c->tune[kick][dim] = best;
+        return VP_OK;
+    }
+    cudaEvent_t e0, e1;
+    VP_CUDA_TRY(c, cudaEventCreate(&e0));
+    VP_CUDA_TRY(c, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int i = 0; i < nc; ++i) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            rc = geo.inner > 1 ? launch_cols<T>(c, geo, cand[i]) : launch_rows<T>(c, geo, cand[i]);
+            cudaEventRecord(e1, c->stream);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float m = 0.f;
+            cudaEventElapsedTime(&m, e0, e1);
+            ms = m < ms ? m : ms;
+        }
+        if (rc) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best.valid = 1;
+    c->tune[kick][dim] = best;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
 }
@@ -427,4 +673,10 @@ int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double 
 int vp_launch_sweep(vp_ctx *c, int kick, int dim) {
     if (c->g.precision == VP_F32) return launch_sweep_t<float>(c, kick, dim);
     return launch_sweep_t<double>(c, kick, dim);
+}
+
+int vp_tune_sweep(vp_ctx *c, int kick, int dim) {
+    if (c->tune[kick][dim].valid) return VP_OK;
+    if (c->g.precision == VP_F32) return tune_t<float>(c, kick, dim);
+    return tune_t<double>(c, kick, dim);
 }

@@ -24,6 +24,7 @@ VP_POIS_PERIODIC, VP_POIS_ISOLATED = 0, 1
 VP_SPLIT_KDK, VP_SPLIT_DKD = 0, 1
 VP_IC_LANDAU, VP_IC_TWOSTREAM, VP_IC_PLUMMER, VP_IC_ADVECT = 0, 1, 2, 3
 VP_NDIAG = 9
+VP_OPT_SWEEP_IMPL, VP_OPT_AUTOTUNE = 1, 2
 DIAG_NAMES = ("mass", "ke", "fe", "pe", "min_f", "max_f", "mode_amp", "l1", "l2")
 
 _lock = threading.Lock()
@@ -92,6 +93,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_poisson_solve": (I, [P, P, P, P]),
             "vp_diagnostics": (I, [P, I, ctypes.POINTER(vp_diag)]),
             "vp_step": (I, [P, D, I, I, P, I, P]),
+            "vp_sync": (I, [P]),
+            "vp_set_option": (I, [P, I, LL]),
+            "vp_get_tuning": (I, [P, I, I, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -208,6 +212,20 @@ def vp_step(ctx, dt: float, split: int, nsteps: int, accel, mode: int = 1, diag=
     _check(ctx, load().vp_step(ctx, dt, split, nsteps, _ptr(accel), mode, _ptr(diag)))
 
 
+def vp_sync(ctx) -> None:
+    _check(ctx, load().vp_sync(ctx))
+
+
+def vp_set_option(ctx, option: int, value: int) -> None:
+    _check(ctx, load().vp_set_option(ctx, option, value))
+
+
+def vp_get_tuning(ctx, kick: int, dim: int) -> dict:
+    out = (ctypes.c_int * 4)()
+    _check(ctx, load().vp_get_tuning(ctx, kick, dim, ctypes.cast(out, ctypes.c_void_p)))
+    return {"impl": out[0], "tile": out[1], "segments": out[2], "ctas_per_sm": out[3]}
+
+
 # ---- convenience owner -----------------------------------------------------------
 
 class Simulation:
@@ -254,7 +272,7 @@ class Simulation:
         return vp_diagnostics(self.ctx, mode)
 
     def sync(self) -> None:
-        self.stream.synchronize()
+        vp_sync(self.ctx)
 
     def close(self) -> None:
         if self.ctx:

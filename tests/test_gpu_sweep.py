@@ -61,6 +61,50 @@ def test_fp64_sweeps_match_oracle(dims, nx, nv, order, xbc):
     sim.close()
 
 
+TMA_CASES = [
+    # every strided sweep eligible for the TMA kernel (inner % 4 == 0), with
+    # ragged column tiles and lines up to the 256-cell box limit
+    (1, [37], [132]),
+    (1, [256], [36]),
+    (2, [9, 7], [12, 20]),
+    (3, [5, 3, 4], [8, 4, 12]),
+]
+
+
+@pytest.mark.parametrize("dims,nx,nv", TMA_CASES)
+@pytest.mark.parametrize("impl", [1, 2])
+@pytest.mark.parametrize("precision", [V.VP_F64, V.VP_F32])
+def test_sweep_kernels_agree_with_oracle(dims, nx, nv, impl, precision):
+    """Both strided-axis kernels (staged loads, TMA pipeline) against the
+    oracle, with the autotuner on (it must leave f untouched)."""
+    g = grid(dims, nx, nv, order=7, xbc=1 if dims == 3 else 0)
+    sim, og = both(g, precision)
+    V.vp_set_option(sim.ctx, V.VP_OPT_SWEEP_IMPL, impl)
+    f0 = inputs.random_f(og.NX * og.NV, seed=23).astype(np.float32).astype(np.float64)
+    acc = inputs.random_accel(og.NX, dims, seed=8, amax=6.0)
+    tol_max = 1e-12 if precision == V.VP_F64 else None
+    for kick in (0, 1):
+        for d in range(dims):
+            f_o = f0.copy()
+            to_gpu(sim, f0)
+            if kick:
+                O.kick_sweep(og, f_o, d, 0.53, acc[d])
+                V.vp_kick_sweep(sim.ctx, d, 0.53, accel_tensor(sim, acc[d]))
+            else:
+                O.drift_sweep(og, f_o, d, 0.71)
+                V.vp_drift_sweep(sim.ctx, d, 0.71)
+            f_g = from_gpu(sim)
+            if tol_max:
+                assert rel_max(f_g, f_o) <= tol_max, (kick, d)
+            else:
+                assert rel_l1(f_g, f_o) <= 2e-6, (kick, d)
+            tu = V.vp_get_tuning(sim.ctx, kick, d)
+            assert tu["impl"] in (1, 2)
+            if impl == 1:
+                assert tu["impl"] == 1
+    sim.close()
+
+
 @pytest.mark.parametrize("mp,pp", [(0, 0), (1, 0), (0, 1)])
 def test_fp64_limiter_switches(mp, pp):
     g = grid(2, [12, 9], [20, 17], order=7, mp=mp, pp=pp)
