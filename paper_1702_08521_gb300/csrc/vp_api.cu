@@ -399,7 +399,8 @@ int vp_sync(vp_ctx *c) {
     VP_CUDA_TRY(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) {
         cudaMemset(c->d_status, 0, sizeof(int));
-        return vp_fail(c, VP_ETIMEOUT, "a device-side wait gave up (status %d)", st);
+        if (st == VP_ETIMEOUT) return vp_fail(c, VP_ETIMEOUT, "a device-side wait gave up");
+        return vp_fail(c, VP_ECUDA, "a kernel's self-check failed (status %d)", st);
     }
     return VP_OK;
 }

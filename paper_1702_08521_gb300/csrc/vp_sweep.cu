@@ -289,11 +289,22 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
     __shared__ __align__(8) uint64_t bar[2];
     const int W = geo.W, L = geo.L;
     const int tile = L * W;
-    T *in_buf = reinterpret_cast<T *>(smraw);  // [2][L][W]
-    T *out_buf = in_buf + 2 * tile;            // [2][L][W]
+    // TMA tensor copies need 128-byte aligned shared-memory buffers: align
+    // the dynamic region explicitly (the launch reserves 128 spare bytes)
+    const uint32_t base = vp_tma::saddr(smraw);
+    const uint32_t pad = (128u - (base & 127u)) & 127u;
+    T *in_buf = reinterpret_cast<T *>(smraw + pad);  // [2][L][W]
+    T *out_buf = in_buf + 2 * tile;                   // [2][L][W]
     const long long tpo = (geo.inner + W - 1) / W;
     const long long ntiles = geo.outer * tpo;
     const uint32_t bytes = (uint32_t)(tile * sizeof(T));
+    // self-check of every alignment the copies rely on; on failure report and
+    // leave before issuing any copy
+    if (((vp_tma::saddr(in_buf) | vp_tma::saddr(out_buf) | bytes) & 127u) != 0 ||
+        ((W * sizeof(T)) & 15u) != 0) {
+        if (threadIdx.x == 0) atomicExch(status, VP_EINVAL);
+        return;
+    }
     if (threadIdx.x == 0) {
         vp_tma::mbar_init(&bar[0], 1);
         vp_tma::mbar_init(&bar[1], 1);
@@ -446,7 +457,8 @@ bool tma_eligible(const vp_ctx *c, const SweepGeo &geo, int W) {
     constexpr int VEC = 16 / sizeof(T);
     return geo.inner > 1 && geo.inner % VEC == 0 && W % VEC == 0 && geo.inner < (1LL << 31) &&
            geo.outer < (1LL << 31) && geo.L <= 256 && W <= 256 &&
-           (size_t)4 * geo.L * W * sizeof(T) <= 200 * 1024 && tensor_map_encoder() != nullptr &&
+           ((size_t)geo.L * W * sizeof(T)) % 128 == 0 &&
+           (size_t)4 * geo.L * W * sizeof(T) + 128 <= 200 * 1024 && tensor_map_encoder() != nullptr &&
            (reinterpret_cast<uintptr_t>(c->f) & 15) == 0;
 }
 
@@ -476,7 +488,7 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
                                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return vp_fail(c, VP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-        const size_t smem = (size_t)4 * L * W * sizeof(T);
+        const size_t smem = (size_t)4 * L * W * sizeof(T) + 128;
         int per_sm = tu.ctas_per_sm;
         if (per_sm <= 0) {
             if (seven)
@@ -617,7 +629,11 @@ int tune_t(vp_ctx *c, int kick, int dim) {
             rc = geo.inner > 1 ? launch_cols<T>(c, geo, cand[i]) : launch_rows<T>(c, geo, cand[i]);
             cudaEventRecord(e1, c->stream);
             if (rc) break;
-            cudaEventSynchronize(e1);
+            const cudaError_t se = cudaEventSynchronize(e1);
+            if (se != cudaSuccess) {
+                rc = vp_fail(c, VP_ECUDA, "sweep candidate failed: %s", cudaGetErrorString(se));
+                break;
+            }
             float m = 0.f;
             cudaEventElapsedTime(&m, e0, e1);
             ms = m < ms ? m : ms;
