@@ -216,6 +216,35 @@ int vp_set_option(vp_ctx *ctx, int option, long long value);
  * CTAs per SM (0 = occupancy maximum)}; impl 0 means not tuned yet. */
 int vp_get_tuning(const vp_ctx *ctx, int kick, int dim, int *out4);
 
+/*
+ * vp_poisson_periodic_noalloc -- the periodic Poisson solve and force of
+ * vp_poisson_solve (same arguments and results for a grid with
+ * poisson == VP_POIS_PERIODIC), for callers that cannot allocate device
+ * memory while they run: code whose device memory is all owned by its own
+ * pool or caching allocator and budgeted up front, and latency-critical
+ * loops that cannot afford the device-wide synchronisation of cudaMalloc and
+ * cudaFree.  It needs no context and allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  The paper has no counterpart;
+ * this is a library entry point only.
+ *   grid:     the grid (only dx, nx, xlo, xhi, pois_order, coupling, rho_bg
+ *             and poisson are read); rho_dev: NX doubles in; phi_dev: NX
+ *             doubles out or NULL; accel_dev: dx * NX doubles out (device).
+ *   Limits:   NX = prod nx <= VP_NOALLOC_MAX_POINTS (262144), each axis
+ *             <= 4096 cells; larger grids return VP_EINVAL.
+ *   Scratch:  a 4 MiB static device array (VP_NOALLOC_MAX_POINTS complex
+ *             doubles) held by every GPU that loads the library until the
+ *             process exits.  Every call uses the same array and leaves its
+ *             contents behind; calls that overlap on the GPU (two streams,
+ *             two threads) race on it and must be serialised by the caller.
+ *   Set-up:   the first call on each device looks up the array's device
+ *             address (with that device current) and sets a kernel
+ *             attribute; make that first call before any stream capture.
+ * Returns VP_OK, VP_EINVAL (bad or too large grid, NULL array) or VP_ECUDA.
+ */
+#define VP_NOALLOC_MAX_POINTS 262144
+int vp_poisson_periodic_noalloc(const vp_grid *grid, void *cuda_stream, const double *rho_dev,
+                                double *phi_dev, double *accel_dev);
+
 #ifdef __cplusplus
 }
 #endif

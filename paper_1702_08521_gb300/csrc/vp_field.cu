@@ -8,6 +8,7 @@
 // double, then double across threads).  Fourier transforms, Green functions
 // and forces are double precision throughout.
 #include <cmath>
+#include <mutex>
 
 #include "vp_internal.cuh"
 
@@ -653,4 +654,121 @@ int vp_launch_init(vp_ctx *c, int kind, const double *p, int np) {
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
+}
+
+// ---- allocation-free periodic Poisson solve ------------------------------------
+// vp_poisson_periodic_noalloc: the periodic solve of vp_poisson_solve for
+// callers that must not allocate device memory.  Its complex FFT work array is
+// this file-scope device array (VP_NOALLOC_MAX_POINTS complex doubles, 4 MiB,
+// held by every device that loads the library until the process exits); the
+// Green function is evaluated on the fly instead of read from a table.  The
+// array is shared by all calls: calls that overlap on the GPU race on it.
+
+static __device__ __align__(256) double2 g_noalloc_fft[VP_NOALLOC_MAX_POINTS];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2 *g_noalloc_dev_ptr[kNoallocMaxDevices];
+
+__device__ double noalloc_stencil_eig(int order, double theta) {
+    // eigenvalue of the symmetric discrete Laplacian stencil (b_0..b_3)/den
+    // (Eqs. C1, C5, C6) times h^2: -(4/den) sum_m b_m sin^2(m theta / 2)
+    double b1 = 1.0, b2 = 0.0, b3 = 0.0, den = 1.0;
+    if (order == 4) {
+        b1 = 16.0;
+        b2 = -1.0;
+        den = 12.0;
+    } else if (order == 6) {
+        b1 = 270.0;
+        b2 = -27.0;
+        b3 = 2.0;
+        den = 180.0;
+    }
+    const double s1 = sin(0.5 * theta), s2 = sin(theta), s3 = sin(1.5 * theta);
+    return -4.0 * (b1 * s1 * s1 + b2 * s2 * s2 + b3 * s3 * s3) / den;
+}
+
+// multiply every Fourier mode by S / lambda(k) / NX (k = 0 -> 0)
+__global__ void k_green_onfly(double2 *__restrict__ a, long long NX, int dims, int3 n, double3 h,
+                              int order, double S) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= NX) return;
+    const int nn[3] = {n.x, n.y, n.z};
+    const double hh[3] = {h.x, h.y, h.z};
+    long long r = x;
+    bool allzero = true;
+    double lam = 0.0;
+    for (int d = dims - 1; d >= 0; --d) {
+        const long long k = r % nn[d];
+        r /= nn[d];
+        if (k) allzero = false;
+        lam += noalloc_stencil_eig(order, 2.0 * 3.141592653589793238462643383279502884 * (double)k / (double)nn[d]) /
+               (hh[d] * hh[d]);
+    }
+    const double sc = allzero ? 0.0 : S / lam / (double)NX;
+    a[x] = make_double2(a[x].x * sc, a[x].y * sc);
+}
+
+}  // namespace
+
+extern "C" int vp_poisson_periodic_noalloc(const vp_grid *g, void *cuda_stream, const double *rho_dev,
+                                           double *phi_dev, double *accel_dev) {
+    if (!g || !rho_dev || !accel_dev) return VP_EINVAL;
+    if (g->dx < 1 || g->dx > 3 || g->poisson != VP_POIS_PERIODIC) return VP_EINVAL;
+    if (g->pois_order != 2 && g->pois_order != 4 && g->pois_order != 6) return VP_EINVAL;
+    if (!std::isfinite(g->coupling) || !std::isfinite(g->rho_bg)) return VP_EINVAL;
+    const int D = g->dx;
+    long long NX = 1;
+    for (int d = 0; d < D; ++d) {
+        if (g->nx[d] < 1 || g->nx[d] > 4096) return VP_EINVAL;
+        if (!(g->xhi[d] > g->xlo[d]) || !std::isfinite(g->xhi[d]) || !std::isfinite(g->xlo[d]))
+            return VP_EINVAL;
+        NX *= g->nx[d];
+    }
+    if (NX > VP_NOALLOC_MAX_POINTS) return VP_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return VP_ECUDA;
+    double2 *buf = nullptr;
+    {
+        // once per device, with that device current: the device address of the
+        // static array (its name in host code is only a host-side stand-in)
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_dev_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_fft) != cudaSuccess || !p) return VP_ECUDA;
+            if (cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     2 * 4096 * (int)sizeof(double2)) != cudaSuccess)
+                return VP_ECUDA;
+            g_noalloc_dev_ptr[dev] = static_cast<double2 *>(p);
+        }
+        buf = g_noalloc_dev_ptr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int3 nb = make_int3(g->nx[0], D > 1 ? g->nx[1] : 1, D > 2 ? g->nx[2] : 1);
+    const int m[3] = {nb.x, nb.y, nb.z};
+    // every element of the work array that is read is written first: no clearing needed
+    k_load_rho<<<nblk(NX, kBlock), kBlock, 0, st>>>(buf, rho_dev, g->rho_bg, NX, nb, nb, D);
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int a = 0; a < D; ++a) {
+            long long inner = 1;
+            for (int d = a + 1; d < D; ++d) inner *= m[d];
+            const size_t smem = 2 * (size_t)m[a] * sizeof(double2);
+            const int th = m[a] / 2 < 32 ? 32 : (m[a] / 2 > 256 ? 256 : m[a] / 2);
+            k_fft_axis<<<(unsigned)(NX / m[a]), th, smem, st>>>(buf, inner, m[a], pass == 0 ? -1 : +1);
+        }
+        if (pass == 0) {
+            const double3 h = make_double3((g->xhi[0] - g->xlo[0]) / g->nx[0],
+                                           D > 1 ? (g->xhi[1] - g->xlo[1]) / g->nx[1] : 1.0,
+                                           D > 2 ? (g->xhi[2] - g->xlo[2]) / g->nx[2] : 1.0);
+            k_green_onfly<<<nblk(NX, kBlock), kBlock, 0, st>>>(buf, NX, D, nb, h, g->pois_order, g->coupling);
+        }
+    }
+    const double3 h = make_double3((g->xhi[0] - g->xlo[0]) / g->nx[0],
+                                   D > 1 ? (g->xhi[1] - g->xlo[1]) / g->nx[1] : 1.0,
+                                   D > 2 ? (g->xhi[2] - g->xlo[2]) / g->nx[2] : 1.0);
+    k_force<<<nblk(NX, kBlock), kBlock, 0, st>>>(buf, 1.0, phi_dev, accel_dev, NX, nb, nb, D, h,
+                                                 fda_coeffs(g->pois_order), g->pois_order / 2);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
 }

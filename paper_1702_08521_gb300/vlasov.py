@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_sync": (I, [P]),
             "vp_set_option": (I, [P, I, LL]),
             "vp_get_tuning": (I, [P, I, I, P]),
+            "vp_poisson_periodic_noalloc": (I, [GP, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -224,6 +225,16 @@ def vp_get_tuning(ctx, kick: int, dim: int) -> dict:
     out = (ctypes.c_int * 4)()
     _check(ctx, load().vp_get_tuning(ctx, kick, dim, ctypes.cast(out, ctypes.c_void_p)))
     return {"impl": out[0], "tile": out[1], "segments": out[2], "ctas_per_sm": out[3]}
+
+
+VP_NOALLOC_MAX_POINTS = 262144
+
+
+def vp_poisson_periodic_noalloc(grid: vp_grid, stream, rho, phi, accel) -> int:
+    """Allocation-free periodic Poisson solve (returns the VP_* status code)."""
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    return int(load().vp_poisson_periodic_noalloc(ctypes.byref(grid), ctypes.c_void_p(h), _ptr(rho),
+                                                  _ptr(phi), _ptr(accel)))
 
 
 # ---- convenience owner -----------------------------------------------------------
