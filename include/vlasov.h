@@ -216,6 +216,52 @@ int vp_set_option(vp_ctx *ctx, int option, long long value);
  * CTAs per SM (0 = occupancy maximum)}; impl 0 means not tuned yet. */
 int vp_get_tuning(const vp_ctx *ctx, int kick, int dim, int *out4);
 
+/* ---- batched ensembles ---------------------------------------------------
+ * Many independent 1D1V / 2D2V runs of uneven size (FP32, MP5 or MP7 with
+ * MP and PP, periodic space, zero-inflow velocity, periodic Poisson) advanced
+ * together: one KDK step (Eq. 55) of every run is one persistent kernel
+ * launch working through a queue of (run, stage, tile) items with per-run
+ * stage counters (bounded waits), captured once in a CUDA graph.  All runs'
+ * f live in one caller-owned FP32 pool (run r at its f_offset, layout as for
+ * a single run); the library owns the per-run fields and the work plan.
+ */
+typedef struct {
+    int dims;               /* 1 or 2 (dv == dx) */
+    int nx[2], nv[2];       /* spatial axes: powers of two <= 256, NX <= 4096; nv <= 4096 */
+    double xlo[2], xhi[2], vlo[2], vhi[2];
+    double coupling, rho_bg;/* as in vp_grid */
+    int pois_order;         /* 2, 4 or 6 */
+} vp_run_desc;
+
+typedef struct vp_ens vp_ens;
+
+int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda_stream, vp_ens **out);
+void vp_ensemble_destroy(vp_ens *ens);
+const char *vp_ensemble_last_error(const vp_ens *ens);
+/* cells of the pool (sum of the runs' cells, each run padded to 32 floats) */
+long long vp_ensemble_num_cells(const vp_ens *ens);
+/* element offset of run `run` in the pool and of its field in the field array */
+int vp_ensemble_run_layout(const vp_ens *ens, int run, long long *f_offset, long long *acc_offset);
+/* attach the caller's FP32 pool (vp_ensemble_num_cells floats, 128-byte aligned) */
+int vp_ensemble_bind(vp_ens *ens, float *pool_dev);
+/* analytic initial condition of one run (VP_IC_LANDAU or VP_IC_TWOSTREAM, as vp_init_f) */
+int vp_ensemble_init_run(vp_ens *ens, int run, int kind, const double *params, int nparams);
+/* density + Poisson of every run from the current f (needed once before the first step); synchronises */
+int vp_ensemble_field(vp_ens *ens);
+/* device pointer to the field array (sum over runs of dims * NX doubles) */
+int vp_ensemble_accel(const vp_ens *ens, const double **accel_dev);
+/* tile shapes: W columns per strided tile, R lines per contiguous tile (both
+ * dividing 256), CTAs per SM of the persistent grid (0 = occupancy maximum) */
+int vp_ensemble_set_tiles(vp_ens *ens, int W, int R, int ctas_per_sm);
+int vp_ensemble_get_tiles(const vp_ens *ens, int *out3);
+/* time candidate tile shapes with whole steps at dt = 0 (f unchanged); keep the fastest; synchronises */
+int vp_ensemble_autotune(vp_ens *ens);
+/* nsteps KDK steps of every run (one persistent launch each, graph replay) */
+int vp_ensemble_step(vp_ens *ens, double dt, int nsteps);
+/* wait for the stream; VP_ETIMEOUT if a bounded wait in the kernel gave up */
+int vp_ensemble_sync(vp_ens *ens);
+long long vp_ensemble_launch_count(const vp_ens *ens);
+
 /*
  * vp_poisson_periodic_noalloc -- the periodic Poisson solve and force of
  * vp_poisson_solve (same arguments and results for a grid with

@@ -27,7 +27,9 @@ namespace {
 // measured by y = 1/2 - x so that the flux interface is y = 0 and the
 // departure point is y = nu.  With Q_k(y) = sum_{m >= k} l_m(y) (l_m the
 // Lagrange basis on the nodes y_m = -m), w_k(nu) = -(Q_k(nu) - Q_k(0)) / nu.
-WPoly csl_weight_polys(int order) {
+}  // namespace
+
+WPoly vp_csl_weight_polys(int order) {
     WPoly wp{};
     const int h = (order - 1) / 2;
     const int npt = 2 * h + 2;          // interfaces
@@ -63,6 +65,8 @@ WPoly csl_weight_polys(int order) {
     }
     return wp;
 }
+
+namespace {
 
 bool is_fin(double x) { return std::isfinite(x); }
 
@@ -234,7 +238,7 @@ int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out) {
     }
     c->ncell = c->NX * c->NV;
     c->esize = c->g.precision == VP_F32 ? 4 : 8;
-    c->wp = csl_weight_polys(c->g.order);
+    c->wp = vp_csl_weight_polys(c->g.order);
     long long ncls = c->NX;
     for (int d = 0; d < c->g.dv; ++d) ncls = c->g.nv[d] > ncls ? c->g.nv[d] : ncls;
     c->shift_cap = ncls;

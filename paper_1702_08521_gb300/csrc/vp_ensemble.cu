@@ -1,0 +1,884 @@
+// vp_ensemble.cu -- batched ensembles of independent 1D1V / 2D2V
+// Vlasov-Poisson runs (uneven sizes) advanced one KDK step per persistent
+// kernel launch, the step captured in a CUDA graph.
+//
+// Work queue: one step of every run is a list of items (run, stage, tile)
+// sorted by stage.  Each CTA of a persistent grid pops the next item with an
+// atomic counter, waits (bounded) until the previous stage of that run has
+// finished all its tiles, processes the tile and counts it done.  Items are
+// popped in queue order by running CTAs only, so every wait is on work that a
+// running CTA already holds: no deadlock, whatever the residency.
+//
+// Stages of a KDK step (Eq. 55), per run:
+//   1D1V: kick v (dt/2) | drift x (dt) | density + Poisson | kick v (dt/2)
+//   2D2V: kick v1, kick v2 (dt/2) | drift x2, drift x1 (dt) | density |
+//         Poisson | kick v1, kick v2 (dt/2)
+// Sweeps reuse the line walker of the single-run kernels; the shift of every
+// line is decomposed in FP64 on the fly.  Data written by other CTAs inside
+// the launch (f of the previous stage, density, field) is read with L1-bypass
+// loads (ld.global.cg).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vp_internal.cuh"
+#include "vp_sweep_core.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxStages = 8;
+
+enum StageKind { ST_COLS = 0, ST_ROWS = 1, ST_MOMENT = 2, ST_POISSON = 3 };
+
+struct StageDesc {
+    int kind;
+    int kick;        // 1: velocity axis (speed = acceleration), 0: spatial axis
+    int axis;        // axis index within x or v
+    int half;        // 1: dt/2
+    long long outer, inner;
+    int L;
+    int periodic;
+    int cls_from_inner;
+    long long cdiv, cmod;
+    int tiles;
+    int tw;          // tile width: columns (strided sweep) or lines (contiguous sweep)
+    int done_slot;   // index of this stage's completion counter
+};
+
+struct RunDesc {
+    long long f_off;
+    int dims;
+    int nx[2], nv[2];
+    long long NX, NV;
+    double xlo[2], hx[2], vlo[2], hv[2];
+    long long acc_off, rho_off;
+    double coupling, rho_bg;
+    int pois_order;
+    int nstage;
+    StageDesc st[kMaxStages];
+};
+
+struct EnsItem {
+    int run, stage, tile, pad;
+};
+
+struct EnsParams {
+    double dt;
+    double alpha;
+    int mp, pp, order;
+    int W, R;          // tile widths of strided / contiguous sweeps
+    int xpt;           // spatial points per density tile
+    WPoly wp;
+};
+
+// ---- device helpers ----------------------------------------------------------------
+
+__device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+
+// wait until counter >= target (thread 0); false on timeout
+__device__ bool wait_count(const unsigned *ctr, unsigned target) {
+    for (unsigned it = 0; it < (1u << 24); ++it) {
+        const unsigned v = *reinterpret_cast<const volatile unsigned *>(ctr);
+        if (v >= target) {
+            __threadfence();
+            return true;
+        }
+        __nanosleep(64);
+    }
+    return false;
+}
+
+template <int ORDER, bool PER>
+__device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int tile,
+                          const double *acc_pool, const EnsParams &P, float *sm) {
+    const int L = s.L;
+    const int W = s.tw;
+    const long long tpo = (s.inner + W - 1) / W;
+    const long long o = tile / tpo;
+    const long long c0 = (tile % tpo) * W;
+    const int wc = (int)((s.inner - c0) < W ? (s.inner - c0) : W);
+    float *base = pool + r.f_off + o * L * s.inner + c0;
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        sm[c] = 0.f;
+        sm[(L + 1) * W + c] = 0.f;
+    }
+    for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
+        const int row = e / W, cc = e - row * W;
+        sm[W + e] = cc < wc ? ldcg(base + (long long)row * s.inner + cc) : 0.f;
+    }
+    __syncthreads();
+    const int nseg = blockDim.x / W;
+    const int cc = threadIdx.x % W, seg = threadIdx.x / W;
+    if (cc < wc && seg < nseg) {
+        const unsigned cls = s.cls_from_inner ? (unsigned)(((c0 + cc) / s.cdiv) % s.cmod) : (unsigned)(o / s.cdiv);
+        const double dt = s.half ? 0.5 * P.dt : P.dt;
+        double speed, h;
+        if (s.kick) {
+            speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
+            h = r.hv[s.axis];
+        } else {
+            speed = vp_core::cell_centre(r.vlo[s.axis], r.hv[s.axis], (int)cls);
+            h = r.hx[s.axis];
+        }
+        const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, P.wp);
+        const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
+        const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+        struct St {
+            float *p;
+            long long step;
+            __device__ void operator()(int, float v) {
+                *p = v;
+                p += step;
+            }
+        } st{base + cc + (long long)i0 * s.inner, (long long)sh.sigma * s.inner};
+        vp_core::walk<float, ORDER, PER, true>(sm + (PER ? W : 0) + cc, W, L, sh, r0, r1, (float)P.alpha, P.mp,
+                                         P.pp, st);
+    }
+}
+
+template <int ORDER>
+__device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int tile,
+                          const double *acc_pool, const EnsParams &P, float *sm) {
+    const int L = s.L;
+    const int R = s.tw;
+    const int Pp = (L + 2) | 1, Q = L | 1;
+    float *in = sm, *out = sm + R * Pp;
+    const long long l0 = (long long)tile * R;
+    const int nl = (int)((s.outer - l0) < R ? (s.outer - l0) : R);
+    float *base = pool + r.f_off + l0 * L;
+    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+        in[k * Pp] = 0.f;
+        in[k * Pp + L + 1] = 0.f;
+    }
+    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+        const int row = e / L, pos = e - row * L;
+        in[row * Pp + 1 + pos] = ldcg(base + e);
+    }
+    __syncthreads();
+    const int nseg = blockDim.x / R;
+    const int line = threadIdx.x % R, seg = threadIdx.x / R;
+    if (line < nl && seg < nseg) {
+        const unsigned cls = (unsigned)((l0 + line) / s.cdiv);
+        const double dt = s.half ? 0.5 * P.dt : P.dt;
+        const double speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
+        const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, r.hv[s.axis], P.wp);
+        const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
+        const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+        struct St {
+            float *p;
+            int step;
+            __device__ void operator()(int, float v) {
+                *p = v;
+                p += step;
+            }
+        } st{out + line * Q + i0, sh.sigma};
+        vp_core::walk<float, ORDER, false, true>(in + line * Pp, 1, L, sh, r0, r1, (float)P.alpha, P.mp, P.pp, st);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+        const int row = e / L, pos = e - row * L;
+        base[e] = out[row * Q + pos];
+    }
+}
+
+__device__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// density of spatial points [x0, x1): one warp per point, compensated float
+// sums per lane combined in double
+__device__ void density_points(const float *pool, const RunDesc &r, long long x0, long long x1,
+                               double *rho_pool) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double dV = r.dims == 1 ? r.hv[0] : r.hv[0] * r.hv[1];
+    for (long long x = x0 + warp; x < x1; x += nw) {
+        const float *p = pool + r.f_off + x * r.NV;
+        float s = 0.f, e = 0.f;
+        for (long long v = lane; v < r.NV; v += 32) {
+            const float y = ldcg(p + v);
+            const float t = s + y;
+            const float bp = t - s;
+            e += (s - (t - bp)) + (y - bp);
+            s = t;
+        }
+        const double tot = warp_sum_d((double)s + (double)e);
+        if (lane == 0) rho_pool[r.rho_off + x] = tot * dV;
+    }
+}
+
+// batched in-place radix-2 FFT of a row-major [n0][n1] (or [n0]) complex
+// array in shared memory along `axis`; sign -1 forward, +1 inverse (no 1/n)
+__device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sign) {
+    const int n = axis == 0 ? n0 : n1;
+    const int lines = dims == 1 ? 1 : (axis == 0 ? n1 : n0);
+    const int stride = (dims == 1 || axis == 1) ? 1 : n1;   // element stride along the axis
+    const int lstride = (dims == 1) ? 0 : (axis == 0 ? 1 : n1);  // stride between lines
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    // bit-reversal permutation
+    for (int t = threadIdx.x; t < lines * n; t += blockDim.x) {
+        const int l = t / n, j = t - l * n;
+        const int rj = logn ? (int)(__brev((unsigned)j) >> (32 - logn)) : 0;
+        if (j < rj) {
+            double2 *pa = a + l * lstride + j * stride, *pb = a + l * lstride + rj * stride;
+            const double2 tmp = *pa;
+            *pa = *pb;
+            *pb = tmp;
+        }
+    }
+    __syncthreads();
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1;
+        for (int t = threadIdx.x; t < lines * (n / 2); t += blockDim.x) {
+            const int l = t / (n / 2), b = t - l * (n / 2);
+            const int grp = b / half, k = b - grp * half;
+            const int i0 = grp * len + k, i1 = i0 + half;
+            double sn, cs;
+            sincospi((double)sign * 2.0 * (double)k / (double)len, &sn, &cs);
+            double2 *pu = a + l * lstride + i0 * stride, *pv = a + l * lstride + i1 * stride;
+            const double2 u = *pu, v = *pv;
+            const double2 tw = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+            *pu = make_double2(u.x + tw.x, u.y + tw.y);
+            *pv = make_double2(u.x - tw.x, u.y - tw.y);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ double lap_eig(int order, double theta) {
+    // eigenvalue (times h^2) of the symmetric discrete Laplacian stencil of
+    // Eqs. C1, C5, C6: -(4 / den) sum_m b_m sin^2(m theta / 2)
+    double b1 = 1.0, b2 = 0.0, b3 = 0.0, den = 1.0;
+    if (order == 4) {
+        b1 = 16.0;
+        b2 = -1.0;
+        den = 12.0;
+    } else if (order == 6) {
+        b1 = 270.0;
+        b2 = -27.0;
+        b3 = 2.0;
+        den = 180.0;
+    }
+    const double s1 = sin(0.5 * theta), s2 = sin(theta), s3 = sin(1.5 * theta);
+    return -4.0 * (b1 * s1 * s1 + b2 * s2 * s2 + b3 * s3 * s3) / den;
+}
+
+// periodic Poisson + FDA force of one run, all in one CTA (NX <= 4096)
+__device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *acc_pool, double2 *a) {
+    const int D = r.dims;
+    const int n0 = r.nx[0], n1 = D == 2 ? r.nx[1] : 1;
+    const long long NX = r.NX;
+    for (long long x = threadIdx.x; x < NX; x += blockDim.x)
+        a[x] = make_double2(ldcg(rho_pool + r.rho_off + x) - r.rho_bg, 0.0);
+    __syncthreads();
+    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, -1);
+    const double kTwoPi = 6.283185307179586476925286766559;
+    for (long long x = threadIdx.x; x < NX; x += blockDim.x) {
+        const int k0 = (int)(D == 2 ? x / n1 : x);
+        const int k1 = (int)(D == 2 ? x % n1 : 0);
+        double lam = lap_eig(r.pois_order, kTwoPi * (double)k0 / (double)n0) / (r.hx[0] * r.hx[0]);
+        if (D == 2) lam += lap_eig(r.pois_order, kTwoPi * (double)k1 / (double)n1) / (r.hx[1] * r.hx[1]);
+        const double sc = (k0 == 0 && k1 == 0) ? 0.0 : r.coupling / lam / (double)NX;
+        a[x] = make_double2(a[x].x * sc, a[x].y * sc);
+    }
+    __syncthreads();
+    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, +1);
+    // a = -grad phi by the 2/4/6-point FDA (Eqs. C9-C11)
+    double c1 = 1.0, c2 = 0.0, c3 = 0.0, den = 2.0;
+    if (r.pois_order == 4) {
+        c1 = 8.0;
+        c2 = -1.0;
+        den = 12.0;
+    } else if (r.pois_order == 6) {
+        c1 = 45.0;
+        c2 = -9.0;
+        c3 = 1.0;
+        den = 60.0;
+    }
+    for (long long x = threadIdx.x; x < NX; x += blockDim.x) {
+        const int i0 = (int)(D == 2 ? x / n1 : x);
+        const int i1 = (int)(D == 2 ? x % n1 : 0);
+        for (int d = 0; d < D; ++d) {
+            auto at = [&](int off) -> double {
+                int j0 = i0, j1 = i1;
+                if (d == 0) j0 = ((i0 + off) % n0 + n0) % n0;
+                else j1 = ((i1 + off) % n1 + n1) % n1;
+                return a[j0 * n1 + j1].x;
+            };
+            const double g = c1 * (at(1) - at(-1)) + c2 * (at(2) - at(-2)) + c3 * (at(3) - at(-3));
+            acc_pool[r.acc_off + (long long)d * NX + x] = -g / (den * r.hx[d]);
+        }
+    }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_ensemble(float *__restrict__ pool,
+                                                       const RunDesc *__restrict__ runs,
+                                                       const EnsItem *__restrict__ items, int nitems,
+                                                       unsigned *__restrict__ ctr, double *acc_pool,
+                                                       double *rho_pool, EnsParams P,
+                                                       int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char ens_smem[];
+    __shared__ int s_item;
+    __shared__ int s_ok;
+    unsigned *head = ctr;
+    unsigned *done = ctr + 1;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const EnsItem e = items[it];
+        const RunDesc &r = runs[e.run];
+        const StageDesc &s = r.st[e.stage];
+        if (threadIdx.x == 0) {
+            s_ok = 1;
+            if (e.stage > 0) {
+                const StageDesc &prev = r.st[e.stage - 1];
+                if (!wait_count(done + prev.done_slot, (unsigned)prev.tiles)) {
+                    atomicExch(status, VP_ETIMEOUT);
+                    s_ok = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        if (s.kind == ST_COLS) {
+            if (s.periodic)
+                tile_cols<ORDER, true>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
+            else
+                tile_cols<ORDER, false>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
+        } else if (s.kind == ST_ROWS) {
+            tile_rows<ORDER>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
+        } else if (s.kind == ST_MOMENT) {
+            const long long x0 = (long long)e.tile * P.xpt;
+            const long long x1 = x0 + P.xpt < r.NX ? x0 + P.xpt : r.NX;
+            density_points(pool, r, x0, x1, rho_pool);
+        } else {
+            if (r.dims == 1) {  // the 1D density is small enough to fuse here
+                density_points(pool, r, 0, r.NX, rho_pool);
+                __threadfence_block();
+                __syncthreads();
+            }
+            poisson_run(r, rho_pool, acc_pool, reinterpret_cast<double2 *>(ens_smem));
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(done + s.done_slot, 1u);
+    }
+}
+
+size_t smem_need(const std::vector<RunDesc> &runs) {
+    size_t need = 0;
+    for (const RunDesc &r : runs) {
+        for (int k = 0; k < r.nstage; ++k) {
+            const StageDesc &s = r.st[k];
+            size_t b = 0;
+            if (s.kind == ST_COLS) {
+                b = (size_t)(s.L + 2) * s.tw * sizeof(float);
+            } else if (s.kind == ST_ROWS) {
+                b = (size_t)s.tw * (((s.L + 2) | 1) + (s.L | 1)) * sizeof(float);
+            } else if (s.kind == ST_POISSON) {
+                b = (size_t)r.NX * sizeof(double2);
+            }
+            need = b > need ? b : need;
+        }
+    }
+    return need;
+}
+
+}  // namespace
+
+// ---- host side --------------------------------------------------------------------
+
+struct vp_ens {
+    std::vector<RunDesc> runs;
+    std::vector<EnsItem> items_step, items_field;
+    cudaStream_t stream;
+    int device, sm_count;
+    float *pool;
+    long long pool_cells;
+    double *d_acc, *d_rho;
+    long long acc_total, rho_total;
+    RunDesc *d_runs;
+    EnsItem *d_items_step, *d_items_field;
+    unsigned *d_ctr;
+    int nslots;
+    int *d_status;
+    EnsParams P;
+    int ctas_per_sm;
+    size_t smem;
+    int tuned;
+    cudaGraphExec_t graph;
+    double graph_dt;
+    int graph_valid;
+    long long launches;
+    char err[256];
+};
+
+static int ens_fail(vp_ens *e, int code, const char *msg) {
+    if (e) snprintf(e->err, sizeof(e->err), "%s", msg);
+    return code;
+}
+
+// stage lists of one run
+static int build_stages(RunDesc &r, int W, int R, int xpt, int &slot) {
+    const int D = r.dims;
+    auto cols = [&](int kick, int axis, int half, long long outer, int L, long long inner, int per,
+                    int from_inner, long long cdiv, long long cmod) {
+        StageDesc s{};
+        s.kind = ST_COLS;
+        s.kick = kick;
+        s.axis = axis;
+        s.half = half;
+        s.outer = outer;
+        s.L = L;
+        s.inner = inner;
+        s.periodic = per;
+        s.cls_from_inner = from_inner;
+        s.cdiv = cdiv;
+        s.cmod = cmod;
+        // tile width: the requested W, halved until the staged tile fits 36 KB
+        int w = W;
+        while (w > 8 && (size_t)(L + 2) * w * sizeof(float) > 36 * 1024) w /= 2;
+        if (inner < w) w = (int)inner;
+        s.tw = w;
+        s.tiles = (int)(outer * ((inner + w - 1) / w));
+        return s;
+    };
+    auto rows = [&](int axis, long long outer, int L, long long cdiv) {
+        StageDesc s{};
+        s.kind = ST_ROWS;
+        s.kick = 1;
+        s.axis = axis;
+        s.half = 1;
+        s.outer = outer;
+        s.L = L;
+        s.inner = 1;
+        s.cdiv = cdiv;
+        s.cmod = 1;
+        int rr = R;
+        while (rr > 8 && (size_t)rr * (((L + 2) | 1) + (L | 1)) * sizeof(float) > 36 * 1024) rr /= 2;
+        s.tw = rr;
+        s.tiles = (int)((outer + rr - 1) / rr);
+        return s;
+    };
+    int k = 0;
+    if (D == 1) {
+        r.st[k++] = rows(0, r.NX, r.nv[0], 1);
+        r.st[k++] = cols(0, 0, 0, 1, r.nx[0], r.NV, 1, 1, 1, r.nv[0]);
+        StageDesc p{};
+        p.kind = ST_POISSON;
+        p.tiles = 1;
+        r.st[k++] = p;
+        r.st[k++] = rows(0, r.NX, r.nv[0], 1);
+    } else {
+        // kick v1 (strided over v2), kick v2 (contiguous)
+        r.st[k++] = cols(1, 0, 1, r.NX, r.nv[0], r.nv[1], 0, 0, 1, 1);
+        r.st[k++] = rows(1, r.NX * r.nv[0], r.nv[1], r.nv[0]);
+        // drift x2 then x1 (Eq. 55 order)
+        r.st[k++] = cols(0, 1, 0, r.nx[0], r.nx[1], r.NV, 1, 1, 1, r.nv[1]);
+        r.st[k++] = cols(0, 0, 0, 1, r.nx[0], (long long)r.nx[1] * r.NV, 1, 1, r.nv[1], r.nv[0]);
+        StageDesc m{};
+        m.kind = ST_MOMENT;
+        m.tiles = (int)((r.NX + xpt - 1) / xpt);
+        r.st[k++] = m;
+        StageDesc p{};
+        p.kind = ST_POISSON;
+        p.tiles = 1;
+        r.st[k++] = p;
+        r.st[k++] = cols(1, 0, 1, r.NX, r.nv[0], r.nv[1], 0, 0, 1, 1);
+        r.st[k++] = rows(1, r.NX * r.nv[0], r.nv[1], r.nv[0]);
+    }
+    r.nstage = k;
+    for (int i = 0; i < k; ++i) r.st[i].done_slot = slot++;
+    return VP_OK;
+}
+
+static void build_items(vp_ens *e) {
+    e->items_step.clear();
+    e->items_field.clear();
+    int maxst = 0;
+    for (const RunDesc &r : e->runs) maxst = r.nstage > maxst ? r.nstage : maxst;
+    for (int st = 0; st < maxst; ++st)
+        for (int ri = 0; ri < (int)e->runs.size(); ++ri) {
+            const RunDesc &r = e->runs[ri];
+            if (st >= r.nstage) continue;
+            for (int t = 0; t < r.st[st].tiles; ++t) e->items_step.push_back(EnsItem{ri, st, t, 0});
+        }
+    // field-only list: the density (2D) and Poisson stages, as stages 0/1 of a
+    // separate pass (their waits refer to the previous stage of the same list)
+    for (int ri = 0; ri < (int)e->runs.size(); ++ri) {
+        const RunDesc &r = e->runs[ri];
+        for (int st = 0; st < r.nstage; ++st)
+            if (r.st[st].kind == ST_MOMENT || r.st[st].kind == ST_POISSON)
+                for (int t = 0; t < r.st[st].tiles; ++t) e->items_field.push_back(EnsItem{ri, st, t, 0});
+    }
+}
+
+static int upload_plan(vp_ens *e) {
+    cudaFree(e->d_runs);
+    cudaFree(e->d_items_step);
+    cudaFree(e->d_items_field);
+    e->d_runs = nullptr;
+    e->d_items_step = e->d_items_field = nullptr;
+    if (cudaMalloc(&e->d_runs, sizeof(RunDesc) * e->runs.size()) != cudaSuccess ||
+        cudaMalloc(&e->d_items_step, sizeof(EnsItem) * e->items_step.size()) != cudaSuccess ||
+        cudaMalloc(&e->d_items_field, sizeof(EnsItem) * (e->items_field.size() + 1)) != cudaSuccess)
+        return ens_fail(e, VP_ENOMEM, "plan allocation failed");
+    if (cudaMemcpy(e->d_runs, e->runs.data(), sizeof(RunDesc) * e->runs.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(e->d_items_step, e->items_step.data(), sizeof(EnsItem) * e->items_step.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_items_field, e->items_field.data(), sizeof(EnsItem) * e->items_field.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return ens_fail(e, VP_ECUDA, "plan upload failed");
+    return VP_OK;
+}
+
+// the field pass waits on stage - 1 of the full list; give it its own view in
+// which the density stage (2D) precedes Poisson and nothing precedes density
+static int launch_pass(vp_ens *e, const EnsItem *items, int nitems, double dt) {
+    EnsParams P = e->P;
+    P.dt = dt;
+    if (cudaMemsetAsync(e->d_ctr, 0, sizeof(unsigned) * (e->nslots + 1), e->stream) != cudaSuccess)
+        return ens_fail(e, VP_ECUDA, "counter reset failed");
+    const int grid = e->ctas_per_sm * e->sm_count;
+    if (e->P.order == 7)
+        k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
+                                                             e->d_acc, e->d_rho, P, e->d_status);
+    else
+        k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
+                                                             e->d_acc, e->d_rho, P, e->d_status);
+    e->launches++;
+    const cudaError_t er = cudaGetLastError();
+    if (er != cudaSuccess) return ens_fail(e, VP_ECUDA, cudaGetErrorString(er));
+    return VP_OK;
+}
+
+extern "C" {
+
+int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda_stream, vp_ens **out) {
+    if (!out) return VP_EINVAL;
+    *out = nullptr;
+    if (!runs || nruns < 1 || (order != 5 && order != 7)) return VP_EINVAL;
+    vp_ens *e = new (std::nothrow) vp_ens();
+    if (!e) return VP_ENOMEM;
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&e->device);
+    cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, e->device);
+    e->P.alpha = 4.0;
+    e->P.mp = 1;
+    e->P.pp = 1;
+    e->P.order = order;
+    e->P.W = 64;
+    e->P.R = 32;
+    e->P.xpt = 8;
+    e->P.wp = vp_csl_weight_polys(order);
+    long long off = 0, aoff = 0, roff = 0;
+    int slot = 0;
+    for (int i = 0; i < nruns; ++i) {
+        const vp_run_desc &d = runs[i];
+        RunDesc r{};
+        if (d.dims < 1 || d.dims > 2) {
+            delete e;
+            return VP_EINVAL;
+        }
+        r.dims = d.dims;
+        r.NX = r.NV = 1;
+        for (int k = 0; k < d.dims; ++k) {
+            if (d.nx[k] < 1 || d.nv[k] < 1 || d.nv[k] > 4096 || d.nx[k] > 256 ||
+                (d.nx[k] & (d.nx[k] - 1)) != 0 || !(d.xhi[k] > d.xlo[k]) || !(d.vhi[k] > d.vlo[k])) {
+                delete e;
+                return VP_EINVAL;  // power-of-two spatial axes up to 256 (one-CTA FFT)
+            }
+            r.nx[k] = d.nx[k];
+            r.nv[k] = d.nv[k];
+            r.xlo[k] = d.xlo[k];
+            r.vlo[k] = d.vlo[k];
+            r.hx[k] = (d.xhi[k] - d.xlo[k]) / d.nx[k];
+            r.hv[k] = (d.vhi[k] - d.vlo[k]) / d.nv[k];
+            r.NX *= d.nx[k];
+            r.NV *= d.nv[k];
+        }
+        if (r.NX > 4096) {
+            delete e;
+            return VP_EINVAL;
+        }
+        r.f_off = off;
+        r.acc_off = aoff;
+        r.rho_off = roff;
+        r.coupling = d.coupling;
+        r.rho_bg = d.rho_bg;
+        r.pois_order = d.pois_order == 2 || d.pois_order == 4 ? d.pois_order : 6;
+        off += ((r.NX * r.NV + 31) / 32) * 32;  // 128-byte aligned runs
+        aoff += r.dims * r.NX;
+        roff += r.NX;
+        e->runs.push_back(r);
+    }
+    e->pool_cells = off;
+    e->acc_total = aoff;
+    e->rho_total = roff;
+    for (RunDesc &r : e->runs) build_stages(r, e->P.W, e->P.R, e->P.xpt, slot);
+    e->nslots = slot;
+    build_items(e);
+    if (cudaMalloc(&e->d_acc, sizeof(double) * aoff) != cudaSuccess ||
+        cudaMalloc(&e->d_rho, sizeof(double) * roff) != cudaSuccess ||
+        cudaMalloc(&e->d_ctr, sizeof(unsigned) * (slot + 1)) != cudaSuccess ||
+        cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess) {
+        vp_ensemble_destroy(e);
+        return VP_ENOMEM;
+    }
+    cudaMemset(e->d_acc, 0, sizeof(double) * aoff);
+    cudaMemset(e->d_status, 0, sizeof(int));
+    int rc = upload_plan(e);
+    if (rc) {
+        vp_ensemble_destroy(e);
+        return rc;
+    }
+    e->smem = smem_need(e->runs);
+    cudaFuncSetAttribute(k_ensemble<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ensemble<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int per = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, order == 7 ? (const void *)k_ensemble<7>
+                                                                   : (const void *)k_ensemble<5>,
+                                                  kThreads, e->smem);
+    e->ctas_per_sm = per < 1 ? 1 : per;
+    *out = e;
+    return VP_OK;
+}
+
+void vp_ensemble_destroy(vp_ens *e) {
+    if (!e) return;
+    cudaStreamSynchronize(e->stream);
+    cudaFree(e->d_acc);
+    cudaFree(e->d_rho);
+    cudaFree(e->d_ctr);
+    cudaFree(e->d_status);
+    cudaFree(e->d_runs);
+    cudaFree(e->d_items_step);
+    cudaFree(e->d_items_field);
+    if (e->graph_valid) cudaGraphExecDestroy(e->graph);
+    delete e;
+}
+
+const char *vp_ensemble_last_error(const vp_ens *e) { return e ? e->err : "null ensemble"; }
+
+long long vp_ensemble_num_cells(const vp_ens *e) { return e ? e->pool_cells : 0; }
+
+int vp_ensemble_run_layout(const vp_ens *e, int run, long long *f_offset, long long *acc_offset) {
+    if (!e || run < 0 || run >= (int)e->runs.size()) return VP_EINVAL;
+    if (f_offset) *f_offset = e->runs[run].f_off;
+    if (acc_offset) *acc_offset = e->runs[run].acc_off;
+    return VP_OK;
+}
+
+int vp_ensemble_bind(vp_ens *e, float *pool_dev) {
+    if (!e || !pool_dev || (reinterpret_cast<uintptr_t>(pool_dev) & 127)) return VP_EINVAL;
+    e->pool = pool_dev;
+    if (e->graph_valid) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph_valid = 0;
+    }
+    return VP_OK;
+}
+
+int vp_ensemble_accel(const vp_ens *e, const double **accel_dev) {
+    if (!e || !accel_dev) return VP_EINVAL;
+    *accel_dev = e->d_acc;
+    return VP_OK;
+}
+
+int vp_ensemble_field(vp_ens *e) {
+    if (!e || !e->pool) return VP_EINVAL;
+    // the field list holds, per run, (density, Poisson) for 2D and (Poisson) for
+    // 1D; the wait of each item refers to stage - 1 of its run in the full
+    // plan, which the field pass has not run: run it stage by stage instead
+    std::vector<EnsItem> pass;
+    for (int phase = 0; phase < 2; ++phase) {
+        pass.clear();
+        for (const EnsItem &it : e->items_field) {
+            const StageDesc &s = e->runs[it.run].st[it.stage];
+            if ((phase == 0) == (s.kind == ST_MOMENT)) pass.push_back(it);
+        }
+        if (pass.empty()) continue;
+        if (cudaMemcpy(e->d_items_field, pass.data(), sizeof(EnsItem) * pass.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return ens_fail(e, VP_ECUDA, "field plan upload failed");
+        // mark every previous stage complete so the waits pass immediately
+        std::vector<unsigned> ctr(e->nslots + 1, 0u);
+        for (const RunDesc &r : e->runs)
+            for (int k = 0; k < r.nstage; ++k) ctr[1 + r.st[k].done_slot] = (unsigned)r.st[k].tiles;
+        for (const EnsItem &it : pass) ctr[1 + e->runs[it.run].st[it.stage].done_slot] = 0;
+        if (cudaMemcpyAsync(e->d_ctr, ctr.data(), sizeof(unsigned) * ctr.size(), cudaMemcpyHostToDevice,
+                            e->stream) != cudaSuccess)
+            return ens_fail(e, VP_ECUDA, "counter upload failed");
+        const int grid = e->ctas_per_sm * e->sm_count;
+        EnsParams P = e->P;
+        P.dt = 0.0;
+        if (e->P.order == 7)
+            k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
+                                                                 (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
+                                                                 P, e->d_status);
+        else
+            k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
+                                                                 (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
+                                                                 P, e->d_status);
+        e->launches++;
+        if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "field pass failed");
+    }
+    return VP_OK;
+}
+
+int vp_ensemble_init_run(vp_ens *e, int run, int kind, const double *params, int nparams) {
+    if (!e || !e->pool || run < 0 || run >= (int)e->runs.size()) return VP_EINVAL;
+    const RunDesc &r = e->runs[run];
+    if (kind != VP_IC_LANDAU && kind != VP_IC_TWOSTREAM) return ens_fail(e, VP_EINVAL, "unsupported initial condition");
+    vp_grid g{};
+    g.dx = g.dv = r.dims;
+    for (int k = 0; k < r.dims; ++k) {
+        g.nx[k] = r.nx[k];
+        g.nv[k] = r.nv[k];
+        g.xlo[k] = r.xlo[k];
+        g.xhi[k] = r.xlo[k] + r.hx[k] * r.nx[k];
+        g.vlo[k] = r.vlo[k];
+        g.vhi[k] = r.vlo[k] + r.hv[k] * r.nv[k];
+    }
+    g.precision = VP_F32;
+    const int rc = vp_launch_init_ptr(e->pool + r.f_off, g, kind, params, nparams, e->stream);
+    e->launches++;
+    return rc ? ens_fail(e, rc, "initial condition launch failed") : VP_OK;
+}
+
+int vp_ensemble_set_tiles(vp_ens *e, int W, int R, int ctas_per_sm) {
+    if (!e || W < 8 || W > 256 || R < 8 || R > 256 || ctas_per_sm < 0) return VP_EINVAL;
+    if (kThreads % W != 0 || kThreads % R != 0) return VP_EINVAL;
+    e->P.W = W;
+    e->P.R = R;
+    int slot = 0;
+    for (RunDesc &r : e->runs) build_stages(r, W, R, e->P.xpt, slot);
+    build_items(e);
+    int rc = upload_plan(e);
+    if (rc) return rc;
+    e->smem = smem_need(e->runs);
+    int per = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, e->P.order == 7 ? (const void *)k_ensemble<7>
+                                                                        : (const void *)k_ensemble<5>,
+                                                  kThreads, e->smem);
+    per = per < 1 ? 1 : per;
+    e->ctas_per_sm = ctas_per_sm > 0 && ctas_per_sm < per ? ctas_per_sm : per;
+    if (e->graph_valid) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph_valid = 0;
+    }
+    return VP_OK;
+}
+
+int vp_ensemble_get_tiles(const vp_ens *e, int *out3) {
+    if (!e || !out3) return VP_EINVAL;
+    out3[0] = e->P.W;
+    out3[1] = e->P.R;
+    out3[2] = e->ctas_per_sm;
+    return VP_OK;
+}
+
+int vp_ensemble_autotune(vp_ens *e) {
+    if (!e || !e->pool) return VP_EINVAL;
+    // time whole steps with dt = 0 (every shift is zero: f is unchanged)
+    const int Ws[3] = {32, 64, 128};
+    const int Rs[2] = {32, 64};
+    float best = 1e30f;
+    int bw = e->P.W, br = e->P.R, bc = 0;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int wi = 0; wi < 3; ++wi)
+        for (int ri = 0; ri < 2; ++ri) {
+            if (vp_ensemble_set_tiles(e, Ws[wi], Rs[ri], 0)) continue;
+            const int maxc = e->ctas_per_sm;
+            for (int cps = maxc; cps >= 1 && cps >= maxc - 2; --cps) {
+                e->ctas_per_sm = cps;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    cudaEventRecord(a, e->stream);
+                    int rc = launch_pass(e, e->d_items_step, (int)e->items_step.size(), 0.0);
+                    cudaEventRecord(b, e->stream);
+                    if (rc || cudaEventSynchronize(b) != cudaSuccess) {
+                        cudaEventDestroy(a);
+                        cudaEventDestroy(b);
+                        return ens_fail(e, VP_ECUDA, "autotune pass failed");
+                    }
+                    float m = 0.f;
+                    cudaEventElapsedTime(&m, a, b);
+                    ms = m < ms ? m : ms;
+                }
+                if (ms < best) {
+                    best = ms;
+                    bw = Ws[wi];
+                    br = Rs[ri];
+                    bc = cps;
+                }
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->tuned = 1;
+    return vp_ensemble_set_tiles(e, bw, br, bc);
+}
+
+int vp_ensemble_step(vp_ens *e, double dt, int nsteps) {
+    if (!e || !e->pool || nsteps < 0 || !std::isfinite(dt)) return VP_EINVAL;
+    const bool use_graph = e->stream != nullptr && e->stream != cudaStreamLegacy;
+    if (use_graph && !(e->graph_valid && e->graph_dt == dt)) {
+        if (e->graph_valid) {
+            cudaGraphExecDestroy(e->graph);
+            e->graph_valid = 0;
+        }
+        if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return ens_fail(e, VP_ECUDA, "capture failed");
+        const long long before = e->launches;
+        int rc = launch_pass(e, e->d_items_step, (int)e->items_step.size(), dt);
+        cudaGraph_t g;
+        const cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+        e->launches = before;
+        if (rc) return rc;
+        if (ce != cudaSuccess) return ens_fail(e, VP_ECUDA, "capture failed");
+        const cudaError_t ie = cudaGraphInstantiate(&e->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return ens_fail(e, VP_ECUDA, "graph instantiate failed");
+        e->graph_valid = 1;
+        e->graph_dt = dt;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        if (use_graph) {
+            if (cudaGraphLaunch(e->graph, e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "graph launch failed");
+            e->launches++;
+        } else {
+            int rc = launch_pass(e, e->d_items_step, (int)e->items_step.size(), dt);
+            if (rc) return rc;
+        }
+    }
+    return VP_OK;
+}
+
+int vp_ensemble_sync(vp_ens *e) {
+    if (!e) return VP_EINVAL;
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "stream failed");
+    int st = 0;
+    cudaMemcpy(&st, e->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (st) {
+        cudaMemset(e->d_status, 0, sizeof(int));
+        return ens_fail(e, VP_ETIMEOUT, "a bounded wait in the ensemble kernel gave up");
+    }
+    return VP_OK;
+}
+
+long long vp_ensemble_launch_count(const vp_ens *e) { return e ? e->launches : 0; }
+
+}  // extern "C"

@@ -631,12 +631,12 @@ int vp_launch_diag(vp_ctx *c, int mode, double *out_dev) {
     return VP_OK;
 }
 
-int vp_launch_init(vp_ctx *c, int kind, const double *p, int np) {
-    const vp_grid &g = c->g;
+int vp_launch_init_ptr(void *f, const vp_grid &g, int kind, const double *p, int np, cudaStream_t st) {
     IcArgs a{};
     a.kind = kind;
     a.dims = g.dx;
-    a.NV = c->NV;
+    a.NV = 1;
+    long long NX = 1;
     for (int d = 0; d < g.dx; ++d) {
         a.nx[d] = g.nx[d];
         a.nv[d] = g.nv[d];
@@ -645,14 +645,22 @@ int vp_launch_init(vp_ctx *c, int kind, const double *p, int np) {
         a.hx[d] = (g.xhi[d] - g.xlo[d]) / g.nx[d];
         a.hv[d] = (g.vhi[d] - g.vlo[d]) / g.nv[d];
         a.xc[d] = 0.5 * (g.xlo[d] + g.xhi[d]);
+        a.NV *= g.nv[d];
+        NX *= g.nx[d];
     }
     for (int i = 0; i < np && i < 8; ++i) a.p[i] = p[i];
+    const long long ncell = NX * a.NV;
     if (g.precision == VP_F32)
-        k_init<float><<<nblk(c->ncell, kBlock), kBlock, 0, c->stream>>>(static_cast<float *>(c->f), c->ncell, a);
+        k_init<float><<<nblk(ncell, kBlock), kBlock, 0, st>>>(static_cast<float *>(f), ncell, a);
     else
-        k_init<double><<<nblk(c->ncell, kBlock), kBlock, 0, c->stream>>>(static_cast<double *>(c->f), c->ncell, a);
+        k_init<double><<<nblk(ncell, kBlock), kBlock, 0, st>>>(static_cast<double *>(f), ncell, a);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}
+
+int vp_launch_init(vp_ctx *c, int kind, const double *p, int np) {
+    const int rc = vp_launch_init_ptr(c->f, c->g, kind, p, np, c->stream);
     c->launches++;
-    VP_CUDA_TRY(c, cudaGetLastError());
+    if (rc) return vp_fail(c, rc, "initial condition launch failed");
     return VP_OK;
 }
 

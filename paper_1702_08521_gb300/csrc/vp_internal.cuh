@@ -109,4 +109,8 @@ int vp_launch_poisson(vp_ctx *c, const double *rho, double *phi, double *acc);
 int vp_launch_diag(vp_ctx *c, int mode, double *out_dev);
 int vp_launch_init(vp_ctx *c, int kind, const double *p, int np);
 int vp_field_setup(vp_ctx *c);          // Green function tables (at create)
+// CSL weight polynomials of the given order (5 or 7), from the definition of the SL flux
+WPoly vp_csl_weight_polys(int order);
+// analytic initial condition into any f array of grid g (precision from g)
+int vp_launch_init_ptr(void *f, const vp_grid &g, int kind, const double *p, int np, cudaStream_t st);
 int vp_sweep_setup(vp_ctx *c);          // kernel attributes (at create)

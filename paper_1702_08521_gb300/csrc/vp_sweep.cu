@@ -24,209 +24,58 @@
 #include <cmath>
 
 #include "vp_internal.cuh"
+#include "vp_sweep_core.cuh"
 #include "vp_tma.cuh"
 
 namespace {
 
-// ---- limiter arithmetic (Appendix A and Sec. 2.1.1) -------------------------
+using vp_core::line_class;
+using vp_core::walk;
 
+// running-pointer store of one line's new values (element stride `step`
+// between consecutive cells of the walk)
 template <typename T>
-__device__ __forceinline__ T mm2(T a, T b) {
-    // minmod: smallest magnitude if both share a sign, else 0
-    if (a > T(0) && b > T(0)) return a < b ? a : b;
-    if (a < T(0) && b < T(0)) return a > b ? a : b;
-    return T(0);
-}
-
-template <typename T>
-__device__ __forceinline__ T mm4(T a, T b, T c, T d) {
-    if (a > T(0) && b > T(0) && c > T(0) && d > T(0)) return fmin(fmin(a, b), fmin(c, d));
-    if (a < T(0) && b < T(0) && c < T(0) && d < T(0)) return fmax(fmax(a, b), fmax(c, d));
-    return T(0);
-}
-
-template <typename T>
-__device__ __forceinline__ T mid3(T a, T b, T c) {
-    // middle value of three
-    return fmax(fmin(a, b), fmin(fmax(a, b), c));
-}
-
-// MP bound of the interface value phi between cells u0 (upwind) and u1,
-// neighbours um2, um1 upwind and u2 downwind.
-template <typename T>
-__device__ __forceinline__ T mp_bound(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
-    const T back = u0 - um1;
-    const T fstar = u0 + mm2(u1 - u0, alpha * back);
-    const T a = phi - u0, b = phi - fstar;
-    if ((a > T(0) && b < T(0)) || (a < T(0) && b > T(0))) return phi;  // strictly between
-    if (um1 == u0 && u0 == u1) return u0;  // all bounds collapse onto u0
-    const T dm = um2 + u0 - T(2) * um1;   // curvature at the upwind neighbour
-    const T dc = um1 + u1 - T(2) * u0;    // at the upwind cell
-    const T dp = u0 + u2 - T(2) * u1;     // at the downwind cell
-    const T m4p = mm4(T(4) * dc - dp, T(4) * dp - dc, dc, dp);
-    const T m4m = mm4(T(4) * dm - dc, T(4) * dc - dm, dm, dc);
-    const T ful = u0 + alpha * back;
-    const T fmd = T(0.5) * (u0 + u1) - T(0.5) * m4p;
-    const T flc = u0 + T(0.5) * back + (T(4) / T(3)) * m4m;
-    const T lo = fmax(fmin(fmin(u0, u1), fmd), fmin(fmin(u0, ful), flc));
-    const T hi = fmin(fmax(fmax(u0, u1), fmd), fmax(fmax(u0, ful), flc));
-    return mid3(phi, lo, hi);
-}
-
-template <typename T>
-struct Eps;
-template <>
-struct Eps<float> {
-    static constexpr float safety = 1.0f - 8.0f * 5.9604644775390625e-08f;  // 1 - 8 * 2^-24
-};
-template <>
-struct Eps<double> {
-    static constexpr double safety = 1.0 - 8.0 * 1.1102230246251565e-16;  // 1 - 8 * 2^-53
+struct PtrStore {
+    T *p;
+    long long step;
+    __device__ __forceinline__ void operator()(int, T v) {
+        *p = v;
+        p += step;
+    }
 };
 
-// Positivity blend: keep both halves f_i - 2 nu phi >= 0 (outflow side) and
-// f_{i+1} + 2 nu phi >= 0 (inflow side of the downwind cell).
-template <typename T>
-__device__ __forceinline__ T pp_blend(T phi, T u0, T u1, T nu) {
-    const T two_nu = T(2) * nu;
-    const T up = u0 - two_nu * phi;
-    const T um = u1 + two_nu * phi;
-    if (!(up < T(0)) && !(um < T(0))) return phi;
-    T th = T(1);
-    if (up < T(0)) {
-        const T base = u0 - two_nu * u0;
-        const T den = base - up;
-        th = den > T(0) ? base / den : T(0);
-    }
-    if (um < T(0)) {
-        const T base = u1 + two_nu * u0;
-        const T den = base - um;
-        const T t2 = den > T(0) ? base / den : T(0);
-        th = t2 < th ? t2 : th;
-    }
-    th *= Eps<T>::safety;
-    th = th < T(0) ? T(0) : (th > T(1) ? T(1) : th);
-    return th * phi + (T(1) - th) * u0;
-}
-
-template <typename T, int ORDER>
-__device__ __forceinline__ T iface(const T *u, const LineShift<T> &sh, T alpha, int mp, int pp) {
-    // u points at the upwind cell (u[0]); u[-3..3] valid
-    T phi;
-    if (ORDER == 7) {
-        phi = sh.w[0] * u[-3];
-        phi = fma(sh.w[1], u[-2], phi);
-        phi = fma(sh.w[2], u[-1], phi);
-        phi = fma(sh.w[3], u[0], phi);
-        phi = fma(sh.w[4], u[1], phi);
-        phi = fma(sh.w[5], u[2], phi);
-        phi = fma(sh.w[6], u[3], phi);
-    } else {
-        phi = sh.w[1] * u[-2];
-        phi = fma(sh.w[2], u[-1], phi);
-        phi = fma(sh.w[3], u[0], phi);
-        phi = fma(sh.w[4], u[1], phi);
-        phi = fma(sh.w[5], u[2], phi);
-    }
-    if (mp) phi = mp_bound(phi, u[-2], u[-1], u[0], u[1], u[2], alpha);
-    if (pp) phi = pp_blend(phi, u[0], u[1], sh.nu);
-    return phi;
-}
-
-// Advance cells [r0, r1) of one staged line.  sm: line in shared memory with
-// element stride ss; out: the same line in global memory, element stride gs.
-template <typename T, int ORDER>
-__device__ __forceinline__ void sweep_segment(const T *__restrict__ sm, int ss, int L, int periodic,
-                                              const LineShift<T> &sh, int r0, int r1,
-                                              T *__restrict__ out, long long gs, T alpha, int mp,
-                                              int pp) {
-    if (r0 >= r1) return;
-    const int sg = sh.sigma;
-    int n = sh.n;
-    if (periodic) {
-        n %= L;
-        if (n < 0) n += L;
-    }
-    const T nu = sh.nu;
-    // walk in the upwind-to-downwind direction
-    int i = sg > 0 ? r0 : r1 - 1;
-    const int cnt = r1 - r0;
-    // window u[k+4] = value of the shifted line at cell i + sg*k, k = -4..3
-    T win[8];
-    int p = i - n - 4 * sg;  // source position of u[-4]
-    if (periodic) {
-        p %= L;
-        if (p < 0) p += L;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        T v;
-        if (periodic) {
-            v = sm[p * ss];
-        } else {
-            v = (p >= 0 && p < L) ? sm[p * ss] : T(0);
-        }
-        win[k] = v;
-        p += sg;
-        if (periodic) {
-            if (p >= L) p -= L;
-            if (p < 0) p += L;
-        }
-    }
-    // p now points at the source of u[4] (the next value to enter)
-    T fin = iface<T, ORDER>(&win[3], sh, alpha, mp, pp);  // upwind cell i - sg
-    for (int t = 0; t < cnt; ++t) {
-        const T fout = iface<T, ORDER>(&win[4], sh, alpha, mp, pp);
-        out[(long long)i * gs] = win[4] - nu * (fout - fin);
-        fin = fout;
-        i += sg;
-        T v;
-        if (periodic) {
-            v = sm[p * ss];
-        } else {
-            v = (p >= 0 && p < L) ? sm[p * ss] : T(0);
-        }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) win[k] = win[k + 1];
-        win[7] = v;
-        p += sg;
-        if (periodic) {
-            if (p >= L) p -= L;
-            if (p < 0) p += L;
-        }
-    }
-}
-
-__device__ __forceinline__ long long line_class(const SweepGeo &g, long long o, long long c) {
-    return g.cls_from_inner ? (c / g.cdiv) % g.cmod : o / g.cdiv;
-}
-
-template <typename T, int ORDER>
+// staged-load strided sweep: tile = W columns x the whole line, rows 1..L of
+// a [(L + 2)][W] shared tile (rows 0 and L + 1 are the zero ghosts)
+template <typename T, int ORDER, bool PERIODIC, bool FULL>
 __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
                                                     const LineShift<T> *__restrict__ tab,
                                                     SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
     const int W = geo.W, L = geo.L;
-    const long long tpo = (geo.inner + W - 1) / W;
-    const long long o = blockIdx.x / tpo;
-    const long long c0 = (blockIdx.x % tpo) * W;
+    const unsigned tpo = (unsigned)((geo.inner + W - 1) / W);
+    const unsigned o = blockIdx.x / tpo;
+    const unsigned c0 = (blockIdx.x - o * tpo) * (unsigned)W;
     const int wc = (int)((geo.inner - c0) < W ? (geo.inner - c0) : W);
-    T *base = f + o * (long long)L * geo.inner + c0;
-    // stage the tile [L][W]
+    T *base = f + (long long)o * L * geo.inner + c0;
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        sm[c] = T(0);
+        sm[(L + 1) * W + c] = T(0);
+    }
     constexpr int VEC = 16 / sizeof(T);
-    const bool vec = (wc == W) && (geo.inner % VEC == 0) && (W % VEC == 0);
-    if (vec) {
-        const int wv = W / VEC;
-        for (int e = threadIdx.x; e < L * wv; e += blockDim.x) {
-            const int r = e / wv, cv = e - r * wv;
-            const float4 x = *reinterpret_cast<const float4 *>(base + (long long)r * geo.inner + cv * VEC);
-            *reinterpret_cast<float4 *>(sm + r * W + cv * VEC) = x;
-        }
+    const int wv = W / VEC;
+    if (wc == W && geo.inner % VEC == 0 && W % VEC == 0 && blockDim.x % wv == 0) {
+        const int cv = threadIdx.x % wv;
+        const int rstep = blockDim.x / wv;
+        const T *src = base + cv * VEC;
+        T *dst = sm + W + cv * VEC;
+        for (int r = threadIdx.x / wv; r < L; r += rstep)
+            *reinterpret_cast<float4 *>(dst + r * W) =
+                *reinterpret_cast<const float4 *>(src + (long long)r * geo.inner);
     } else {
         for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
             const int r = e / W, cc = e - r * W;
-            sm[e] = cc < wc ? base[(long long)r * geo.inner + cc] : T(0);
+            sm[W + e] = cc < wc ? base[(long long)r * geo.inner + cc] : T(0);
         }
     }
     __syncthreads();
@@ -234,76 +83,116 @@ __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
     const int seg = threadIdx.x / W;
     if (cc < wc && seg < geo.nseg) {
         const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
-        const int r0 = (int)((long long)seg * L / geo.nseg);
-        const int r1 = (int)((long long)(seg + 1) * L / geo.nseg);
-        sweep_segment<T, ORDER>(sm + cc, W, L, geo.periodic, sh, r0, r1, base + cc, geo.inner,
-                                (T)lp.alpha, lp.mp, lp.pp);
+        const int r0 = seg * L / geo.nseg;
+        const int r1 = (seg + 1) * L / geo.nseg;
+        const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+        PtrStore<T> st{base + cc + (long long)i0 * geo.inner, (long long)sh.sigma * geo.inner};
+        walk<T, ORDER, PERIODIC, FULL>(sm + (PERIODIC ? W : 0) + cc, W, L, sh, r0, r1, (T)lp.alpha, lp.mp,
+                                 lp.pp, st);
     }
 }
 
-template <typename T, int ORDER>
+// contiguous-axis sweep: R lines per CTA.  Input rows at odd pitch P with a
+// zero ghost on each side, results to a second shared tile (odd pitch Q), then
+// copied out with 16-byte coalesced stores.
+template <typename T, int ORDER, bool PERIODIC, bool FULL>
 __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
                                                     const LineShift<T> *__restrict__ tab,
                                                     SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
     const int L = geo.L, R = geo.R;
-    const int P = L | 1;  // odd pitch: 32 lines -> 32 banks
+    const int P = (L + 2) | 1;
+    const int Q = L | 1;
+    T *in = reinterpret_cast<T *>(smraw);
+    T *out = in + R * P;
     const long long l0 = (long long)blockIdx.x * R;
     const int nl = (int)((geo.outer - l0) < R ? (geo.outer - l0) : R);
     T *base = f + l0 * L;
     const int tot = nl * L;
+    for (int r = threadIdx.x; r < nl; r += blockDim.x) {
+        in[r * P] = T(0);
+        in[r * P + L + 1] = T(0);
+    }
     constexpr int VEC = 16 / sizeof(T);
-    if ((L % VEC) == 0) {
+    const bool vec = (L % VEC) == 0;
+    if (vec) {
         for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
             const float4 x = *reinterpret_cast<const float4 *>(base + e);
             const T *xv = reinterpret_cast<const T *>(&x);
             const int r = e / L, pos = e - r * L;
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) sm[r * P + pos + k] = xv[k];
+            for (int k = 0; k < VEC; ++k) in[r * P + 1 + pos + k] = xv[k];
         }
     } else {
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             const int r = e / L, pos = e - r * L;
-            sm[r * P + pos] = base[e];
+            in[r * P + 1 + pos] = base[e];
         }
     }
     __syncthreads();
     const int line = threadIdx.x % R;
     const int seg = threadIdx.x / R;
     if (line < nl && seg < geo.nseg) {
-        const LineShift<T> sh = tab[line_class(geo, l0 + line, 0)];
-        const int r0 = (int)((long long)seg * L / geo.nseg);
-        const int r1 = (int)((long long)(seg + 1) * L / geo.nseg);
-        sweep_segment<T, ORDER>(sm + line * P, 1, L, geo.periodic, sh, r0, r1,
-                                base + (long long)line * L, 1, (T)lp.alpha, lp.mp, lp.pp);
+        const LineShift<T> sh = tab[line_class(geo, (unsigned)(l0 + line), 0u)];
+        const int r0 = seg * L / geo.nseg;
+        const int r1 = (seg + 1) * L / geo.nseg;
+        const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+        PtrStore<T> st{out + line * Q + i0, (long long)sh.sigma};
+        walk<T, ORDER, PERIODIC, FULL>(in + line * P + (PERIODIC ? 1 : 0), 1, L, sh, r0, r1, (T)lp.alpha,
+                                 lp.mp, lp.pp, st);
+    }
+    __syncthreads();
+    if (vec) {
+        for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
+            const int r = e / L, pos = e - r * L;
+            float4 x;
+            T *xv = reinterpret_cast<T *>(&x);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) xv[k] = out[r * Q + pos + k];
+            *reinterpret_cast<float4 *>(base + e) = x;
+        }
+    } else {
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int r = e / L, pos = e - r * L;
+            base[e] = out[r * Q + pos];
+        }
     }
 }
 
-template <typename T, int ORDER>
+// TMA-fed persistent strided sweep (two input and two output stages)
+template <typename T, int ORDER, bool PERIODIC, bool FULL>
 __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ CUtensorMap tmap,
                                                         const LineShift<T> *__restrict__ tab,
                                                         SweepGeo geo, LimParams lp,
                                                         int *__restrict__ status) {
-    extern __shared__ __align__(128) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw_tma[];
+    unsigned char *smraw = smraw_tma;
     __shared__ __align__(8) uint64_t bar[2];
     const int W = geo.W, L = geo.L;
-    const int tile = L * W;
+    const int itile = (L + 2) * W;  // input stage: zero row, L rows, zero row
+    const int otile = L * W;
     // TMA tensor copies need 128-byte aligned shared-memory buffers: align
     // the dynamic region explicitly (the launch reserves 128 spare bytes)
-    const uint32_t base = vp_tma::saddr(smraw);
-    const uint32_t pad = (128u - (base & 127u)) & 127u;
-    T *in_buf = reinterpret_cast<T *>(smraw + pad);  // [2][L][W]
-    T *out_buf = in_buf + 2 * tile;                   // [2][L][W]
-    const long long tpo = (geo.inner + W - 1) / W;
-    const long long ntiles = geo.outer * tpo;
-    const uint32_t bytes = (uint32_t)(tile * sizeof(T));
+    const uint32_t sbase = vp_tma::saddr(smraw);
+    const uint32_t pad = (128u - (sbase & 127u)) & 127u;
+    T *in_buf = reinterpret_cast<T *>(smraw + pad);  // [2][L + 2][W]
+    T *out_buf = in_buf + 2 * itile;                  // [2][L][W]
+    const unsigned tpo = (unsigned)((geo.inner + W - 1) / W);
+    const unsigned ntiles = (unsigned)geo.outer * tpo;
+    const uint32_t bytes = (uint32_t)(otile * sizeof(T));
     // self-check of every alignment the copies rely on; on failure report and
     // leave before issuing any copy
-    if (((vp_tma::saddr(in_buf) | vp_tma::saddr(out_buf) | bytes) & 127u) != 0 ||
-        ((W * sizeof(T)) & 15u) != 0) {
+    if (((vp_tma::saddr(in_buf + W) | vp_tma::saddr(in_buf + itile + W) | vp_tma::saddr(out_buf) |
+          vp_tma::saddr(out_buf + otile)) & 127u) != 0 ||
+        ((W * sizeof(T)) & 127u) != 0) {
         if (threadIdx.x == 0) atomicExch(status, VP_EINVAL);
         return;
+    }
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        in_buf[c] = T(0);
+        in_buf[(L + 1) * W + c] = T(0);
+        in_buf[itile + c] = T(0);
+        in_buf[itile + (L + 1) * W + c] = T(0);
     }
     if (threadIdx.x == 0) {
         vp_tma::mbar_init(&bar[0], 1);
@@ -313,22 +202,23 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
-            const long long t = blockIdx.x + (long long)s * gridDim.x;
+            const unsigned t = blockIdx.x + (unsigned)s * gridDim.x;
             if (t < ntiles) {
                 vp_tma::mbar_expect_tx(&bar[s], bytes);
-                vp_tma::load_3d(in_buf + s * tile, &tmap, &bar[s], (int)((t % tpo) * W), 0, (int)(t / tpo));
+                vp_tma::load_3d(in_buf + s * itile + W, &tmap, &bar[s], (int)((t % tpo) * W), 0,
+                                (int)(t / tpo));
             }
         }
     }
     const int cc = threadIdx.x % W;
     const int seg = threadIdx.x / W;
-    const int r0 = (int)((long long)seg * L / geo.nseg);
-    const int r1 = (int)((long long)(seg + 1) * L / geo.nseg);
+    const int r0 = seg * L / geo.nseg;
+    const int r1 = (seg + 1) * L / geo.nseg;
     int k = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int s = k & 1;
-        T *in = in_buf + s * tile;
-        T *out = out_buf + s * tile;
+        T *in = in_buf + s * itile;
+        T *out = out_buf + s * otile;
         if (!vp_tma::mbar_wait(&bar[s], (uint32_t)((k >> 1) & 1))) {
             // the tile never arrived: report, drain our stores, leave
             if (threadIdx.x == 0) {
@@ -338,23 +228,25 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
             }
             return;
         }
-        const long long o = t / tpo;
-        const long long c0 = (t % tpo) * W;
+        const unsigned o = t / tpo;
+        const unsigned c0 = (t - o * tpo) * (unsigned)W;
         const int wc = (int)((geo.inner - c0) < W ? (geo.inner - c0) : W);
         if (cc < wc && seg < geo.nseg) {
             const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
-            sweep_segment<T, ORDER>(in + cc, W, L, geo.periodic, sh, r0, r1, out + cc, W,
-                                    (T)lp.alpha, lp.mp, lp.pp);
+            const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+            PtrStore<T> st{out + cc + i0 * W, (long long)sh.sigma * W};
+            walk<T, ORDER, PERIODIC, FULL>(in + (PERIODIC ? W : 0) + cc, W, L, sh, r0, r1, (T)lp.alpha,
+                                     lp.mp, lp.pp, st);
         }
         vp_tma::fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             vp_tma::store_3d(&tmap, out, (int)c0, 0, (int)o);
             vp_tma::commit();
-            const long long tn = t + 2LL * gridDim.x;
+            const unsigned tn = t + 2u * gridDim.x;
             if (tn < ntiles) {
                 vp_tma::mbar_expect_tx(&bar[s], bytes);
-                vp_tma::load_3d(in, &tmap, &bar[s], (int)((tn % tpo) * W), 0, (int)(tn / tpo));
+                vp_tma::load_3d(in + W, &tmap, &bar[s], (int)((tn % tpo) * W), 0, (int)(tn / tpo));
             }
             vp_tma::wait_read<1>();  // the other output tile is free again
         }
@@ -372,38 +264,50 @@ __global__ void k_shift_table(LineShift<T> *__restrict__ tab, int nclass, int ki
                               WPoly wp) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nclass) return;
-    double speed;
-    if (kick) {
-        speed = accel[c];
-    } else {
-        speed = __dadd_rn(lo, __dmul_rn((double)c + 0.5, dvel));
-    }
-    const double s = __ddiv_rn(__dmul_rn(speed, dt), h);
-    const double n = round(s);
-    const double z = __dadd_rn(s, -n);
-    const double nu = fabs(z);
-    LineShift<T> sh;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        double acc = 0.0;
-        for (int j = wp.nterm - 1; j >= 0; --j) acc = fma(acc, nu, wp.c[j][k]);
-        sh.w[k] = (T)acc;
-    }
-    sh.nu = (T)nu;
-    sh.n = (int)n;
-    sh.sigma = z < 0.0 ? -1 : 1;
-    tab[c] = sh;
+    const double speed = kick ? accel[c] : vp_core::cell_centre(lo, dvel, c);
+    tab[c] = vp_core::make_shift<T>(speed, dt, h, wp);
+}
+
+template <typename T, int ORDER, bool PER, bool FULL>
+void set_attrs_one() {
+    cudaFuncSetAttribute(k_sweep_cols<T, ORDER, PER, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(k_sweep_rows<T, ORDER, PER, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(k_sweep_cols_tma<T, ORDER, PER, FULL>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 template <typename T, int ORDER>
 void set_attrs() {
-    cudaFuncSetAttribute(k_sweep_cols<T, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(k_sweep_rows<T, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(k_sweep_cols_tma<T, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+    set_attrs_one<T, ORDER, true, true>();
+    set_attrs_one<T, ORDER, false, true>();
+    set_attrs_one<T, ORDER, true, false>();
+    set_attrs_one<T, ORDER, false, false>();
 }
+
+// compile-time dispatch on the scheme order, the line's periodicity and
+// whether both limiters are on
+#define VP_DISPATCH(ORDER_, PER_, FULL_, CALL)                         \
+    do {                                                               \
+        if ((ORDER_) == 7) {                                           \
+            if (PER_) {                                                \
+                if (FULL_) { CALL(7, true, true); }                    \
+                else { CALL(7, true, false); }                         \
+            } else {                                                   \
+                if (FULL_) { CALL(7, false, true); }                   \
+                else { CALL(7, false, false); }                        \
+            }                                                          \
+        } else {                                                       \
+            if (PER_) {                                                \
+                if (FULL_) { CALL(5, true, true); }                    \
+                else { CALL(5, true, false); }                         \
+            } else {                                                   \
+                if (FULL_) { CALL(5, false, true); }                   \
+                else { CALL(5, false, false); }                        \
+            }                                                          \
+        }                                                              \
+    } while (0)
 
 // geometry of the sweep along axis `dim` (kick: velocity axis, else spatial)
 SweepGeo make_geo(const vp_ctx *c, int kick, int dim) {
@@ -453,12 +357,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 template <typename T>
+size_t tma_smem(int L, int W) {
+    return (size_t)(2 * (L + 2) * W + 2 * L * W) * sizeof(T) + 128;
+}
+
+template <typename T>
 bool tma_eligible(const vp_ctx *c, const SweepGeo &geo, int W) {
     constexpr int VEC = 16 / sizeof(T);
     return geo.inner > 1 && geo.inner % VEC == 0 && W % VEC == 0 && geo.inner < (1LL << 31) &&
            geo.outer < (1LL << 31) && geo.L <= 256 && W <= 256 &&
-           ((size_t)geo.L * W * sizeof(T)) % 128 == 0 &&
-           (size_t)4 * geo.L * W * sizeof(T) + 128 <= 200 * 1024 && tensor_map_encoder() != nullptr &&
+           (W * sizeof(T)) % 128 == 0 && tma_smem<T>(geo.L, W) <= 200 * 1024 &&
+           tensor_map_encoder() != nullptr &&
            (reinterpret_cast<uintptr_t>(c->f) & 15) == 0;
 }
 
@@ -474,7 +383,10 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     geo.nseg = tu.nseg;
     const int threads = ((W * tu.nseg + 31) / 32) * 32;
     const long long tiles = geo.outer * ((geo.inner + W - 1) / W);
-    const bool seven = c->g.order == 7;
+    if (tiles >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
+    const int order = c->g.order;
+    const bool per = geo.periodic != 0;
+    const bool full = c->g.mp && c->g.pp;
     if (tu.impl == 2 && tma_eligible<T>(c, geo, W)) {
         CUtensorMap map;
         const cuuint64_t dims[3] = {(cuuint64_t)geo.inner, (cuuint64_t)L, (cuuint64_t)geo.outer};
@@ -488,32 +400,35 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
                                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return vp_fail(c, VP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-        const size_t smem = (size_t)4 * L * W * sizeof(T) + 128;
+        const size_t smem = tma_smem<T>(L, W);
         int per_sm = tu.ctas_per_sm;
         if (per_sm <= 0) {
-            if (seven)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_cols_tma<T, 7>, threads, smem);
-            else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_cols_tma<T, 5>, threads, smem);
+#define VP_OCC(O, P, F) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_cols_tma<T, O, P, F>, threads, smem)
+            VP_DISPATCH(order, per, full, VP_OCC);
+#undef VP_OCC
             per_sm = per_sm < 1 ? 1 : per_sm;
         }
         long long grid = (long long)per_sm * c->sm_count;
         grid = grid > tiles ? tiles : grid;
-        if (seven)
-            k_sweep_cols_tma<T, 7><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status);
-        else
-            k_sweep_cols_tma<T, 5><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status);
+#define VP_LAUNCH(O, P, F) \
+    k_sweep_cols_tma<T, O, P, F><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status)
+        VP_DISPATCH(order, per, full, VP_LAUNCH);
+#undef VP_LAUNCH
     } else {
-        const size_t smem = (size_t)L * W * sizeof(T);
+        const size_t smem = (size_t)(L + 2) * W * sizeof(T);
         if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
-        if (seven)
-            k_sweep_cols<T, 7><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
-        else
-            k_sweep_cols<T, 5><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+#define VP_LAUNCH(O, P, F) k_sweep_cols<T, O, P, F><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp)
+        VP_DISPATCH(order, per, full, VP_LAUNCH);
+#undef VP_LAUNCH
     }
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
+}
+
+template <typename T>
+size_t rows_smem(int L, int R) {
+    return (size_t)R * (((L + 2) | 1) + (L | 1)) * sizeof(T);
 }
 
 template <typename T>
@@ -527,13 +442,15 @@ int launch_rows(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     geo.R = R;
     geo.nseg = tu.nseg;
     const long long blocks = (geo.outer + R - 1) / R;
-    const size_t smem = (size_t)R * (L | 1) * sizeof(T);
+    if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
+    const size_t smem = rows_smem<T>(L, R);
     if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
     const int threads = ((R * tu.nseg + 31) / 32) * 32;
-    if (c->g.order == 7)
-        k_sweep_rows<T, 7><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
-    else
-        k_sweep_rows<T, 5><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
+    const bool per = geo.periodic != 0;
+    const bool full = c->g.mp && c->g.pp;
+#define VP_LAUNCH(O, P, F) k_sweep_rows<T, O, P, F><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp)
+    VP_DISPATCH(c->g.order, per, full, VP_LAUNCH);
+#undef VP_LAUNCH
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
@@ -601,7 +518,7 @@ int tune_t(vp_ctx *c, int kick, int dim) {
                     if (th < 64 || th > 512 || nseg > geo.L) continue;
                     const int Weff = geo.inner < W ? (int)geo.inner : W;
                     if (impls[ii] == 2 && !tma_eligible<T>(c, geo, Weff)) continue;
-                    if (impls[ii] == 1 && (size_t)geo.L * W * sizeof(T) > 200 * 1024) continue;
+                    if (impls[ii] == 1 && (size_t)(geo.L + 2) * W * sizeof(T) > 200 * 1024) continue;
                     if (nc < 32) cand[nc++] = SweepTune{1, impls[ii], W, nseg, 0};
                 }
         }
@@ -610,7 +527,7 @@ int tune_t(vp_ctx *c, int kick, int dim) {
             for (int nseg = 1; nseg <= 8; nseg *= 2) {
                 const int th = R * nseg;
                 if (th < 64 || th > 512 || nseg > geo.L) continue;
-                if ((size_t)R * (geo.L | 1) * sizeof(T) > 200 * 1024) continue;
+                if (rows_smem<T>(geo.L, R) > 200 * 1024) continue;
                 if (nc < 32) cand[nc++] = SweepTune{1, 1, R, nseg, 0};
             }
     }

@@ -1,0 +1,272 @@
+// vp_sweep_core.cuh -- per-interface arithmetic of the SL-MPP5/7 sweep and
+// the line walker shared by every sweep kernel (strided, contiguous, TMA,
+// ensemble).
+#pragma once
+
+#include "vp_internal.cuh"
+
+namespace vp_core {
+
+// ---- limiter arithmetic (Appendix A and Sec. 2.1.1) -------------------------
+
+// minmod(a, b): the argument of smaller magnitude if both share a sign, else 0
+// (written as a clamp of a into [min(0, b), max(0, b)], which returns a, b or 0)
+template <typename T>
+__device__ __forceinline__ T mm2(T a, T b) {
+    return fmin(fmax(a, fmin(T(0), b)), fmax(T(0), b));
+}
+
+// minmod of four: min if all > 0, max if all < 0, else 0 (= max(min,0) + min(max,0))
+template <typename T>
+__device__ __forceinline__ T mm4(T a, T b, T c, T d) {
+    const T mn = fmin(fmin(a, b), fmin(c, d));
+    const T mx = fmax(fmax(a, b), fmax(c, d));
+    return fmax(mn, T(0)) + fmin(mx, T(0));
+}
+
+// middle value of three
+template <typename T>
+__device__ __forceinline__ T mid3(T a, T b, T c) {
+    return fmax(fmin(a, b), fmin(fmax(a, b), c));
+}
+
+// Steps 4-7 of the MP constraint (taken only when step 3 rejects phi).
+template <typename T>
+__device__ __noinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
+    if (um1 == u0 && u0 == u1) return u0;  // every bound collapses onto u0
+    const T back = u0 - um1;
+    const T dm = um2 + u0 - T(2) * um1;  // curvature at the upwind neighbour
+    const T dc = um1 + u1 - T(2) * u0;   // at the upwind cell
+    const T dp = u0 + u2 - T(2) * u1;    // at the downwind cell
+    const T m4p = mm4(T(4) * dc - dp, T(4) * dp - dc, dc, dp);
+    const T m4m = mm4(T(4) * dm - dc, T(4) * dc - dm, dm, dc);
+    const T ful = u0 + alpha * back;
+    const T fmd = T(0.5) * (u0 + u1) - T(0.5) * m4p;
+    const T flc = u0 + T(0.5) * back + (T(4) / T(3)) * m4m;
+    const T lo = fmax(fmin(fmin(u0, u1), fmd), fmin(fmin(u0, ful), flc));
+    const T hi = fmin(fmax(fmax(u0, u1), fmd), fmax(fmax(u0, ful), flc));
+    return mid3(phi, lo, hi);
+}
+
+// MP constraint of phi at the interface between u0 (upwind) and u1.
+template <typename T>
+__device__ __forceinline__ T mp_limit(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
+    const T fstar = u0 + mm2(u1 - u0, alpha * (u0 - um1));
+    const T a = phi - u0, b = fstar - phi;  // accept iff phi lies strictly between u0 and f*
+    if (fmin(a, b) > T(0) || fmax(a, b) < T(0)) return phi;
+    return mp_bounds(phi, um2, um1, u0, u1, u2, alpha);
+}
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+    static constexpr float safety = 1.0f - 8.0f * 5.9604644775390625e-08f;  // 1 - 8 * 2^-24
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+};
+template <>
+struct Prec<double> {
+    static constexpr double safety = 1.0 - 8.0 * 1.1102230246251565e-16;  // 1 - 8 * 2^-53
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+};
+
+// theta blend when one half of the Euler update would go negative
+template <typename T>
+__device__ __noinline__ T pp_blend(T phi, T u0, T u1, T two_nu, T up, T um) {
+    T th = T(1);
+    if (up < T(0)) {
+        const T base = u0 - two_nu * u0;  // U^{UP,+}
+        const T den = base - up;
+        th = den > T(0) ? Prec<T>::div(base, den) : T(0);
+    }
+    if (um < T(0)) {
+        const T base = u1 + two_nu * u0;  // U^{UP,-}
+        const T den = base - um;
+        const T t2 = den > T(0) ? Prec<T>::div(base, den) : T(0);
+        th = fmin(th, t2);
+    }
+    th *= Prec<T>::safety;
+    th = fmin(fmax(th, T(0)), T(1));
+    return th * phi + (T(1) - th) * u0;
+}
+
+// PP limiter: keep f_i - 2 nu phi >= 0 and f_{i+1} + 2 nu phi >= 0
+template <typename T>
+__device__ __forceinline__ T pp_limit(T phi, T u0, T u1, T two_nu) {
+    const T up = u0 - two_nu * phi;
+    const T um = u1 + two_nu * phi;
+    if (fmin(up, um) >= T(0)) return phi;
+    return pp_blend(phi, u0, u1, two_nu, up, um);
+}
+
+// MP then PP on a flux that failed the combined fast test below
+template <typename T>
+__device__ __noinline__ T limit_slow(T phi, T um2, T um1, T u0, T u1, T u2, T alpha, T two_nu) {
+    phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
+    return pp_limit(phi, u0, u1, two_nu);
+}
+
+// Interface flux on the upwind-ordered stencil (u0 = upwind cell).
+// FULL (MP and PP both on): one combined test keeps the common case -- phi
+// strictly between u0 and f* (App. A step 3 accepts) and both halves of the
+// Euler update non-negative (PP inactive) -- on a short branch-free path; a
+// product that underflows only sends a case to the exact slow path, which
+// returns the same value.
+template <typename T, int ORDER, bool FULL>
+__device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
+                                  T alpha, T two_nu, int mp, int pp) {
+    T phi;
+    if (ORDER == 7) {
+        phi = sh.w[0] * um3;
+        phi = fma(sh.w[1], um2, phi);
+    } else {
+        phi = sh.w[1] * um2;
+    }
+    phi = fma(sh.w[2], um1, phi);
+    phi = fma(sh.w[3], u0, phi);
+    phi = fma(sh.w[4], u1, phi);
+    phi = fma(sh.w[5], u2, phi);
+    if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
+    if (FULL) {
+        const T fstar = u0 + mm2(u1 - u0, alpha * (u0 - um1));
+        const T up = u0 - two_nu * phi;
+        const T um = u1 + two_nu * phi;
+        if ((phi - u0) * (fstar - phi) > T(0) && fmin(up, um) >= T(0)) return phi;
+        return limit_slow(phi, um2, um1, u0, u1, u2, alpha, two_nu);
+    }
+    if (mp) phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
+    if (pp) phi = pp_limit(phi, u0, u1, two_nu);
+    return phi;
+}
+
+// ---- line walker ---------------------------------------------------------------
+//
+// Advance cells [r0, r1) of one line staged in shared memory.  Row r of the
+// line is at sm[(r + PAD) * ss] with PAD = 1 for zero-inflow lines, whose
+// rows -1 and L hold zeros: reads outside the line are clamped onto them.
+// Periodic lines (PAD = 0) wrap; the walk is split into wrap-free chunks.
+// The walk goes upwind -> downwind so that each interface flux is computed
+// once; the 8-cell stencil window rotates through registers (unrolled by 8).
+// store(i, v) writes the new value of cell i.
+
+template <typename T, int ORDER, bool PERIODIC, bool FULL, typename Store>
+__device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, const LineShift<T> &sh,
+                                     int r0, int r1, T alpha, int mp, int pp, Store store) {
+    if (r0 >= r1) return;
+    constexpr int PAD = PERIODIC ? 0 : 1;
+    const int sg = sh.sigma;
+    const T nu = sh.nu;
+    const T two_nu = T(2) * nu;
+    int i = sg > 0 ? r0 : r1 - 1;
+    const int cnt = r1 - r0;
+    int p;  // source row of the next value to enter the window
+    if (PERIODIC) {
+        int n = sh.n % L;
+        p = (i - n - 4 * sg) % L;
+        if (p < 0) p += L;
+    } else {
+        p = i - sh.n - 4 * sg;
+    }
+    auto load = [&](int q) -> T {
+        if (!PERIODIC) q = min(max(q, -1), L);
+        return sm[(q + PAD) * ss];
+    };
+    auto advance = [&]() {
+        p += sg;
+        if (PERIODIC) {
+            if (p >= L) p -= L;
+            if (p < 0) p += L;
+        }
+    };
+    T w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        w[k] = load(p);
+        advance();
+    }
+    // incoming flux of the first cell: upwind cell i - sg, stencil w[0..6]
+    T fin = flux<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, two_nu, mp, pp);
+
+    // one cell with the window rotated by K (u_k at w[(K + 4 + k) & 7])
+#define VP_WALK_STEP(K)                                                                           \
+    {                                                                                             \
+        const T fout = flux<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7], w[(K + 3) & 7],   \
+                                      w[(K + 4) & 7], w[(K + 5) & 7], w[(K + 6) & 7],             \
+                                      w[(K + 7) & 7], alpha, two_nu, mp, pp);                     \
+        store(i, w[(K + 4) & 7] - nu * (fout - fin));                                             \
+        fin = fout;                                                                               \
+        i += sg;                                                                                  \
+        w[K & 7] = load(p);                                                                       \
+        p += sg;                                                                                  \
+    }
+
+    int t = 0;
+    while (t < cnt) {
+        int end = cnt;
+        if (PERIODIC) {
+            // loads stay inside [0, L) for this many steps
+            const int room = sg > 0 ? L - p : p + 1;
+            end = t + room < cnt ? t + room : cnt;
+        }
+        for (; t + 8 <= end; t += 8) {
+            VP_WALK_STEP(0)
+            VP_WALK_STEP(1)
+            VP_WALK_STEP(2)
+            VP_WALK_STEP(3)
+            VP_WALK_STEP(4)
+            VP_WALK_STEP(5)
+            VP_WALK_STEP(6)
+            VP_WALK_STEP(7)
+        }
+        for (; t < end; ++t) {
+            VP_WALK_STEP(0)
+            // restore the canonical order (u_-4 in w[0])
+            const T w0 = w[0];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) w[k] = w[k + 1];
+            w[7] = w0;
+        }
+        if (PERIODIC) {
+            if (p >= L) p -= L;
+            if (p < 0) p += L;
+        }
+    }
+#undef VP_WALK_STEP
+}
+
+// Shift decomposition of one line, in double precision so that the integer
+// part is exact (reading R2): s = c dt / h, n = nearest integer (halves away
+// from zero), zeta = s - n, nu = |zeta|, sigma = sign(zeta); the CSL weights
+// are the weight polynomials evaluated at nu.
+template <typename T>
+__device__ __forceinline__ LineShift<T> make_shift(double speed, double dt, double h, const WPoly &wp) {
+    const double s = __ddiv_rn(__dmul_rn(speed, dt), h);
+    double n = round(s);
+    const double z = __dadd_rn(s, -n);
+    const double nu = fabs(z);
+    LineShift<T> sh;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        double acc = 0.0;
+        for (int j = wp.nterm - 1; j >= 0; --j) acc = fma(acc, nu, wp.c[j][k]);
+        sh.w[k] = (T)acc;
+    }
+    // shifts beyond a billion cells only happen with absurd inputs; clamp so
+    // the integer conversion stays defined (a zero-inflow line is empty anyway)
+    n = fmin(fmax(n, -1.0e9), 1.0e9);
+    sh.nu = (T)nu;
+    sh.n = (int)n;
+    sh.sigma = z < 0.0 ? -1 : 1;
+    return sh;
+}
+
+// velocity of cell j of an axis: lo + (j + 1/2) dv, rounded step by step
+__device__ __forceinline__ double cell_centre(double lo, double dvel, int j) {
+    return __dadd_rn(lo, __dmul_rn((double)j + 0.5, dvel));
+}
+
+__device__ __forceinline__ unsigned line_class(const SweepGeo &g, unsigned o, unsigned c) {
+    return g.cls_from_inner ? (c / (unsigned)g.cdiv) % (unsigned)g.cmod : o / (unsigned)g.cdiv;
+}
+
+}  // namespace vp_core

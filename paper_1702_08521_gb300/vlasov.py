@@ -50,6 +50,15 @@ class vp_grid(ctypes.Structure):
     ]
 
 
+class vp_run_desc(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int), ("nx", ctypes.c_int * 2), ("nv", ctypes.c_int * 2),
+        ("xlo", ctypes.c_double * 2), ("xhi", ctypes.c_double * 2),
+        ("vlo", ctypes.c_double * 2), ("vhi", ctypes.c_double * 2),
+        ("coupling", ctypes.c_double), ("rho_bg", ctypes.c_double), ("pois_order", ctypes.c_int),
+    ]
+
+
 class vp_diag(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in DIAG_NAMES]
 
@@ -97,6 +106,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_set_option": (I, [P, I, LL]),
             "vp_get_tuning": (I, [P, I, I, P]),
             "vp_poisson_periodic_noalloc": (I, [GP, P, P, P, P]),
+            "vp_ensemble_create": (I, [P, I, I, P, ctypes.POINTER(P)]),
+            "vp_ensemble_destroy": (None, [P]),
+            "vp_ensemble_last_error": (ctypes.c_char_p, [P]),
+            "vp_ensemble_num_cells": (LL, [P]),
+            "vp_ensemble_run_layout": (I, [P, I, P, P]),
+            "vp_ensemble_bind": (I, [P, P]),
+            "vp_ensemble_init_run": (I, [P, I, I, P, I]),
+            "vp_ensemble_field": (I, [P]),
+            "vp_ensemble_accel": (I, [P, P]),
+            "vp_ensemble_set_tiles": (I, [P, I, I, I]),
+            "vp_ensemble_get_tiles": (I, [P, P]),
+            "vp_ensemble_autotune": (I, [P]),
+            "vp_ensemble_step": (I, [P, D, I]),
+            "vp_ensemble_sync": (I, [P]),
+            "vp_ensemble_launch_count": (LL, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -235,6 +259,95 @@ def vp_poisson_periodic_noalloc(grid: vp_grid, stream, rho, phi, accel) -> int:
     h = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
     return int(load().vp_poisson_periodic_noalloc(ctypes.byref(grid), ctypes.c_void_p(h), _ptr(rho),
                                                   _ptr(phi), _ptr(accel)))
+
+
+# ---- batched ensembles -----------------------------------------------------------
+
+def _echeck(ens, rc: int) -> None:
+    if rc != VP_OK:
+        raise VpError(rc, load().vp_ensemble_last_error(ens).decode() if ens else "")
+
+
+def make_run(dims: int, nx, nv, xlo, xhi, vlo, vhi, coupling: float = -1.0, rho_bg: float = 1.0,
+             pois_order: int = 6, **_ignored) -> vp_run_desc:
+    r = vp_run_desc()
+    r.dims = dims
+    for d in range(dims):
+        r.nx[d], r.nv[d] = int(nx[d]), int(nv[d])
+        r.xlo[d], r.xhi[d], r.vlo[d], r.vhi[d] = float(xlo[d]), float(xhi[d]), float(vlo[d]), float(vhi[d])
+    r.coupling, r.rho_bg, r.pois_order = float(coupling), float(rho_bg), int(pois_order)
+    return r
+
+
+def vp_ensemble_create(runs, order: int = 7, stream=None):
+    arr = (vp_run_desc * len(runs))(*runs)
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    out = ctypes.c_void_p()
+    rc = load().vp_ensemble_create(ctypes.cast(arr, ctypes.c_void_p), len(runs), order, ctypes.c_void_p(h),
+                                   ctypes.byref(out))
+    if rc != VP_OK:
+        raise VpError(rc, "vp_ensemble_create failed")
+    return out
+
+
+def vp_ensemble_destroy(ens) -> None:
+    load().vp_ensemble_destroy(ens)
+
+
+def vp_ensemble_num_cells(ens) -> int:
+    return int(load().vp_ensemble_num_cells(ens))
+
+
+def vp_ensemble_run_layout(ens, run: int):
+    f = ctypes.c_longlong()
+    a = ctypes.c_longlong()
+    _echeck(ens, load().vp_ensemble_run_layout(ens, run, ctypes.byref(f), ctypes.byref(a)))
+    return f.value, a.value
+
+
+def vp_ensemble_bind(ens, pool) -> None:
+    _echeck(ens, load().vp_ensemble_bind(ens, _ptr(pool)))
+
+
+def vp_ensemble_init_run(ens, run: int, kind: int, params) -> None:
+    arr = (ctypes.c_double * len(params))(*[float(p) for p in params])
+    _echeck(ens, load().vp_ensemble_init_run(ens, run, kind, ctypes.cast(arr, ctypes.c_void_p), len(params)))
+
+
+def vp_ensemble_field(ens) -> None:
+    _echeck(ens, load().vp_ensemble_field(ens))
+
+
+def vp_ensemble_accel(ens) -> int:
+    p = ctypes.c_void_p()
+    _echeck(ens, load().vp_ensemble_accel(ens, ctypes.byref(p)))
+    return p.value
+
+
+def vp_ensemble_set_tiles(ens, W: int, R: int, ctas_per_sm: int = 0) -> None:
+    _echeck(ens, load().vp_ensemble_set_tiles(ens, W, R, ctas_per_sm))
+
+
+def vp_ensemble_get_tiles(ens) -> dict:
+    out = (ctypes.c_int * 3)()
+    _echeck(ens, load().vp_ensemble_get_tiles(ens, ctypes.cast(out, ctypes.c_void_p)))
+    return {"W": out[0], "R": out[1], "ctas_per_sm": out[2]}
+
+
+def vp_ensemble_autotune(ens) -> None:
+    _echeck(ens, load().vp_ensemble_autotune(ens))
+
+
+def vp_ensemble_step(ens, dt: float, nsteps: int) -> None:
+    _echeck(ens, load().vp_ensemble_step(ens, dt, nsteps))
+
+
+def vp_ensemble_sync(ens) -> None:
+    _echeck(ens, load().vp_ensemble_sync(ens))
+
+
+def vp_ensemble_launch_count(ens) -> int:
+    return int(load().vp_ensemble_launch_count(ens))
 
 
 # ---- convenience owner -----------------------------------------------------------

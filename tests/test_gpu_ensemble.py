@@ -1,0 +1,125 @@
+"""Batched ensemble (one persistent launch per KDK step of all runs) against
+the single-run path (itself checked against the oracle) and the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1702_08521_gb300 import inputs
+from paper_1702_08521_gb300 import vlasov as V
+
+from gpu_helpers import rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def _runs():
+    """A small uneven ensemble: 1D Landau / two-stream of several sizes and
+    one 2D2V Landau run."""
+    specs = []
+    for kind, nx, nv, k, a in [("landau", 32, 64, 0.5, 0.3), ("two_stream", 64, 128, 0.4, 0.05),
+                               ("landau", 128, 256, 0.35, 0.01), ("landau", 256, 512, 0.6, 0.2),
+                               ("two_stream", 32, 512, 0.3, 0.1)]:
+        vmax = 6.0 if kind == "landau" else 8.0
+        specs.append(dict(kind=kind, dims=1, nx=[nx], nv=[nv], k=[k], alpha=a, xlo=[0.0],
+                          xhi=[2 * math.pi / k], vlo=[-vmax], vhi=[vmax]))
+    specs.append(dict(kind="landau", dims=2, nx=[16, 16], nv=[32, 32], k=[0.5, 0.5], alpha=0.05,
+                      xlo=[0.0, 0.0], xhi=[4 * math.pi] * 2, vlo=[-6.0, -6.0], vhi=[6.0, 6.0]))
+    return specs
+
+
+def _ic(spec):
+    if spec["kind"] == "landau":
+        k = spec["k"] + [0.0] * (3 - len(spec["k"]))
+        return V.VP_IC_LANDAU, [spec["alpha"], k[0], k[1], k[2], 1.0, 1.0]
+    return V.VP_IC_TWOSTREAM, [spec["alpha"], spec["k"][0]]
+
+
+def _grid(spec):
+    return dict(dims=spec["dims"], nx=spec["nx"], nv=spec["nv"], xlo=spec["xlo"], xhi=spec["xhi"],
+                vlo=spec["vlo"], vhi=spec["vhi"], order=7)
+
+
+def _ensemble(specs, stream):
+    import torch
+    runs = [V.make_run(**_grid(s)) for s in specs]
+    ens = V.vp_ensemble_create(runs, 7, stream)
+    pool = torch.zeros(V.vp_ensemble_num_cells(ens) + 64, dtype=torch.float32, device="cuda")
+    V.vp_ensemble_bind(ens, pool)
+    for i, s in enumerate(specs):
+        V.vp_ensemble_init_run(ens, i, *_ic(s))
+    V.vp_ensemble_field(ens)
+    return ens, pool
+
+
+def _run_slice(ens, pool, i, spec):
+    off, _ = V.vp_ensemble_run_layout(ens, i)
+    n = int(np.prod(spec["nx"])) * int(np.prod(spec["nv"]))
+    return pool[off:off + n].double().cpu().numpy()
+
+
+def test_ensemble_matches_single_runs():
+    import torch
+    specs = _runs()
+    stream = torch.cuda.Stream()
+    ens, pool = _ensemble(specs, stream)
+    dt, steps = 0.05, 20
+    V.vp_ensemble_step(ens, dt, steps)
+    V.vp_ensemble_sync(ens)
+    for i, s in enumerate(specs):
+        sim = V.Simulation(_grid(s), precision=V.VP_F32)
+        V.vp_init_f(sim.ctx, *_ic(s))
+        sim.field()
+        sim.step(dt, steps, split=V.VP_SPLIT_KDK)
+        sim.sync()
+        ref = sim.f.double().cpu().numpy()
+        got = _run_slice(ens, pool, i, s)
+        assert rel_l1(got, ref) <= 1e-6, (i, rel_l1(got, ref))
+        assert got.min() >= 0.0
+        sim.close()
+    V.vp_ensemble_destroy(ens)
+
+
+def test_ensemble_run_vs_oracle():
+    """One two-stream member, FP32 in the ensemble vs the FP64 oracle."""
+    import torch
+    specs = _runs()[:2]
+    stream = torch.cuda.Stream()
+    ens, pool = _ensemble(specs, stream)
+    V.vp_ensemble_step(ens, 0.05, 20)
+    V.vp_ensemble_sync(ens)
+    s = specs[1]
+    og = O.grid(**_grid(s))
+    kind, params = _ic(s)
+    f = O.init_f(og, kind, params).astype(np.float32).astype(np.float64)
+    # the ensemble initialised its own f on the device: compare its t = 0 state first
+    _, _, acc = O.field(og, f)
+    O.step(og, f, 0.05, 20, np.ascontiguousarray(acc), split=O.SPLIT_KDK)
+    got = _run_slice(ens, pool, 1, s)
+    assert rel_l1(got, f) <= 1e-5
+    V.vp_ensemble_destroy(ens)
+
+
+def test_autotune_leaves_f_unchanged_and_graph_matches_direct():
+    import torch
+    specs = _runs()
+    stream = torch.cuda.Stream()
+    ens, pool = _ensemble(specs, stream)
+    before = pool.clone()
+    V.vp_ensemble_autotune(ens)
+    V.vp_ensemble_sync(ens)
+    assert torch.equal(before, pool)
+    tiles = V.vp_ensemble_get_tiles(ens)
+    assert tiles["W"] in (32, 64, 128) and tiles["ctas_per_sm"] >= 1
+    # graph replay (non-default stream) vs direct launches on the legacy stream
+    V.vp_ensemble_step(ens, 0.05, 3)
+    V.vp_ensemble_sync(ens)
+    ens2, pool2 = _ensemble(specs, None)
+    V.vp_ensemble_set_tiles(ens2, tiles["W"], tiles["R"], tiles["ctas_per_sm"])
+    V.vp_ensemble_step(ens2, 0.05, 3)
+    V.vp_ensemble_sync(ens2)
+    n = V.vp_ensemble_num_cells(ens)
+    assert rel_l1(pool2[:n].double().cpu().numpy(), pool[:n].double().cpu().numpy()) <= 1e-6
+    V.vp_ensemble_destroy(ens)
+    V.vp_ensemble_destroy(ens2)
