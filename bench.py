@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--sweep-impl", type=int, default=0, choices=[0, 1, 2],
                    help="0 auto, 1 staged-load kernels, 2 TMA pipeline")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--ensemble-steps", type=int, default=20)
     return p.parse_args()
 
 
@@ -192,6 +194,67 @@ def small_cfg(cfg):
     return cfg, f"{cfg['name']} FP64, KDK sweep sequence"
 
 
+def job_rate(t_local: float, units_local: int, world: int, device=None):
+    """Whole-job throughput of weakly scaled replicas: every rank processes
+    units_local units; the job time is the slowest rank's time.  Returns
+    (max time over ranks, total units / max time)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    tmax = float(tt.item())
+    return tmax, world * units_local / tmax
+
+
+def ensemble_bench(steps: int, warmup: int = 3):
+    """Batched-ensemble workload (512 uneven 1D1V runs + 8 2D2V 64^2 x 64^2
+    Landau runs from PCG64(1702)), FP32 MP7+PP, dt = 0.05, KDK: one persistent
+    launch per step of all runs, graph-captured, autotuned tiles."""
+    import torch
+    from paper_1702_08521_gb300 import inputs
+    from paper_1702_08521_gb300 import vlasov as V
+    draws = inputs.ensemble_draws()
+    runs = [V.make_run(dims=d["dims"], nx=d["nx"], nv=d["nv"], xlo=d["xlo"], xhi=d["xhi"], vlo=d["vlo"],
+                       vhi=d["vhi"]) for d in draws]
+    stream = torch.cuda.Stream()
+    ens = V.vp_ensemble_create(runs, 7, stream)
+    pool = torch.zeros(V.vp_ensemble_num_cells(ens) + 64, dtype=torch.float32, device="cuda")
+    V.vp_ensemble_bind(ens, pool)
+    cells = 0
+    updates_per_step = 0
+    for i, d in enumerate(draws):
+        k = d["k"] + [0.0] * (3 - len(d["k"]))
+        if d["kind"] == "landau":
+            V.vp_ensemble_init_run(ens, i, V.VP_IC_LANDAU, [d["alpha"], k[0], k[1], k[2], 1.0, 1.0])
+        else:
+            V.vp_ensemble_init_run(ens, i, V.VP_IC_TWOSTREAM, [d["alpha"], k[0]])
+        n = 1
+        for v in d["nx"] + d["nv"]:
+            n *= v
+        cells += n
+        updates_per_step += n * 3 * d["dims"]
+    V.vp_ensemble_field(ens)
+    V.vp_ensemble_autotune(ens)
+    V.vp_ensemble_step(ens, 0.05, warmup)
+    V.vp_ensemble_sync(ens)
+    l0 = V.vp_ensemble_launch_count(ens)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    V.vp_ensemble_step(ens, 0.05, steps)
+    b.record(stream)
+    V.vp_ensemble_sync(ens)
+    ms = a.elapsed_time(b) / steps
+    out = {"workload": "ensemble 512 x 1D1V + 8 x 2D2V 64^2x64^2 (PCG64 seed 1702), FP32 MP7+PP, KDK",
+           "runs": len(draws), "cells": cells, "steps": steps, "ms_per_step": ms,
+           "value": updates_per_step / (ms / 1e3), "unit": "cell-updates/s",
+           "launches_per_step": (V.vp_ensemble_launch_count(ens) - l0) / steps,
+           "tiles": V.vp_ensemble_get_tiles(ens)}
+    V.vp_ensemble_destroy(ens)
+    del pool
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -270,11 +333,7 @@ def main():
         barrier()
     launches = V.vp_launch_count(sim.ctx) - l0
     t = ev0.elapsed_time(ev1) / 1e3
-    tt = torch.tensor([t], device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    tmax = float(tt.item())
-    value = world * ncell * nsw * args.steps / tmax
+    tmax, value = job_rate(t, ncell * nsw * args.steps, world, dev)
 
     # per-sweep-kind timing of the sweep kernel (CUDA events on the library stream)
     dims = cfg["grid"]["dims"]
@@ -338,6 +397,13 @@ def main():
         except RuntimeError as ex:
             e2e = {"value": None, "unit": "cell-updates/s", "error": str(ex)[:200]}
 
+    ens = None
+    if not args.no_ensemble and rank == 0:
+        try:
+            ens = ensemble_bench(args.ensemble_steps)
+        except Exception as ex:  # reported, not hidden
+            ens = {"error": str(ex)[:300]}
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         small, desc = small_cfg(cfg)
@@ -355,7 +421,8 @@ def main():
                           "dt": dt, "l2": "inputs larger than L2 (f is %.1f GB)" % (ncell * esize / 1e9),
                           "parallelism": f"replicas x{world}"},
                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
-               "sweeps": per_kind, "tuning": tuning, "e2e": e2e, "cpu_baseline": cpu}
+               "sweeps": per_kind, "tuning": tuning, "ensemble": ens, "e2e": e2e,
+               "cpu_baseline": cpu}
         print(json.dumps(out))
     sim.close()
     if world > 1:

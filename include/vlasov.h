@@ -262,6 +262,67 @@ int vp_ensemble_step(vp_ens *ens, double dt, int nsteps);
 int vp_ensemble_sync(vp_ens *ens);
 long long vp_ensemble_launch_count(const vp_ens *ens);
 
+/* ---- learned flux correction (not in the paper) --------------------------
+ * A 9 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the CSL7 flux of a sweep
+ * on a coarse velocity grid: Phi = Phi_CSL7 + s g(x), where s = max |u_k| + 1e-30
+ * over the upwind-ordered 8-cell stencil u_{-3..4} of the interface and
+ * x = ((u_k - u_0) / s for k = -3..4, nu).  The corrected flux then passes the
+ * MP constraint (App. A) and the PP limiter (Sec. 2.1.1), and the update keeps
+ * the flux form (Eq. 49), so mass conservation and f >= 0 hold as for the
+ * plain scheme.  Weights and matrix inputs are rounded to bfloat16, sums are
+ * FP32.  Parameters: VP_NET_NPARAM floats, W1[32][9] b1[32] W2[32][32] b2[32]
+ * W3[32][32] b3[32] w4[32] b4[1] (FP32 master copy; rounded when used).
+ * Training pairs come from fine-grid runs of the method (vp_fine_flux,
+ * vp_fluxnet_line_map, vp_group_mean, vp_restrict_velocity, vp_make_samples).
+ */
+#define VP_NET_NPARAM 2465
+
+/* one sweep of the grid of ctx (FP32, order 7) with the network correction
+ * (use_net = 1) or without it (use_net = 0: identical to vp_drift_sweep /
+ * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); in place. */
+int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
+                     const float *wts_dev, int use_net);
+
+/* Mass that the sweep (kick, dim, dt) of ctx's current f moves through every
+ * `every`-th interface of every line, in cell units: G[line][j] for the
+ * interface before cell j * every (j = 0 .. L / every); f' = f + G_{i-1/2} -
+ * G_{i+1/2} reproduces the sweep.  f is not modified.  G_dev: device doubles. */
+int vp_fine_flux(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev, int every,
+                 double *G_dev);
+
+/* For a coarse grid whose velocity cells are factor^D fine cells (same
+ * spatial grid, D <= 2): the fine lines averaged by every coarse line of the
+ * sweep (kick, dim).  map_host (host, n_coarse_lines * group entries) may be
+ * NULL to query the sizes. */
+int vp_fluxnet_line_map(const vp_grid *fine, const vp_grid *coarse, int factor, int kick, int dim,
+                        long long *map_host, long long *n_coarse_lines, int *group);
+
+/* G_coarse[l][j] = scale * mean_g G_fine[map[l][g]][j] (device arrays) */
+int vp_group_mean(const double *G_fine, long long n_coarse_lines, int nout, const long long *map_dev,
+                  int group, double scale, double *G_coarse, void *cuda_stream);
+
+/* coarse f = mean over factor1 x factor2 fine velocity cells ([NX][nf1][nf2]
+ * -> [NX][nf1/factor1][nf2/factor2]; nf2 = factor2 = 1 for one velocity
+ * dimension); device arrays */
+int vp_restrict_velocity(const float *f_fine, float *f_coarse, long long NX, int nf1, int nf2, int factor1,
+                         int factor2, void *cuda_stream);
+
+/* Training pairs on the coarse grid of ctx: for every line and interface
+ * (L + 1 per line), X (9 floats) and y = (Phi_target - Phi_CSL7) / s, where
+ * Phi_target = (Gc - whole coarse cells swept) / nu; y = NaN where |zeta|
+ * < zmin or the interface is the duplicate periodic end. */
+int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *accel_dev,
+                    const double *Gc_dev, double zmin, float *X_dev, float *y_dev);
+
+/* loss += mean (g - y)^2 and grad += its gradient over nsamp samples
+ * (straight-through bfloat16 rounding); all device arrays */
+int vp_net_grad(const float *X_dev, const float *y_dev, long long nsamp, const float *wts_dev,
+                float *grad_dev, float *loss_dev, void *cuda_stream);
+
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the FP32 parameters; zeroes grad */
+int vp_net_adam(float *wts_dev, float *m_dev, float *v_dev, float *grad_dev, int step, float lr,
+                void *cuda_stream);
+
 /*
  * vp_poisson_periodic_noalloc -- the periodic Poisson solve and force of
  * vp_poisson_solve (same arguments and results for a grid with

@@ -1,0 +1,112 @@
+"""FP64 reference of the learned flux correction (test infrastructure only).
+
+Not part of the paper: the learned correction is a spec addition to the
+method.  It is restated here in plain numpy, in double precision, so that the
+GPU training and inference kernels can be checked against it.
+
+Network (per interface, upwind-ordered stencil u_{-3..4}, u_0 = upwind cell):
+    s    = max_k |u_k| + 1e-30
+    x    = [(u_k - u_0) / s for k = -3..4] + [nu]          (9 features)
+    h1   = relu(W1 x  + b1)      W1: 32 x 9
+    h2   = relu(W2 h1 + b2)      W2: 32 x 32
+    h3   = relu(W3 h2 + b3)      W3: 32 x 32
+    g    = w4 . h3 + b4          w4: 32
+    Phi_net = Phi_CSL + s * g    (then the MP constraint and the PP limiter)
+Weights and every matrix input (x, h1, h2, h3) are rounded to bfloat16 as on
+the tensor cores; sums are exact here (FP64) and FP32 on the GPU.  Training
+loss: mean over samples of (g - y)^2 with y = (Phi_target - Phi_CSL) / s.
+The backward pass treats the bfloat16 rounding as the identity.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+HIDDEN = 32
+NFEAT = 9
+SHAPES = {"W1": (HIDDEN, NFEAT), "b1": (HIDDEN,), "W2": (HIDDEN, HIDDEN), "b2": (HIDDEN,),
+          "W3": (HIDDEN, HIDDEN), "b3": (HIDDEN,), "w4": (HIDDEN,), "b4": (1,)}
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
+
+
+def bf16(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    nan = np.isnan(f)
+    if np.any(nan):
+        out[nan] = np.nan
+    return out
+
+
+def features(u, nu) -> tuple:
+    """u: (B, 8) upwind-ordered stencils u_{-3..4}; nu: (B,). Returns (X, s)."""
+    u = np.asarray(u, dtype=np.float64)
+    s = np.abs(u).max(axis=1) + 1e-30
+    X = np.concatenate([(u - u[:, 3:4]) / s[:, None], np.asarray(nu, dtype=np.float64)[:, None]], axis=1)
+    return X, s
+
+
+def init_params(seed: int = 0) -> dict:
+    rng = np.random.default_rng(seed)
+    p = {}
+    for k, shp in SHAPES.items():
+        if k.startswith("W") or k == "w4":
+            fan_in = shp[-1] if len(shp) == 2 else HIDDEN
+            p[k] = rng.normal(0.0, np.sqrt(2.0 / fan_in), size=shp) * (0.1 if k == "w4" else 1.0)
+        else:
+            p[k] = np.zeros(shp)
+    return p
+
+
+def pack(p: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).ravel() for k in ORDER])
+
+
+def unpack(v) -> dict:
+    v = np.asarray(v, dtype=np.float64)
+    p, o = {}, 0
+    for k in ORDER:
+        n = int(np.prod(SHAPES[k]))
+        p[k] = v[o:o + n].reshape(SHAPES[k])
+        o += n
+    return p
+
+
+def forward(p: dict, X, *, round_bf16: bool = True):
+    """g (B,) and the cache for backward."""
+    q = (lambda a: bf16(a)) if round_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    W1, W2, W3, w4 = q(p["W1"]), q(p["W2"]), q(p["W3"]), q(p["w4"])
+    x0 = q(X)
+    z1 = x0 @ W1.T + p["b1"]
+    h1 = np.maximum(z1, 0.0)
+    x1 = q(h1)
+    z2 = x1 @ W2.T + p["b2"]
+    h2 = np.maximum(z2, 0.0)
+    x2 = q(h2)
+    z3 = x2 @ W3.T + p["b3"]
+    h3 = np.maximum(z3, 0.0)
+    x3 = q(h3)
+    g = x3 @ w4 + p["b4"][0]
+    return g, (x0, z1, x1, z2, x2, z3, x3, W1, W2, W3, w4)
+
+
+def loss_and_grad(p: dict, X, y, *, round_bf16: bool = True):
+    """Mean squared error and its gradient (dict) over the batch."""
+    g, (x0, z1, x1, z2, x2, z3, x3, W1, W2, W3, w4) = forward(p, X, round_bf16=round_bf16)
+    B = len(y)
+    r = g - np.asarray(y, dtype=np.float64)
+    loss = float(np.mean(r * r))
+    dg = 2.0 * r / B
+    grads = {"w4": x3.T @ dg, "b4": np.array([dg.sum()])}
+    dh3 = np.outer(dg, w4) * (z3 > 0)
+    grads["W3"] = dh3.T @ x2
+    grads["b3"] = dh3.sum(axis=0)
+    dh2 = (dh3 @ W3) * (z2 > 0)
+    grads["W2"] = dh2.T @ x1
+    grads["b2"] = dh2.sum(axis=0)
+    dh1 = (dh2 @ W2) * (z1 > 0)
+    grads["W1"] = dh1.T @ x0
+    grads["b1"] = dh1.sum(axis=0)
+    return loss, grads

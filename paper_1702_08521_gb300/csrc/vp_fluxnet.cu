@@ -1,0 +1,689 @@
+// vp_fluxnet.cu -- learned flux correction on a coarser velocity grid
+// (a spec addition to the method, not in the paper).
+//
+// A 9 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the CSL7 flux of a
+// coarse-grid sweep: Phi = Phi_CSL7 + s g(x), s = max |u| over the 8-cell
+// upwind-ordered stencil u_{-3..4}, x = ((u_k - u_0) / s, nu).  Weights and
+// matrix inputs are bfloat16, sums FP32.  The corrected flux then passes the
+// MP constraint and the PP limiter unchanged, so conservation (flux form)
+// and f >= 0 hold exactly as for the plain scheme.
+//
+// Training data come from fine-grid runs of the method itself: for a sweep,
+// the fine-grid mass through every coarse interface (mean over the fine
+// lines a coarse line aggregates), minus the coarse integer-shift part,
+// divided by the coarse CFL number, is the target coarse flux.
+// Training: per-sample forward/backward (FP32, bfloat16-rounded weights and
+// activations, straight-through backward), per-CTA weight-gradient
+// reductions, Adam.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "vp_internal.cuh"
+#include "vp_sweep_core.cuh"
+
+namespace {
+
+constexpr int H = VP_NET_HIDDEN;
+constexpr int NF = VP_NET_FEATURES;
+
+// parameter layout (floats): W1[H][NF] b1[H] W2[H][H] b2[H] W3[H][H] b3[H] w4[H] b4[1]
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + H * NF;
+constexpr int OFF_W2 = OFF_B1 + H;
+constexpr int OFF_B2 = OFF_W2 + H * H;
+constexpr int OFF_W3 = OFF_B2 + H;
+constexpr int OFF_B3 = OFF_W3 + H * H;
+constexpr int OFF_W4 = OFF_B3 + H;
+constexpr int OFF_B4 = OFF_W4 + H;
+constexpr int NPARAM = OFF_B4 + 1;
+static_assert(NPARAM == VP_NET_NPARAM, "parameter count");
+
+__device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// ---- network on one sample (SIMT, weights in shared memory, rounded) -------------
+
+struct NetAct {
+    float x[NF], h1[H], h2[H], h3[H];
+    float z1[H], z2[H], z3[H];
+};
+
+__device__ __forceinline__ float net_forward(const float *__restrict__ w, const float *xin, float *h1,
+                                             float *h2, float *h3) {
+    float x[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) x[k] = bfr(xin[k]);
+#pragma unroll 4
+    for (int j = 0; j < H; ++j) {
+        float a = w[OFF_B1 + j];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) a = fmaf(w[OFF_W1 + j * NF + k], x[k], a);
+        h1[j] = bfr(fmaxf(a, 0.f));
+    }
+#pragma unroll 4
+    for (int j = 0; j < H; ++j) {
+        float a = w[OFF_B2 + j];
+#pragma unroll
+        for (int k = 0; k < H; ++k) a = fmaf(w[OFF_W2 + j * H + k], h1[k], a);
+        h2[j] = bfr(fmaxf(a, 0.f));
+    }
+    float g = w[OFF_B4];
+#pragma unroll 4
+    for (int j = 0; j < H; ++j) {
+        float a = w[OFF_B3 + j];
+#pragma unroll
+        for (int k = 0; k < H; ++k) a = fmaf(w[OFF_W3 + j * H + k], h2[k], a);
+        const float v = bfr(fmaxf(a, 0.f));
+        if (h3) h3[j] = v;
+        g = fmaf(w[OFF_W4 + j], v, g);
+    }
+    return g;
+}
+
+// features of the upwind-ordered stencil u[0..7] = u_{-3..4}
+__device__ __forceinline__ float net_features(const float *u, float nu, float *x) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = fmaxf(s, fabsf(u[k]));
+    s += 1e-30f;
+    const float inv = 1.0f / s;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (u[k] - u[3]) * inv;
+    x[8] = nu;
+    return s;
+}
+
+// ---- training ----------------------------------------------------------------------
+
+constexpr int kTrainThreads = 128;
+
+// One CTA: kTrainThreads samples.  Loss and weight gradients accumulated in
+// global FP32 (per-CTA reductions, then one atomic per parameter).
+__global__ void __launch_bounds__(kTrainThreads) k_net_grad(const float *__restrict__ X,
+                                                            const float *__restrict__ y,
+                                                            const float *__restrict__ wts, long long nsamp,
+                                                            float *__restrict__ grad,
+                                                            float *__restrict__ loss) {
+    __shared__ float w[NPARAM];
+    __shared__ float A0[kTrainThreads][NF + 1];
+    __shared__ float A1[kTrainThreads][H + 1];
+    __shared__ float A2[kTrainThreads][H + 1];
+    __shared__ float D[kTrainThreads][H + 1];  // delta of the current layer
+    __shared__ float red[kTrainThreads];
+    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
+        w[i] = (i >= OFF_B4 || (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) ||
+                (i >= OFF_B3 && i < OFF_W4))
+                   ? wts[i]
+                   : bfr(wts[i]);
+    __syncthreads();
+    const long long sidx = (long long)blockIdx.x * kTrainThreads + threadIdx.x;
+    const bool valid = sidx < nsamp;
+    const int t = threadIdx.x;
+    float x[NF], h1[H], h2[H], h3[H];
+    float r = 0.f;
+    if (valid) {
+        for (int k = 0; k < NF; ++k) x[k] = X[sidx * NF + k];
+        const float g = net_forward(w, x, h1, h2, h3);
+        r = g - y[sidx];
+    } else {
+        for (int k = 0; k < NF; ++k) x[k] = 0.f;
+        for (int j = 0; j < H; ++j) h1[j] = h2[j] = h3[j] = 0.f;
+    }
+    const float dg = valid ? 2.0f * r / (float)nsamp : 0.f;
+    red[t] = valid ? r * r / (float)nsamp : 0.f;
+    for (int k = 0; k < NF; ++k) A0[t][k] = bfr(x[k]);
+    for (int j = 0; j < H; ++j) {
+        A1[t][j] = h1[j];
+        A2[t][j] = h2[j];
+    }
+    // layer 4: g = w4 . h3 + b4
+    for (int j = 0; j < H; ++j) D[t][j] = h3[j];  // temporarily hold h3
+    __syncthreads();
+    // grads of w4, b4: sum_s dg_s h3_s
+    {
+        __shared__ float dgs[kTrainThreads];
+        dgs[t] = dg;
+        __syncthreads();
+        if (t < H) {
+            float a = 0.f;
+            for (int s = 0; s < kTrainThreads; ++s) a = fmaf(dgs[s], D[s][t], a);
+            atomicAdd(grad + OFF_W4 + t, a);
+        }
+        if (t == H) {
+            float a = 0.f, l = 0.f;
+            for (int s = 0; s < kTrainThreads; ++s) {
+                a += dgs[s];
+                l += red[s];
+            }
+            atomicAdd(grad + OFF_B4, a);
+            atomicAdd(loss, l);
+        }
+        __syncthreads();
+    }
+    // delta3 = dg * w4 * [h3 > 0] (h3 > 0 iff its pre-activation was > 0)
+    float d3[H];
+    for (int j = 0; j < H; ++j) d3[j] = (h3[j] > 0.f) ? dg * w[OFF_W4 + j] : 0.f;
+    __syncthreads();
+    for (int j = 0; j < H; ++j) D[t][j] = d3[j];
+    __syncthreads();
+    // grads W3 = sum_s d3_s h2_s^T, b3 = sum_s d3_s
+    for (int e = t; e < H * H; e += blockDim.x) {
+        const int i = e / H, k = e % H;
+        float a = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) a = fmaf(D[s][i], A2[s][k], a);
+        atomicAdd(grad + OFF_W3 + e, a);
+    }
+    if (t < H) {
+        float a = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) a += D[s][t];
+        atomicAdd(grad + OFF_B3 + t, a);
+    }
+    // delta2 = (W3^T d3) * [h2 > 0]
+    float d2[H];
+    for (int k = 0; k < H; ++k) {
+        float a = 0.f;
+        for (int j = 0; j < H; ++j) a = fmaf(w[OFF_W3 + j * H + k], d3[j], a);
+        d2[k] = (h2[k] > 0.f) ? a : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < H; ++j) D[t][j] = d2[j];
+    __syncthreads();
+    for (int e = t; e < H * H; e += blockDim.x) {
+        const int i = e / H, k = e % H;
+        float a = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) a = fmaf(D[s][i], A1[s][k], a);
+        atomicAdd(grad + OFF_W2 + e, a);
+    }
+    if (t < H) {
+        float a = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) a += D[s][t];
+        atomicAdd(grad + OFF_B2 + t, a);
+    }
+    float d1[H];
+    for (int k = 0; k < H; ++k) {
+        float a = 0.f;
+        for (int j = 0; j < H; ++j) a = fmaf(w[OFF_W2 + j * H + k], d2[j], a);
+        d1[k] = (h1[k] > 0.f) ? a : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < H; ++j) D[t][j] = d1[j];
+    __syncthreads();
+    for (int e = t; e < H * NF; e += blockDim.x) {
+        const int i = e / NF, k = e % NF;
+        float a = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) a = fmaf(D[s][i], A0[s][k], a);
+        atomicAdd(grad + OFF_W1 + e, a);
+    }
+    if (t < H) {
+        float a = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) a += D[s][t];
+        atomicAdd(grad + OFF_B1 + t, a);
+    }
+}
+
+__global__ void k_adam(float *__restrict__ wts, float *__restrict__ m, float *__restrict__ v,
+                       float *__restrict__ grad, int n, float lr, float b1, float b2, float eps, float bc1,
+                       float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    wts[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    grad[i] = 0.f;
+}
+
+// ---- training data -----------------------------------------------------------------
+
+// Mass through interfaces of fine lines, in fine-cell units, for one sweep:
+// G_{i+1/2} = sum of the N whole cells swept through + nu Phi_hat at the
+// shifted interface (the flux form of the SL update: f'_i = f_i + G_{i-1/2}
+// - G_{i+1/2}).  Lines: f viewed as [outer][L][inner]; one thread per line;
+// the line's class (speed) as in the sweeps.  Output: G at interfaces
+// j * every - 1/2 for j = 0 .. L/every (boundary interfaces included).
+__global__ void k_fine_flux(const float *__restrict__ f, long long outer, int L, long long inner,
+                            int periodic, int kick, int from_inner, long long cdiv, long long cmod,
+                            const double *__restrict__ accel, double lo, double dvel, double dt,
+                            double h, WPoly wp, int every, double *__restrict__ G, float alpha) {
+    extern __shared__ double fx[];  // [L][blockDim] prefix sums (FP64)
+    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int T = blockDim.x;
+    const bool ok = line < outer * inner;
+    const long long o = ok ? line / inner : 0, c = ok ? line % inner : 0;
+    const float *base = f + o * L * inner + c;
+    const long long cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
+    const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
+    const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, wp);
+    const int sg = sh.sigma;
+    // value of the line in the upwind frame (reversed when sigma < 0)
+    auto val = [&](long long k) -> float {
+        if (periodic) {
+            k %= L;
+            if (k < 0) k += L;
+        } else if (k < 0 || k >= L) {
+            return 0.f;
+        }
+        const long long kk = sg > 0 ? k : L - 1 - k;
+        return base[kk * inner];
+    };
+    // prefix sums S(k) = sum_{m < k} u_m in the upwind frame
+    double acc = 0.0;
+    if (ok)
+        for (int k = 0; k < L; ++k) {
+            fx[k * T + threadIdx.x] = acc;
+            acc += val(k);
+        }
+    const double total = acc;
+    auto S = [&](long long k) -> double {  // sum_{m < k}, extended beyond the line
+        if (periodic) {
+            long long q = k / L, r = k % L;
+            if (r < 0) {
+                r += L;
+                q -= 1;
+            }
+            return fx[r * T + threadIdx.x] + (double)q * total;
+        }
+        if (k <= 0) return 0.0;
+        if (k >= L) return total;
+        return fx[k * T + threadIdx.x];
+    };
+    if (!ok) return;
+    const int n = sh.n * sg;  // whole cells swept, in the upwind frame (>= 0)
+    const int nout = L / every + 1;
+    for (int j = 0; j < nout; ++j) {
+        // interface between cells (i - 1) and i of the original line, i = j * every
+        const int i = j * every;
+        // in the upwind frame the interface sits between cells ip - 1 and ip
+        const int ip = sg > 0 ? i : L - i;
+        // G' = sum_{m = ip - n}^{ip - 1} u_m + nu Phi(upwind cell ip - 1 - n)
+        const long long up = (long long)ip - 1 - n;
+        float u[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) u[k] = val(up - 3 + k);
+        const float two_nu = 2.0f * sh.nu;
+        const float ph = vp_core::flux<float, 7, true>(sh, u[0], u[1], u[2], u[3], u[4], u[5], u[6], alpha,
+                                                       two_nu, 1, 1);
+        const double g = (S(ip) - S(ip - n)) + (double)sh.nu * (double)ph;
+        G[line * nout + j] = sg > 0 ? g : -g;
+    }
+}
+
+// coarse state: mean over the (factor1 x factor2) fine velocity cells of a
+// velocity grid [nf1][nf2] (nf2 = factor2 = 1 for one velocity dimension)
+__global__ void k_restrict_v2(const float *__restrict__ ff, float *__restrict__ fc, long long NX, int nf1,
+                              int nf2, int factor1, int factor2) {
+    const int nc1 = nf1 / factor1, nc2 = nf2 / factor2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= NX * nc1 * nc2) return;
+    const long long x = t / (nc1 * nc2);
+    const int J = (int)(t % (nc1 * nc2));
+    const int J1 = J / nc2, J2 = J % nc2;
+    double s = 0.0;
+    for (int a = 0; a < factor1; ++a)
+        for (int b = 0; b < factor2; ++b)
+            s += ff[x * nf1 * nf2 + (long long)(J1 * factor1 + a) * nf2 + (J2 * factor2 + b)];
+    fc[t] = (float)(s / (factor1 * factor2));
+}
+
+// Samples on coarse lines: for every coarse interface with |zeta| >= zmin,
+// features of the coarse stencil and the normalised target
+// y = (Phi_target - Phi_CSL7) / s.  Gc: coarse-unit masses through the
+// coarse interfaces ([coarse line][L + 1]).  Invalid samples get y = NaN.
+__global__ void k_make_samples(const float *__restrict__ fc, long long outer, int L, long long inner,
+                               int periodic, int kick, int from_inner, long long cdiv, long long cmod,
+                               const double *__restrict__ accel, double lo, double dvel, double dt,
+                               double h, WPoly wp, const double *__restrict__ Gc, double zmin,
+                               float *__restrict__ X, float *__restrict__ y) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nlines = outer * inner;
+    if (t >= nlines * (L + 1)) return;
+    const long long line = t / (L + 1);
+    const int i = (int)(t % (L + 1));  // interface between cells i - 1 and i
+    const long long o = line / inner, c = line % inner;
+    const float *base = fc + o * L * inner + c;
+    const long long cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
+    const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
+    const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, wp);
+    const double s_full = speed * dt / h;
+    const double zeta = s_full - round(s_full);
+    float *xo = X + t * NF;
+    if (fabs(zeta) < zmin || (periodic && i == L)) {
+        for (int k = 0; k < NF; ++k) xo[k] = 0.f;
+        y[t] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int sg = sh.sigma;
+    auto val = [&](long long k) -> float {
+        if (periodic) {
+            k %= L;
+            if (k < 0) k += L;
+        } else if (k < 0 || k >= L) {
+            return 0.f;
+        }
+        const long long kk = sg > 0 ? k : L - 1 - k;
+        return base[kk * inner];
+    };
+    const int ip = sg > 0 ? i : L - i;
+    const int n = sh.n * sg;
+    const long long up = (long long)ip - 1 - n;
+    float u[8];
+    for (int k = 0; k < 8; ++k) u[k] = val(up - 3 + k);
+    // whole cells swept in the upwind frame, signed: sum_{m = ip - n}^{ip - 1} u_m
+    // (n < 0 when the integer shift opposes the fractional one)
+    double whole = 0.0;
+    if (n >= 0)
+        for (long long m = ip - n; m < ip; ++m) whole += val(m);
+    else
+        for (long long m = ip; m < ip - n; ++m) whole -= val(m);
+    const double g = sg > 0 ? Gc[line * (L + 1) + i] : -Gc[line * (L + 1) + i];
+    const double phi_t = (g - whole) / (double)sh.nu;
+    double phi_c = 0.0;
+    for (int k = 0; k < 7; ++k) phi_c += (double)sh.w[k] * (double)u[k];
+    float x[NF];
+    const float s = net_features(u, sh.nu, x);
+    for (int k = 0; k < NF; ++k) xo[k] = x[k];
+    y[t] = (float)((phi_t - phi_c) / (double)s);
+}
+
+// coarse-interface masses from fine ones: mean over `group` fine lines of
+// every fine value, scaled by `scale` (fine -> coarse cell units)
+__global__ void k_group_mean(const double *__restrict__ Gf, long long ncl, int nout, const long long *map,
+                             int group, double scale, double *__restrict__ Gc) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncl * nout) return;
+    const long long cl = t / nout;
+    const int j = (int)(t % nout);
+    double s = 0.0;
+    for (int g = 0; g < group; ++g) s += Gf[map[cl * group + g] * nout + j];
+    Gc[t] = scale * s / group;
+}
+
+// ---- inference: the learned coarse sweep (strided or contiguous lines) ------------------
+//
+// One thread per line of the coarse grid (coarse sweeps are small); the line
+// is read once into registers/shared memory; interface fluxes are computed
+// in the upwind direction as in the plain walk, with the network correction
+// added before the limiters.
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, long long outer, int L,
+                                                       long long inner, int kick, int from_inner,
+                                                       long long cdiv, long long cmod,
+                                                       const double *__restrict__ accel, double lo,
+                                                       double dvel, double dt, double h, WPoly wp,
+                                                       const float *__restrict__ wts, float alpha,
+                                                       int use_net) {
+    extern __shared__ float lsm[];
+    float *w = lsm;                       // NPARAM rounded weights
+    float *line_buf = lsm + NPARAM + 3;   // [L + 2][blockDim] staged line (zero ghosts at 0, L+1)
+    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
+        w[i] = (i >= OFF_B4 || (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) ||
+                (i >= OFF_B3 && i < OFF_W4))
+                   ? wts[i]
+                   : bfr(wts[i]);
+    __syncthreads();
+    const int T = blockDim.x;
+    const long long line = (long long)blockIdx.x * T + threadIdx.x;
+    if (line >= outer * inner) return;
+    const long long o = line / inner, c = line % inner;
+    float *base = f + o * L * inner + c;
+    float *sl = line_buf + threadIdx.x;  // row r at sl[(r + 1) * T]
+    sl[0] = 0.f;
+    sl[(L + 1) * T] = 0.f;
+    for (int r = 0; r < L; ++r) sl[(r + 1) * T] = base[(long long)r * inner];
+    const long long cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
+    const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
+    const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, wp);
+    const int sg = sh.sigma;
+    const float nu = sh.nu, two_nu = 2.f * nu;
+    int n = sh.n;
+    if (PERIODIC) {
+        n %= L;
+        if (n < 0) n += L;
+    }
+    auto ld = [&](int q) -> float {  // row q of the line (any integer)
+        if (PERIODIC) {
+            q %= L;
+            if (q < 0) q += L;
+        } else {
+            q = min(max(q, -1), L);
+        }
+        return sl[(q + 1) * T];
+    };
+    // flux through the interface whose upwind cell is q (upwind-ordered stencil)
+    auto iface = [&](int q) -> float {
+        float u[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[k] = ld(q + sg * (k - 3));
+        float phi = sh.w[0] * u[0];
+#pragma unroll
+        for (int k = 1; k < 7; ++k) phi = fmaf(sh.w[k], u[k], phi);
+        if (use_net) {
+            float x[NF], h1[H], h2[H];
+            const float s = net_features(u, nu, x);
+            phi = fmaf(s, net_forward(w, x, h1, h2, nullptr), phi);
+        }
+        phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
+        return vp_core::pp_limit(phi, u[3], u[4], two_nu);
+    };
+    // new values into registers of the staged line is not possible in place
+    // (neighbours still read old values): compute all, then write
+    float fin = iface((sg > 0 ? 0 : L - 1) - n - sg);
+    for (int t = 0; t < L; ++t) {
+        const int i = sg > 0 ? t : L - 1 - t;
+        const float fout = iface(i - n);
+        base[(long long)i * inner] = ld(i - n) - nu * (fout - fin);
+        fin = fout;
+    }
+}
+
+}  // namespace
+
+// ---- host entry points ------------------------------------------------------------------
+
+extern "C" {
+
+int vp_net_grad(const float *X, const float *y, long long nsamp, const float *wts, float *grad,
+                float *loss, void *stream) {
+    if (!X || !y || !wts || !grad || !loss || nsamp < 1) return VP_EINVAL;
+    const long long blocks = (nsamp + kTrainThreads - 1) / kTrainThreads;
+    k_net_grad<<<(unsigned)blocks, kTrainThreads, 0, static_cast<cudaStream_t>(stream)>>>(X, y, wts, nsamp,
+                                                                                         grad, loss);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}
+
+int vp_net_adam(float *wts, float *m, float *v, float *grad, int step, float lr, void *stream) {
+    if (!wts || !m || !v || !grad || step < 1 || !(lr > 0.f)) return VP_EINVAL;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    k_adam<<<(NPARAM + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(wts, m, v, grad, NPARAM, lr, b1,
+                                                                               b2, 1e-8f, bc1, bc2);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}
+
+}  // extern "C"
+
+// geometry helpers shared with the context-level entry points below
+namespace {
+struct LineGeo {
+    long long outer, inner;
+    int L, periodic, kick, from_inner;
+    long long cdiv, cmod;
+    double lo, dvel, h;
+};
+
+LineGeo line_geo(const vp_grid &g, long long NX, long long NV, int kick, int dim) {
+    LineGeo q{};
+    if (!kick) {
+        long long outer = 1, inner = NV, vstride = 1;
+        for (int k = 0; k < dim; ++k) outer *= g.nx[k];
+        for (int k = dim + 1; k < g.dx; ++k) inner *= g.nx[k];
+        for (int k = dim + 1; k < g.dv; ++k) vstride *= g.nv[k];
+        q.outer = outer;
+        q.inner = inner;
+        q.L = g.nx[dim];
+        q.periodic = g.xbc == VP_BC_PERIODIC;
+        q.from_inner = 1;
+        q.cdiv = vstride;
+        q.cmod = g.nv[dim];
+        q.h = (g.xhi[dim] - g.xlo[dim]) / g.nx[dim];
+    } else {
+        long long vouter = 1, inner = 1;
+        for (int k = 0; k < dim; ++k) vouter *= g.nv[k];
+        for (int k = dim + 1; k < g.dv; ++k) inner *= g.nv[k];
+        q.outer = NX * vouter;
+        q.inner = inner;
+        q.L = g.nv[dim];
+        q.periodic = 0;
+        q.from_inner = 0;
+        q.cdiv = vouter;
+        q.cmod = 1;
+        q.h = (g.vhi[dim] - g.vlo[dim]) / g.nv[dim];
+    }
+    q.kick = kick;
+    q.lo = g.vlo[dim];
+    q.dvel = (g.vhi[dim] - g.vlo[dim]) / g.nv[dim];
+    return q;
+}
+}  // namespace
+
+extern "C" {
+
+int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
+                     int use_net) {
+    if (!c || !c->f) return VP_EINVAL;
+    if (c->g.precision != VP_F32 || c->g.order != 7)
+        return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
+    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
+        return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
+    const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
+    const int T = 128;
+    const size_t smem = (size_t)(NPARAM + 3 + (q.L + 2) * T) * sizeof(float);
+    if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line too long for the learned sweep");
+    const long long nl = q.outer * q.inner;
+    const unsigned blocks = (unsigned)((nl + T - 1) / T);
+    cudaFuncSetAttribute(k_learned_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_learned_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (q.periodic)
+        k_learned_sweep<true><<<blocks, T, smem, c->stream>>>(
+            static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
+            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net);
+    else
+        k_learned_sweep<false><<<blocks, T, smem, c->stream>>>(
+            static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
+            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net);
+    c->launches++;
+    VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+int vp_fine_flux(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, int every,
+                 double *G_dev) {
+    if (!c || !c->f || !G_dev || every < 1) return VP_EINVAL;
+    if (c->g.precision != VP_F32 || c->g.order != 7)
+        return vp_fail(c, VP_ENOTSUP, "fine fluxes are computed for FP32 CSL7 grids");
+    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev)) return vp_fail(c, VP_EINVAL, "bad fine-flux arguments");
+    const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
+    if (q.L % every) return vp_fail(c, VP_EINVAL, "line length must be a multiple of `every`");
+    const int T = 64;
+    const size_t smem = (size_t)q.L * T * sizeof(double);
+    if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line too long");
+    cudaFuncSetAttribute(k_fine_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const long long nl = q.outer * q.inner;
+    k_fine_flux<<<(unsigned)((nl + T - 1) / T), T, smem, c->stream>>>(
+        static_cast<const float *>(c->f), q.outer, q.L, q.inner, q.periodic, kick, q.from_inner, q.cdiv, q.cmod,
+        accel_dev, q.lo, q.dvel, dt, q.h, c->wp, every, G_dev, (float)c->g.alpha);
+    c->launches++;
+    VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+int vp_restrict_velocity(const float *f_fine, float *f_coarse, long long NX, int nf1, int nf2, int factor1,
+                         int factor2, void *stream) {
+    if (!f_fine || !f_coarse || factor1 < 1 || factor2 < 1 || nf1 % factor1 || nf2 % factor2) return VP_EINVAL;
+    const long long n = NX * (nf1 / factor1) * (nf2 / factor2);
+    k_restrict_v2<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        f_fine, f_coarse, NX, nf1, nf2, factor1, factor2);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}
+
+int vp_group_mean(const double *G_fine, long long n_coarse_lines, int nout, const long long *map_dev,
+                  int group, double scale, double *G_coarse, void *stream) {
+    if (!G_fine || !map_dev || !G_coarse || group < 1 || nout < 1) return VP_EINVAL;
+    const long long n = n_coarse_lines * nout;
+    k_group_mean<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        G_fine, n_coarse_lines, nout, map_dev, group, scale, G_coarse);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}
+
+// Fine lines aggregated by every coarse line of a sweep, for a coarse grid
+// whose velocity cells are factor^D fine cells (same spatial grid).
+int vp_fluxnet_line_map(const vp_grid *fine, const vp_grid *coarse, int factor, int kick, int dim,
+                        long long *map_host, long long *n_coarse_lines, int *group) {
+    if (!fine || !coarse || factor < 1 || fine->dx != coarse->dx || fine->dx < 1 || fine->dx > 2) return VP_EINVAL;
+    const int D = fine->dx;
+    long long NXf = 1, NVf = 1, NVc = 1;
+    for (int k = 0; k < D; ++k) {
+        if (fine->nx[k] != coarse->nx[k] || fine->nv[k] != factor * coarse->nv[k]) return VP_EINVAL;
+        NXf *= fine->nx[k];
+        NVf *= fine->nv[k];
+        NVc *= coarse->nv[k];
+    }
+    const LineGeo qc = line_geo(*coarse, NXf, NVc, kick, dim);
+    const LineGeo qf = line_geo(*fine, NXf, NVf, kick, dim);
+    const long long ncl = qc.outer * qc.inner;
+    // velocity cells of the coarse line's other axes, expanded
+    int g = 1;
+    for (int k = 0; k < D; ++k)
+        if (!(kick && k == dim)) g *= factor;
+    if (n_coarse_lines) *n_coarse_lines = ncl;
+    if (group) *group = g;
+    if (!map_host) return VP_OK;
+    for (long long cl = 0; cl < ncl; ++cl) {
+        const long long O = cl / qc.inner, C = cl % qc.inner;
+        // full coarse index of the line's first cell, decomposed [x..][J..]
+        const long long lin = O * (long long)qc.L * qc.inner + C;
+        long long x = lin / NVc, J = lin % NVc;
+        int Jv[2] = {0, 0};
+        for (int k = D - 1; k >= 0; --k) {
+            Jv[k] = (int)(J % coarse->nv[k]);
+            J /= coarse->nv[k];
+        }
+        int idx = 0;
+        for (int a = 0; a < (D > 0 ? factor : 1); ++a)
+            for (int b = 0; b < (D > 1 ? factor : 1); ++b) {
+                int jf[2] = {Jv[0] * factor + a, D > 1 ? Jv[1] * factor + b : 0};
+                // along the swept velocity axis every fine line starts at cell 0
+                if (kick) {
+                    if (dim == 0 && a) continue;
+                    if (dim == 1 && b) continue;
+                    jf[dim] = 0;
+                }
+                long long jl = 0;
+                for (int k = 0; k < D; ++k) jl = jl * fine->nv[k] + jf[k];
+                const long long flin = x * NVf + jl;  // fine index of the line's first cell
+                const long long Of = flin / ((long long)qf.L * qf.inner);
+                const long long Cf = flin % qf.inner;
+                map_host[cl * g + idx++] = Of * qf.inner + Cf;
+            }
+    }
+    return VP_OK;
+}
+
+int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *accel_dev,
+                    const double *Gc_dev, double zmin, float *X_dev, float *y_dev) {
+    vp_ctx *c = coarse;
+    if (!c || !c->f || !Gc_dev || !X_dev || !y_dev) return VP_EINVAL;
+    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev)) return vp_fail(c, VP_EINVAL, "bad sample arguments");
+    const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
+    const long long n = q.outer * q.inner * (q.L + 1);
+    k_make_samples<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(
+        static_cast<const float *>(c->f), q.outer, q.L, q.inner, q.periodic, kick, q.from_inner, q.cdiv, q.cmod,
+        accel_dev, q.lo, q.dvel, dt, q.h, c->wp, Gc_dev, zmin, X_dev, y_dev);
+    c->launches++;
+    VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+}  // extern "C"

@@ -32,7 +32,7 @@ __device__ __forceinline__ T mid3(T a, T b, T c) {
 
 // Steps 4-7 of the MP constraint (taken only when step 3 rejects phi).
 template <typename T>
-__device__ __noinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
+__device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
     if (um1 == u0 && u0 == u1) return u0;  // every bound collapses onto u0
     const T back = u0 - um1;
     const T dm = um2 + u0 - T(2) * um1;  // curvature at the upwind neighbour
@@ -49,10 +49,19 @@ __device__ __noinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alp
 }
 
 // MP constraint of phi at the interface between u0 (upwind) and u1.
+// Step 3 accepts phi iff it lies strictly between u0 and f* = u0 + minmod(p, q),
+// p = u1 - u0, q = alpha (u0 - u_{-1}); with a = phi - u0 that is: a strictly
+// between 0 and p and strictly between 0 and q, i.e. (p - a) a > 0 and
+// (q - a) a > 0 -- products on the FMA pipe instead of min/max chains.  A
+// product that underflows only sends the case to the exact test below.
 template <typename T>
 __device__ __forceinline__ T mp_limit(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
-    const T fstar = u0 + mm2(u1 - u0, alpha * (u0 - um1));
-    const T a = phi - u0, b = fstar - phi;  // accept iff phi lies strictly between u0 and f*
+    const T a = phi - u0;
+    const T p = u1 - u0;
+    const T q = alpha * (u0 - um1);
+    if ((p - a) * a > T(0) && (q - a) * a > T(0)) return phi;
+    const T fstar = u0 + mm2(p, q);
+    const T b = fstar - phi;
     if (fmin(a, b) > T(0) || fmax(a, b) < T(0)) return phi;
     return mp_bounds(phi, um2, um1, u0, u1, u2, alpha);
 }
@@ -72,7 +81,7 @@ struct Prec<double> {
 
 // theta blend when one half of the Euler update would go negative
 template <typename T>
-__device__ __noinline__ T pp_blend(T phi, T u0, T u1, T two_nu, T up, T um) {
+__device__ __forceinline__ T pp_blend(T phi, T u0, T u1, T two_nu, T up, T um) {
     T th = T(1);
     if (up < T(0)) {
         const T base = u0 - two_nu * u0;  // U^{UP,+}
@@ -99,19 +108,8 @@ __device__ __forceinline__ T pp_limit(T phi, T u0, T u1, T two_nu) {
     return pp_blend(phi, u0, u1, two_nu, up, um);
 }
 
-// MP then PP on a flux that failed the combined fast test below
-template <typename T>
-__device__ __noinline__ T limit_slow(T phi, T um2, T um1, T u0, T u1, T u2, T alpha, T two_nu) {
-    phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
-    return pp_limit(phi, u0, u1, two_nu);
-}
-
-// Interface flux on the upwind-ordered stencil (u0 = upwind cell).
-// FULL (MP and PP both on): one combined test keeps the common case -- phi
-// strictly between u0 and f* (App. A step 3 accepts) and both halves of the
-// Euler update non-negative (PP inactive) -- on a short branch-free path; a
-// product that underflows only sends a case to the exact slow path, which
-// returns the same value.
+// Interface flux on the upwind-ordered stencil (u0 = upwind cell).  FULL:
+// MP and PP both on, so the runtime switches drop out of the loop.
 template <typename T, int ORDER, bool FULL>
 __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
                                   T alpha, T two_nu, int mp, int pp) {
@@ -127,15 +125,8 @@ __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T
     phi = fma(sh.w[4], u1, phi);
     phi = fma(sh.w[5], u2, phi);
     if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
-    if (FULL) {
-        const T fstar = u0 + mm2(u1 - u0, alpha * (u0 - um1));
-        const T up = u0 - two_nu * phi;
-        const T um = u1 + two_nu * phi;
-        if ((phi - u0) * (fstar - phi) > T(0) && fmin(up, um) >= T(0)) return phi;
-        return limit_slow(phi, um2, um1, u0, u1, u2, alpha, two_nu);
-    }
-    if (mp) phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
-    if (pp) phi = pp_limit(phi, u0, u1, two_nu);
+    if (FULL || mp) phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
+    if (FULL || pp) phi = pp_limit(phi, u0, u1, two_nu);
     return phi;
 }
 

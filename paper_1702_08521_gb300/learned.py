@@ -1,0 +1,185 @@
+"""Learned flux correction on a coarser velocity grid: data generation from
+fine-grid runs of the method, training, and coarse runs with the network.
+
+The correction acts on the velocity sweeps (kicks), where the coarse grid
+loses resolution; spatial sweeps (drifts) run the plain scheme: their
+coarse-grid error comes from the spread of speeds inside one coarse velocity
+cell, which the spatial stencil the network sees cannot resolve.
+
+Orchestration only: every arithmetic step (sweeps, fine-flux extraction,
+restriction, sample construction, forward/backward, Adam, learned sweeps)
+runs in the CUDA library through the C ABI; torch holds device memory and
+selects rows (valid samples, minibatches).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import vlasov as V
+
+
+def landau_grid(dims: int, nx: int, nv: int, k: float = 0.5, vmax: float = 6.0) -> dict:
+    L = 2 * math.pi / k
+    return dict(dims=dims, nx=[nx] * dims, nv=[nv] * dims, xlo=[0.0] * dims, xhi=[L] * dims,
+                vlo=[-vmax] * dims, vhi=[vmax] * dims, order=7)
+
+
+def _landau_ic(dims, k, alpha):
+    kk = [k] * dims + [0.0] * (3 - dims)
+    return V.VP_IC_LANDAU, [alpha, kk[0], kk[1], kk[2], 1.0, 1.0]
+
+
+def _sweeps(dims):
+    """(kick, dim, dt factor) of a KDK step, with None for the field solve."""
+    seq = [(1, d, 0.5) for d in range(dims)] + [(0, d, 1.0) for d in range(dims - 1, -1, -1)]
+    return seq + [None] + [(1, d, 0.5) for d in range(dims)]
+
+
+class Sampler:
+    """Builds training pairs for one (fine grid, coarse factor) combination."""
+
+    def __init__(self, dims: int, nx: int, nv_fine: int, factor: int, k: float, stream):
+        import torch
+        self.torch = torch
+        self.dims, self.factor, self.stream = dims, factor, stream
+        self.gf = landau_grid(dims, nx, nv_fine, k)
+        self.gc = landau_grid(dims, nx, nv_fine // factor, k)
+        self.fine = V.Simulation(self.gf, precision=V.VP_F32, stream=stream)
+        self.coarse = V.Simulation(self.gc, precision=V.VP_F32, stream=stream)
+        self.maps = {}
+        for kick in (0, 1):
+            for d in range(dims):
+                m, ncl, grp = V.vp_fluxnet_line_map(V.make_grid(**self.gf), V.make_grid(**self.gc),
+                                                    factor, kick, d)
+                self.maps[(kick, d)] = (torch.as_tensor(m, dtype=torch.int64, device="cuda"), ncl, grp)
+
+    def restrict(self):
+        nv = self.gf["nv"]
+        if self.dims == 2:
+            V.vp_restrict_velocity(self.fine.f, self.coarse.f, self.fine.NX, nv[0], nv[1], self.factor,
+                                   self.factor, self.stream)
+        else:
+            V.vp_restrict_velocity(self.fine.f, self.coarse.f, self.fine.NX, nv[0], 1, self.factor, 1,
+                                   self.stream)
+
+    def samples(self, kick, d, dt, zmin, keep, rng):
+        """Pairs for the sweep (kick, d, dt) of the current fine state."""
+        torch = self.torch
+        acc = self.fine.accel[d * self.fine.NX:] if kick else None
+        Lf = self.gf["nv"][d] if kick else self.gf["nx"][d]
+        every = self.factor if kick else 1
+        nlf = self.fine.NX * int(np.prod(self.gf["nv"])) // Lf
+        nout = Lf // every + 1
+        Gf = torch.empty(nlf * nout, dtype=torch.float64, device="cuda")
+        V.vp_fine_flux(self.fine.ctx, kick, d, dt, acc, every, Gf)
+        m, ncl, grp = self.maps[(kick, d)]
+        Gc = torch.empty(ncl * nout, dtype=torch.float64, device="cuda")
+        V.vp_group_mean(Gf, ncl, nout, m, grp, 1.0 / every, Gc, self.stream)
+        self.restrict()
+        ns = ncl * nout
+        X = torch.empty(ns * 9, dtype=torch.float32, device="cuda")
+        y = torch.empty(ns, dtype=torch.float32, device="cuda")
+        cacc = self.coarse.accel[d * self.coarse.NX:] if kick else None
+        if kick:
+            self.coarse.accel.copy_(self.fine.accel)
+        V.vp_make_samples(self.coarse.ctx, kick, d, dt, cacc, Gc, zmin, X, y)
+        self.stream.synchronize()
+        ok = torch.isfinite(y)
+        Xv, yv = X.view(ns, 9)[ok], y[ok]
+        if keep and yv.numel() > keep:
+            sel = torch.as_tensor(rng.choice(yv.numel(), size=keep, replace=False), device="cuda")
+            Xv, yv = Xv[sel], yv[sel]
+        return Xv, yv
+
+    def run_draw(self, k, alpha, dt, steps, every_step, zmin, keep, rng):
+        """Fine run from the Landau state (k, alpha); pairs of its velocity
+        sweeps every `every_step` steps."""
+        V.vp_init_f(self.fine.ctx, *_landau_ic(self.dims, k, alpha))
+        self.fine.field()
+        Xs, ys = [], []
+        for n in range(steps):
+            take = (n + 1) % every_step == 0
+            for sw in _sweeps(self.dims):
+                if sw is None:
+                    self.fine.field()
+                    continue
+                kick, d, fac = sw
+                if take and kick:
+                    X, y = self.samples(kick, d, fac * dt, zmin, keep, rng)
+                    Xs.append(X)
+                    ys.append(y)
+                acc = self.fine.accel[d * self.fine.NX:] if kick else None
+                if kick:
+                    V.vp_kick_sweep(self.fine.ctx, d, fac * dt, acc)
+                else:
+                    V.vp_drift_sweep(self.fine.ctx, d, fac * dt)
+        return Xs, ys
+
+    def close(self):
+        self.fine.close()
+        self.coarse.close()
+
+
+def he_init(seed: int = 0):
+    """Initial parameters (W ~ N(0, 2 / fan_in), last layer x 0.1, zero biases),
+    laid out as W1[32][9] b1 W2[32][32] b2 W3[32][32] b3 w4[32] b4."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for rows, cols, scale in ((32, 9, 1.0), (32, 32, 1.0), (32, 32, 1.0), (1, 32, 0.1)):
+        parts.append(torch.randn(rows * cols, generator=g) * math.sqrt(2.0 / cols) * scale)
+        parts.append(torch.zeros(rows))
+    w = torch.cat(parts)
+    assert w.numel() == V.VP_NET_NPARAM
+    return w.cuda()
+
+
+def train_net(X, y, iters: int = 1500, batch: int = 32768, lr: float = 2e-3, seed: int = 0, stream=None,
+              w0=None):
+    """Adam on the mean squared error over minibatches; returns (weights, losses).
+    w0: initial parameters (VP_NET_NPARAM floats, e.g. a He initialisation)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    w = (w0 if w0 is not None else he_init(seed)).clone().float().cuda()
+    m = torch.zeros_like(w)
+    v = torch.zeros_like(w)
+    grad = torch.zeros_like(w)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    n = y.numel()
+    hist = []
+    for it in range(1, iters + 1):
+        idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
+        Xb = X[idx].contiguous()
+        yb = y[idx].contiguous()
+        loss.zero_()
+        V.vp_net_grad(Xb, yb, yb.numel(), w, grad, loss, stream)
+        V.vp_net_adam(w, m, v, grad, it, lr * (0.1 ** (it / iters)), stream)
+        if it % 50 == 0 or it == iters:
+            hist.append(float(loss.item()))
+    return w, hist
+
+
+def coarse_run(grid: dict, ic, dt: float, steps: int, wts=None, stream=None):
+    """KDK run on `grid` with plain (wts None) or learned sweeps; returns the Simulation."""
+    sim = V.Simulation(grid, precision=V.VP_F32, stream=stream)
+    V.vp_init_f(sim.ctx, *ic)
+    sim.field()
+    dims = grid["dims"]
+    for _ in range(steps):
+        for sw in _sweeps(dims):
+            if sw is None:
+                sim.field()
+                continue
+            kick, d, fac = sw
+            acc = sim.accel[d * sim.NX:] if kick else None
+            if kick and wts is not None:
+                V.vp_learned_sweep(sim.ctx, kick, d, fac * dt, acc, wts, 1)
+            elif kick:
+                V.vp_kick_sweep(sim.ctx, d, fac * dt, acc)
+            else:
+                V.vp_drift_sweep(sim.ctx, d, fac * dt)
+    sim.sync()
+    return sim

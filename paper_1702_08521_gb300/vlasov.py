@@ -121,6 +121,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_ensemble_step": (I, [P, D, I]),
             "vp_ensemble_sync": (I, [P]),
             "vp_ensemble_launch_count": (LL, [P]),
+            "vp_learned_sweep": (I, [P, I, I, D, P, P, I]),
+            "vp_fine_flux": (I, [P, I, I, D, P, I, P]),
+            "vp_fluxnet_line_map": (I, [GP, GP, I, I, I, P, P, P]),
+            "vp_group_mean": (I, [P, LL, I, P, I, D, P, P]),
+            "vp_restrict_velocity": (I, [P, P, LL, I, I, I, I, P]),
+            "vp_make_samples": (I, [P, I, I, D, P, P, D, P, P]),
+            "vp_net_grad": (I, [P, P, LL, P, P, P, P]),
+            "vp_net_adam": (I, [P, P, P, P, I, ctypes.c_float, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -348,6 +356,66 @@ def vp_ensemble_sync(ens) -> None:
 
 def vp_ensemble_launch_count(ens) -> int:
     return int(load().vp_ensemble_launch_count(ens))
+
+
+# ---- learned flux correction -----------------------------------------------------
+
+VP_NET_NPARAM = 2465
+
+
+def _sh(stream):
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+
+
+def _rc(rc: int, what: str) -> None:
+    if rc != VP_OK:
+        raise VpError(rc, what)
+
+
+def vp_learned_sweep(ctx, kick: int, dim: int, dt: float, accel, wts, use_net: int = 1) -> None:
+    _check(ctx, load().vp_learned_sweep(ctx, kick, dim, dt, _ptr(accel), _ptr(wts), use_net))
+
+
+def vp_fine_flux(ctx, kick: int, dim: int, dt: float, accel, every: int, G) -> None:
+    _check(ctx, load().vp_fine_flux(ctx, kick, dim, dt, _ptr(accel), every, _ptr(G)))
+
+
+def vp_fluxnet_line_map(fine: vp_grid, coarse: vp_grid, factor: int, kick: int, dim: int):
+    """Returns (map as a list of ints, n_coarse_lines, group)."""
+    n = ctypes.c_longlong()
+    g = ctypes.c_int()
+    L = load()
+    _rc(L.vp_fluxnet_line_map(ctypes.byref(fine), ctypes.byref(coarse), factor, kick, dim, None,
+                              ctypes.byref(n), ctypes.byref(g)), "line map")
+    arr = (ctypes.c_longlong * (n.value * g.value))()
+    _rc(L.vp_fluxnet_line_map(ctypes.byref(fine), ctypes.byref(coarse), factor, kick, dim,
+                              ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(n), ctypes.byref(g)), "line map")
+    return list(arr), n.value, g.value
+
+
+def vp_group_mean(G_fine, n_coarse_lines: int, nout: int, map_dev, group: int, scale: float, G_coarse,
+                  stream=None) -> None:
+    _rc(load().vp_group_mean(_ptr(G_fine), n_coarse_lines, nout, _ptr(map_dev), group, scale,
+                             _ptr(G_coarse), _sh(stream)), "group mean")
+
+
+def vp_restrict_velocity(f_fine, f_coarse, NX: int, nf1: int, nf2: int, factor1: int, factor2: int,
+                         stream=None) -> None:
+    _rc(load().vp_restrict_velocity(_ptr(f_fine), _ptr(f_coarse), NX, nf1, nf2, factor1, factor2,
+                                    _sh(stream)), "restrict")
+
+
+def vp_make_samples(ctx, kick: int, dim: int, dt: float, accel, Gc, zmin: float, X, y) -> None:
+    _check(ctx, load().vp_make_samples(ctx, kick, dim, dt, _ptr(accel), _ptr(Gc), zmin, _ptr(X), _ptr(y)))
+
+
+def vp_net_grad(X, y, nsamp: int, wts, grad, loss, stream=None) -> None:
+    _rc(load().vp_net_grad(_ptr(X), _ptr(y), nsamp, _ptr(wts), _ptr(grad), _ptr(loss), _sh(stream)),
+        "net grad")
+
+
+def vp_net_adam(wts, m, v, grad, step: int, lr: float, stream=None) -> None:
+    _rc(load().vp_net_adam(_ptr(wts), _ptr(m), _ptr(v), _ptr(grad), step, lr, _sh(stream)), "adam")
 
 
 # ---- convenience owner -----------------------------------------------------------

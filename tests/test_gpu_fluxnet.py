@@ -1,0 +1,202 @@
+"""Learned flux correction: training kernels against the FP64 reference,
+the learned sweep against the plain sweep and an oracle line update,
+conservation and positivity with the network on, the fine-flux extraction
+used to build training data, and what a trained network gains."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import flux_net as N
+from paper_1702_08521_gb300 import inputs
+from paper_1702_08521_gb300 import vlasov as V
+
+from gpu_helpers import both, from_gpu, rel_l1, rel_max, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _params(seed, scale=1.0):
+    p = N.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    for k in p:
+        p[k] = _f32(p[k] * scale + 0.02 * rng.normal(size=p[k].shape))
+    return p
+
+
+def test_net_gradients_match_reference():
+    import torch
+    rng = np.random.default_rng(0)
+    p = _params(1)
+    B = 1000
+    X = _f32(rng.normal(size=(B, N.NFEAT)))
+    y = _f32(rng.normal(size=B))
+    loss_ref, g_ref = N.loss_and_grad(p, X, y, round_bf16=True)
+    w = _t(N.pack(p), torch.float32)
+    grad = torch.zeros_like(w)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    V.vp_net_grad(_t(X.ravel(), torch.float32), _t(y, torch.float32), B, w, grad, loss)
+    torch.cuda.synchronize()
+    assert loss.item() == pytest.approx(loss_ref, rel=1e-4)
+    gv = grad.double().cpu().numpy()
+    rv = N.pack(g_ref)
+    assert np.abs(gv - rv).max() <= 1e-2 * np.abs(rv).max()
+    assert np.linalg.norm(gv - rv) <= 1e-3 * np.linalg.norm(rv)
+
+
+def test_adam_moves_against_the_gradient():
+    import torch
+    w = torch.zeros(V.VP_NET_NPARAM, dtype=torch.float32, device="cuda")
+    g = torch.linspace(-1, 1, V.VP_NET_NPARAM, device="cuda")
+    m, v = torch.zeros_like(w), torch.zeros_like(w)
+    g0 = g.clone()
+    V.vp_net_adam(w, m, v, g, 1, 1e-3)
+    torch.cuda.synchronize()
+    # first Adam step moves every parameter by -lr * g / (|g| + eps), i.e.
+    # -lr * sign(g) wherever |g| >> eps
+    nz = g0.abs() > 1e-4
+    assert torch.allclose(w[nz], -1e-3 * torch.sign(g0[nz]), rtol=1e-3, atol=1e-7)
+    assert torch.count_nonzero(g) == 0
+
+
+def _grid2d(nx, nv):
+    L = 4 * math.pi
+    return dict(dims=2, nx=[nx, nx], nv=[nv, nv], xlo=[0.0, 0.0], xhi=[L, L], vlo=[-6.0, -6.0],
+                vhi=[6.0, 6.0], order=7)
+
+
+def test_learned_sweep_without_net_is_the_plain_sweep():
+    import torch
+    g = _grid2d(8, 16)
+    sim, og = both(g, V.VP_F32)
+    f0 = inputs.random_f(og.NX * og.NV, seed=3).astype(np.float32)
+    acc = inputs.random_accel(og.NX, 2, seed=4, amax=3.0)
+    w = torch.zeros(V.VP_NET_NPARAM, dtype=torch.float32, device="cuda")
+    for kick in (0, 1):
+        for d in range(2):
+            to_gpu(sim, f0)
+            a = _t(acc[d])
+            if kick:
+                V.vp_kick_sweep(sim.ctx, d, 0.4, a)
+            else:
+                V.vp_drift_sweep(sim.ctx, d, 0.4)
+            ref = from_gpu(sim)
+            to_gpu(sim, f0)
+            V.vp_learned_sweep(sim.ctx, kick, d, 0.4, a, w, 0)
+            got = from_gpu(sim)
+            assert rel_max(got, ref) <= 1e-6, (kick, d)
+    sim.close()
+
+
+def _oracle_learned_line(line, s, p, bc):
+    """FP64 learned SL update of one line: CSL7 + s g, then MP, then PP (oracle)."""
+    L = line.size
+    n_int, zeta = O.shift_split(s)
+    sg = -1 if zeta < 0 else 1
+    nu = abs(zeta)
+
+    def val(k):
+        if bc == O.BC_PERIODIC:
+            return line[k % L]
+        return line[k] if 0 <= k < L else 0.0
+
+    def flux(q):  # upwind cell q of the shifted line, stencil in upwind order
+        u = np.array([val(q + sg * (k - 3)) for k in range(8)])
+        phi = O.csl_flux(7, nu, u[:7])
+        X, sc = N.features(u[None, :], np.array([nu]))
+        phi += sc[0] * N.forward(p, X)[0][0]
+        phi = O.mp_constraint(phi, u[:7], 4.0)
+        return O.pp_limiter(phi, u[3], u[4], nu)
+
+    out = np.empty(L)
+    for i in range(L):
+        out[i] = val(i - n_int) - nu * (flux(i - n_int) - flux(i - n_int - sg))
+    return out
+
+
+def test_learned_sweep_matches_oracle_line_update():
+    import torch
+    g = dict(dims=1, nx=[24], nv=[20], xlo=[0.0], xhi=[2.0], vlo=[-3.0], vhi=[3.0], order=7)
+    sim, og = both(g, V.VP_F32)
+    f0 = _f32(inputs.random_f(og.NX * og.NV, seed=5))
+    p = _params(7, scale=0.3)
+    w = _t(N.pack(p), torch.float32)
+    to_gpu(sim, f0)
+    V.vp_learned_sweep(sim.ctx, 0, 0, 0.37, None, w, 1)
+    got = from_gpu(sim).reshape(24, 20)
+    want = np.empty((24, 20))
+    f2 = f0.reshape(24, 20)
+    vc = og.v_centres(0)
+    for j in range(20):
+        s = vc[j] * 0.37 / (2.0 / 24)
+        want[:, j] = _oracle_learned_line(f2[:, j], s, p, O.BC_PERIODIC)
+    # FP32 sums vs FP64 sums can move a bfloat16 rounding by one step
+    assert rel_l1(got, want) <= 2e-3, rel_l1(got, want)
+    sim.close()
+
+
+def test_learned_sweep_conserves_mass_and_positivity():
+    import torch
+    g = _grid2d(8, 16)
+    sim, og = both(g, V.VP_F32)
+    f0 = (inputs.random_f(og.NX * og.NV, seed=9, zeros=0.4) ** 4).astype(np.float32)
+    p = _params(11, scale=3.0)  # a large, untrained correction
+    w = _t(N.pack(p), torch.float32)
+    to_gpu(sim, f0)
+    m0 = float(np.sum(f0, dtype=np.float64))
+    for _ in range(3):
+        for d in range(2):
+            V.vp_learned_sweep(sim.ctx, 0, d, 0.3, None, w, 1)
+    got = from_gpu(sim)
+    assert got.min() >= 0.0
+    assert abs(got.sum() - m0) / m0 <= 1e-6
+    sim.close()
+
+
+def test_fine_flux_reproduces_the_sweep():
+    import torch
+    g = _grid2d(8, 16)
+    sim, og = both(g, V.VP_F32)
+    f0 = inputs.random_f(og.NX * og.NV, seed=12).astype(np.float32)
+    acc = inputs.random_accel(og.NX, 2, seed=13, amax=8.0)
+    for kick, d in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        to_gpu(sim, f0)
+        a = _t(acc[d])
+        L = g["nv"][d] if kick else g["nx"][d]
+        nlines = og.NX * og.NV // L
+        G = torch.zeros(nlines * (L + 1), dtype=torch.float64, device="cuda")
+        V.vp_fine_flux(sim.ctx, kick, d, 0.55, a, 1, G)
+        if kick:
+            V.vp_kick_sweep(sim.ctx, d, 0.55, a)
+        else:
+            V.vp_drift_sweep(sim.ctx, d, 0.55)
+        ref = from_gpu(sim)
+        Gh = G.cpu().numpy().reshape(nlines, L + 1)
+        # rebuild f' = f + G_{i-1/2} - G_{i+1/2} along every line
+        shp = og.shape
+        axis = (2 + d) if kick else d
+        fl = np.moveaxis(f0.reshape(shp).astype(np.float64), axis, -1)
+        lines = fl.reshape(-1, L)
+        order = np.arange(np.prod(shp)).reshape(shp)
+        idx = np.moveaxis(order, axis, -1).reshape(-1, L)
+        # G rows follow the library's line order: [outer][inner]
+        outer = int(np.prod(shp[:axis]))
+        inner = int(np.prod(shp[axis + 1:]))
+        lib_first = (np.arange(outer)[:, None] * L * inner + np.arange(inner)[None, :]).ravel()
+        pos = {v: k for k, v in enumerate(idx[:, 0])}
+        rows = np.array([pos[v] for v in lib_first])
+        new = lines[rows] + Gh[:, :-1] - Gh[:, 1:]
+        got = np.empty(np.prod(shp))
+        got[idx[rows].ravel()] = new.ravel()
+        assert rel_max(got, ref) <= 1e-5, (kick, d, rel_max(got, ref))
+    sim.close()
