@@ -30,10 +30,11 @@ __device__ __forceinline__ T mid3(T a, T b, T c) {
     return fmax(fmin(a, b), fmin(fmax(a, b), c));
 }
 
-// Steps 4-7 of the MP constraint (taken only when step 3 rejects phi).
+// Steps 4-7 of the MP constraint (taken only when step 3 rejects phi).  The
+// median of step 7 is a clamp: both intervals of step 6 contain u0, so
+// f_min <= u0 <= f_max exactly.
 template <typename T>
 __device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
-    if (um1 == u0 && u0 == u1) return u0;  // every bound collapses onto u0
     const T back = u0 - um1;
     const T dm = um2 + u0 - T(2) * um1;  // curvature at the upwind neighbour
     const T dc = um1 + u1 - T(2) * u0;   // at the upwind cell
@@ -45,7 +46,7 @@ __device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T 
     const T flc = u0 + T(0.5) * back + (T(4) / T(3)) * m4m;
     const T lo = fmax(fmin(fmin(u0, u1), fmd), fmin(fmin(u0, ful), flc));
     const T hi = fmin(fmax(fmax(u0, u1), fmd), fmax(fmax(u0, ful), flc));
-    return mid3(phi, lo, hi);
+    return fmin(fmax(phi, lo), hi);
 }
 
 // MP constraint of phi at the interface between u0 (upwind) and u1.
@@ -114,18 +115,24 @@ template <typename T, int ORDER, bool FULL>
 __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
                                   T alpha, T two_nu, int mp, int pp) {
     T phi;
-    if (ORDER == 7) {
-        phi = sh.w[0] * um3;
-        phi = fma(sh.w[1], um2, phi);
+    if ((FULL || mp) && um1 == u0 && u0 == u1) {
+        // flat around the interface: every MP bound collapses onto u0, whatever
+        // the interpolated value (App. A steps 2-7), so skip computing it
+        phi = u0;
     } else {
-        phi = sh.w[1] * um2;
+        if (ORDER == 7) {
+            phi = sh.w[0] * um3;
+            phi = fma(sh.w[1], um2, phi);
+        } else {
+            phi = sh.w[1] * um2;
+        }
+        phi = fma(sh.w[2], um1, phi);
+        phi = fma(sh.w[3], u0, phi);
+        phi = fma(sh.w[4], u1, phi);
+        phi = fma(sh.w[5], u2, phi);
+        if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
+        if (FULL || mp) phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
     }
-    phi = fma(sh.w[2], um1, phi);
-    phi = fma(sh.w[3], u0, phi);
-    phi = fma(sh.w[4], u1, phi);
-    phi = fma(sh.w[5], u2, phi);
-    if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
-    if (FULL || mp) phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
     if (FULL || pp) phi = pp_limit(phi, u0, u1, two_nu);
     return phi;
 }

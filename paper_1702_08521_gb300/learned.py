@@ -139,8 +139,15 @@ def he_init(seed: int = 0):
 def train_net(X, y, iters: int = 1500, batch: int = 32768, lr: float = 2e-3, seed: int = 0, stream=None,
               w0=None):
     """Adam on the mean squared error over minibatches; returns (weights, losses).
-    w0: initial parameters (VP_NET_NPARAM floats, e.g. a He initialisation)."""
+    w0: initial parameters (VP_NET_NPARAM floats, e.g. a He initialisation).
+    Everything runs on the current torch stream (the minibatch gathers and
+    the library's kernels must be ordered); `stream` is accepted for symmetry
+    and waited on first."""
     import torch
+    cur = torch.cuda.current_stream()
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        cur.wait_stream(stream)
+    stream = cur
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     w = (w0 if w0 is not None else he_init(seed)).clone().float().cuda()
@@ -162,10 +169,37 @@ def train_net(X, y, iters: int = 1500, batch: int = 32768, lr: float = 2e-3, see
     return w, hist
 
 
-def coarse_run(grid: dict, ic, dt: float, steps: int, wts=None, stream=None):
-    """KDK run on `grid` with plain (wts None) or learned sweeps; returns the Simulation."""
-    sim = V.Simulation(grid, precision=V.VP_F32, stream=stream)
-    V.vp_init_f(sim.ctx, *ic)
+def restricted_initial_state(dims: int, nx: int, nv_fine: int, factor: int, k: float, alpha: float,
+                             stream=None):
+    """Coarse initial f as the mean of the fine point values (the state the
+    training pairs are built on); factor 1 gives the fine state itself."""
+    import torch
+    fine = V.Simulation(landau_grid(dims, nx, nv_fine, k), precision=V.VP_F32, stream=stream)
+    V.vp_init_f(fine.ctx, *_landau_ic(dims, k, alpha))
+    fine.sync()
+    if factor == 1:
+        out = fine.f.clone()
+    else:
+        NX = nx ** dims
+        nc = nv_fine // factor
+        out = torch.empty(NX * nc ** dims, dtype=torch.float32, device="cuda")
+        if dims == 2:
+            V.vp_restrict_velocity(fine.f, out, NX, nv_fine, nv_fine, factor, factor, stream)
+        else:
+            V.vp_restrict_velocity(fine.f, out, NX, nv_fine, 1, factor, 1, stream)
+    fine.sync()
+    fine.close()
+    return out
+
+
+def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision: int = V.VP_F32):
+    """KDK run on `grid` from the state f0 with plain sweeps, or with learned
+    velocity sweeps when wts is given; returns the Simulation (caller closes)."""
+    sim = V.Simulation(grid, precision=precision, stream=stream)
+    # f0 may still be in flight on the caller's stream
+    sim.stream.wait_stream(sim.torch.cuda.current_stream())
+    with sim.torch.cuda.stream(sim.stream):
+        sim.f.copy_(f0.to(sim.f.dtype))
     sim.field()
     dims = grid["dims"]
     for _ in range(steps):
