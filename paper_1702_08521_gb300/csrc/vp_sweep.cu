@@ -65,17 +65,27 @@ __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
     constexpr int VEC = 16 / sizeof(T);
     const int wv = W / VEC;
     if (wc == W && geo.inner % VEC == 0 && W % VEC == 0 && blockDim.x % wv == 0) {
+        // every 16-byte piece of the tile in flight at once (cp.async), so the
+        // staging is not limited by one outstanding load per thread
         const int cv = threadIdx.x % wv;
         const int rstep = blockDim.x / wv;
         const T *src = base + cv * VEC;
         T *dst = sm + W + cv * VEC;
         for (int r = threadIdx.x / wv; r < L; r += rstep)
-            *reinterpret_cast<float4 *>(dst + r * W) =
-                *reinterpret_cast<const float4 *>(src + (long long)r * geo.inner);
+            vp_tma::cp_async16(dst + r * W, src + (long long)r * geo.inner);
+        vp_tma::cp_async_wait_all();
     } else {
+        // row / column of element e advanced incrementally (no division per element)
+        const int dr = blockDim.x / W, dc = blockDim.x - dr * W;
+        int r = threadIdx.x / W, cc = threadIdx.x - r * W;
         for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
-            const int r = e / W, cc = e - r * W;
             sm[W + e] = cc < wc ? base[(long long)r * geo.inner + cc] : T(0);
+            r += dr;
+            cc += dc;
+            if (cc >= W) {
+                cc -= W;
+                ++r;
+            }
         }
     }
     __syncthreads();
@@ -115,18 +125,54 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     }
     constexpr int VEC = 16 / sizeof(T);
     const bool vec = (L % VEC) == 0;
+    // Element e = r L + pos of the tile: a thread starts at e = VEC t (or t)
+    // and advances by a fixed (rows, positions) step, so no division per element.
     if (vec) {
-        for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
+        constexpr int U = 4;  // 16-byte loads in flight per thread
+        const int st = blockDim.x * VEC;
+        const int dr = st / L, dp = st - dr * L;
+        int r = (threadIdx.x * VEC) / L, pos = threadIdx.x * VEC - r * L;
+        int e = threadIdx.x * VEC;
+        for (; e + (U - 1) * st < tot; e += U * st) {
+            float4 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[u] = *reinterpret_cast<const float4 *>(base + e + u * st);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const T *xv = reinterpret_cast<const T *>(&x[u]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) in[r * P + 1 + pos + k] = xv[k];
+                r += dr;
+                pos += dp;
+                if (pos >= L) {
+                    pos -= L;
+                    ++r;
+                }
+            }
+        }
+        for (; e < tot; e += st) {
             const float4 x = *reinterpret_cast<const float4 *>(base + e);
             const T *xv = reinterpret_cast<const T *>(&x);
-            const int r = e / L, pos = e - r * L;
 #pragma unroll
             for (int k = 0; k < VEC; ++k) in[r * P + 1 + pos + k] = xv[k];
+            r += dr;
+            pos += dp;
+            if (pos >= L) {
+                pos -= L;
+                ++r;
+            }
         }
     } else {
+        const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
+        int r = threadIdx.x / L, pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            const int r = e / L, pos = e - r * L;
             in[r * P + 1 + pos] = base[e];
+            r += dr;
+            pos += dp;
+            if (pos >= L) {
+                pos -= L;
+                ++r;
+            }
         }
     }
     __syncthreads();
@@ -143,18 +189,33 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     }
     __syncthreads();
     if (vec) {
-        for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
-            const int r = e / L, pos = e - r * L;
+        const int st = blockDim.x * VEC;
+        const int dr = st / L, dp = st - dr * L;
+        int r = (threadIdx.x * VEC) / L, pos = threadIdx.x * VEC - r * L;
+        for (int e = threadIdx.x * VEC; e < tot; e += st) {
             float4 x;
             T *xv = reinterpret_cast<T *>(&x);
 #pragma unroll
             for (int k = 0; k < VEC; ++k) xv[k] = out[r * Q + pos + k];
             *reinterpret_cast<float4 *>(base + e) = x;
+            r += dr;
+            pos += dp;
+            if (pos >= L) {
+                pos -= L;
+                ++r;
+            }
         }
     } else {
+        const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
+        int r = threadIdx.x / L, pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            const int r = e / L, pos = e - r * L;
             base[e] = out[r * Q + pos];
+            r += dr;
+            pos += dp;
+            if (pos >= L) {
+                pos -= L;
+                ++r;
+            }
         }
     }
 }
