@@ -53,17 +53,17 @@ __device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T 
 // Step 3 accepts phi iff it lies strictly between u0 and f* = u0 + minmod(p, q),
 // p = u1 - u0, q = alpha (u0 - u_{-1}); with a = phi - u0 that is: a strictly
 // between 0 and p and strictly between 0 and q, i.e. (p - a) a > 0 and
-// (q - a) a > 0 -- products on the FMA pipe instead of min/max chains.  A
-// product that underflows only sends the case to the exact test below.
+// (q - a) a > 0 -- products on the FMA pipe instead of min/max chains.  A phi
+// this test rejects goes to steps 4-7 directly: the interval [u0, f*] lies
+// inside [f_min, f_max] (f_min <= u0; f_max >= min(u1, f_UL) >= f* when the
+// minmod is positive, and the mirror case), so a phi that step 3 would have
+// accepted but whose product underflowed comes back unchanged from the clamp.
 template <typename T>
 __device__ __forceinline__ T mp_limit(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
     const T a = phi - u0;
     const T p = u1 - u0;
     const T q = alpha * (u0 - um1);
     if ((p - a) * a > T(0) && (q - a) * a > T(0)) return phi;
-    const T fstar = u0 + mm2(p, q);
-    const T b = fstar - phi;
-    if (fmin(a, b) > T(0) || fmax(a, b) < T(0)) return phi;
     return mp_bounds(phi, um2, um1, u0, u1, u2, alpha);
 }
 
@@ -157,35 +157,34 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, co
     const T two_nu = T(2) * nu;
     int i = sg > 0 ? r0 : r1 - 1;
     const int cnt = r1 - r0;
-    int p;  // source row of the next value to enter the window
+    // Source row of load k (k = 0, 1, ...) is p0 + k sg; load k feeds step
+    // k - 8 of the walk.  Zero-inflow lines read rows outside [-1, L] as the
+    // ghost row on that side; periodic lines wrap.
+    int p0;
     if (PERIODIC) {
-        int n = sh.n % L;
-        p = (i - n - 4 * sg) % L;
-        if (p < 0) p += L;
+        const int n = sh.n % L;
+        p0 = (i - n - 4 * sg) % L;
+        if (p0 < 0) p0 += L;
     } else {
-        p = i - sh.n - 4 * sg;
+        p0 = i - sh.n - 4 * sg;
     }
-    auto load = [&](int q) -> T {
-        if (!PERIODIC) q = min(max(q, -1), L);
-        return sm[(q + PAD) * ss];
-    };
-    auto advance = [&]() {
-        p += sg;
+    auto row = [&](int q) -> const T * {
         if (PERIODIC) {
-            if (p >= L) p -= L;
-            if (p < 0) p += L;
+            q %= L;
+            if (q < 0) q += L;
+        } else {
+            q = min(max(q, -1), L);
         }
+        return sm + (q + PAD) * ss;
     };
     T w[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        w[k] = load(p);
-        advance();
-    }
+    for (int k = 0; k < 8; ++k) w[k] = *row(p0 + k * sg);
     // incoming flux of the first cell: upwind cell i - sg, stencil w[0..6]
     T fin = flux<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, two_nu, mp, pp);
 
-    // one cell with the window rotated by K (u_k at w[(K + 4 + k) & 7])
+    // one cell with the window rotated by K (u_k at w[(K + 4 + k) & 7]); the
+    // next value enters from *src, which then moves by inc
 #define VP_WALK_STEP(K)                                                                           \
     {                                                                                             \
         const T fout = flux<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7], w[(K + 3) & 7],   \
@@ -194,18 +193,37 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, co
         store(i, w[(K + 4) & 7] - nu * (fout - fin));                                             \
         fin = fout;                                                                               \
         i += sg;                                                                                  \
-        w[K & 7] = load(p);                                                                       \
-        p += sg;                                                                                  \
+        w[K & 7] = *src;                                                                          \
+        src += inc;                                                                               \
     }
 
+    // The walk runs in chunks over which the load pointer moves uniformly:
+    // inside the line it steps one row per cell; on a ghost it stays put.
     int t = 0;
     while (t < cnt) {
-        int end = cnt;
+        const int k = t + 8;  // index of the next load
+        const int q = p0 + k * sg;
+        const T *src;
+        int inc, end;
         if (PERIODIC) {
-            // loads stay inside [0, L) for this many steps
-            const int room = sg > 0 ? L - p : p + 1;
-            end = t + room < cnt ? t + room : cnt;
+            const int qq = ((q % L) + L) % L;
+            src = sm + qq * ss;
+            inc = sg * ss;
+            const int room = sg > 0 ? L - qq : qq + 1;  // loads before the wrap
+            end = t + room;
+        } else if (q < -1 || q > L) {
+            // on a ghost: stays there until the source row comes back inside
+            src = row(q);
+            inc = 0;
+            const int back = sg > 0 ? -1 - q : q - L;  // loads until row -1 / L
+            end = back > 0 ? t + back : cnt;
+        } else {
+            src = sm + (q + PAD) * ss;
+            inc = sg * ss;
+            const int room = sg > 0 ? L + 1 - q : q + 2;  // loads through the far ghost
+            end = t + room;
         }
+        if (end > cnt) end = cnt;
         for (; t + 8 <= end; t += 8) {
             VP_WALK_STEP(0)
             VP_WALK_STEP(1)
@@ -221,12 +239,8 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, co
             // restore the canonical order (u_-4 in w[0])
             const T w0 = w[0];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) w[k] = w[k + 1];
+            for (int kk = 0; kk < 7; ++kk) w[kk] = w[kk + 1];
             w[7] = w0;
-        }
-        if (PERIODIC) {
-            if (p >= L) p -= L;
-            if (p < 0) p += L;
         }
     }
 #undef VP_WALK_STEP
