@@ -135,8 +135,7 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
                 p += step;
             }
         } st{base + cc + (long long)i0 * s.inner, (long long)sh.sigma * s.inner};
-        vp_core::walk<float, ORDER, PER, true>(sm + (PER ? W : 0) + cc, W, L, sh, r0, r1, (float)P.alpha, P.mp,
-                                         P.pp, st);
+        vp_core::walk<float, ORDER, PER, true, 1>(sm + W + cc, W, L, sh, r0, r1, (float)P.alpha, P.mp, P.pp, st);
     }
 }
 
@@ -176,7 +175,8 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
                 p += step;
             }
         } st{out + line * Q + i0, sh.sigma};
-        vp_core::walk<float, ORDER, false, true>(in + line * Pp, 1, L, sh, r0, r1, (float)P.alpha, P.mp, P.pp, st);
+        vp_core::walk<float, ORDER, false, true, 1>(in + line * Pp + 1, 1, L, sh, r0, r1, (float)P.alpha, P.mp,
+                                                    P.pp, st);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {

@@ -22,6 +22,34 @@ struct __align__(16) LineShift {
 };
 
 // Geometry of one sweep: f viewed as [outer][L][inner].
+// Division of 32-bit unsigned values by a divisor fixed before the launch
+// (Granlund & Montgomery 1994, Fig. 4.1): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (t + ((n - t) >> s1)) >> s2
+// where t = high word of m n, s1 = min(l, 1), s2 = max(l - 1, 0).
+struct FastDiv {
+    unsigned d, m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f) {
+    const unsigned t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+__device__ __forceinline__ unsigned fmod_u(unsigned n, const FastDiv &f) { return n - fdiv(n, f) * f.d; }
+#endif
+
 struct SweepGeo {
     long long outer, inner;
     int L;
@@ -31,7 +59,14 @@ struct SweepGeo {
     long long cdiv, cmod;
     // column-kernel tile (W columns x full line), row-kernel lines per CTA
     int W, nseg, R;
+    // divisors of the launch: cdiv, cmod, tiles per outer index, W (or R), nseg
+    FastDiv fd_cdiv, fd_cmod, fd_tpo, fd_w, fd_nseg;
+    unsigned tpo;
 };
+
+// zero rows staged on each side of an outflow line (a shift |n| <= VP_GHOST - 4
+// walks the line without bounds handling)
+#define VP_GHOST 8
 
 // tile configuration of one sweep geometry (chosen by the autotuner)
 struct SweepTune {

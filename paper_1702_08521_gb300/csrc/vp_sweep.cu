@@ -44,42 +44,49 @@ struct PtrStore {
     }
 };
 
-// staged-load strided sweep: tile = W columns x the whole line, rows 1..L of
-// a [(L + 2)][W] shared tile (rows 0 and L + 1 are the zero ghosts)
+// staged-load strided sweep: tile = W columns x the whole line, staged as
+// rows GP..GP+L-1 of a [(L + 2 GP)][W] shared tile; zero-inflow lines get GP =
+// VP_GHOST zero rows on each side, periodic lines none
 template <typename T, int ORDER, bool PERIODIC, bool FULL>
 __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
                                                     const LineShift<T> *__restrict__ tab,
                                                     SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int GP = PERIODIC ? 0 : VP_GHOST;
     T *sm = reinterpret_cast<T *>(smraw);
     const int W = geo.W, L = geo.L;
-    const unsigned tpo = (unsigned)((geo.inner + W - 1) / W);
-    const unsigned o = blockIdx.x / tpo;
-    const unsigned c0 = (blockIdx.x - o * tpo) * (unsigned)W;
+    const unsigned o = fdiv(blockIdx.x, geo.fd_tpo);
+    const unsigned c0 = (blockIdx.x - o * geo.tpo) * (unsigned)W;
     const int wc = (int)((geo.inner - c0) < W ? (geo.inner - c0) : W);
     T *base = f + (long long)o * L * geo.inner + c0;
-    for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        sm[c] = T(0);
-        sm[(L + 1) * W + c] = T(0);
+    T *data = sm + GP * W;  // row 0 of the line
+    for (int e = threadIdx.x; e < GP * W; e += blockDim.x) {
+        sm[e] = T(0);
+        data[L * W + e] = T(0);
     }
     constexpr int VEC = 16 / sizeof(T);
     const int wv = W / VEC;
     if (wc == W && geo.inner % VEC == 0 && W % VEC == 0 && blockDim.x % wv == 0) {
         // every 16-byte piece of the tile in flight at once (cp.async), so the
         // staging is not limited by one outstanding load per thread
-        const int cv = threadIdx.x % wv;
+        const int r = threadIdx.x / wv;
+        const int cv = threadIdx.x - r * wv;
         const int rstep = blockDim.x / wv;
-        const T *src = base + cv * VEC;
-        T *dst = sm + W + cv * VEC;
-        for (int r = threadIdx.x / wv; r < L; r += rstep)
-            vp_tma::cp_async16(dst + r * W, src + (long long)r * geo.inner);
+        const T *src = base + (long long)r * geo.inner + cv * VEC;
+        T *dst = data + r * W + cv * VEC;
+        const long long sstep = (long long)rstep * geo.inner;
+        for (int rr = r; rr < L; rr += rstep) {
+            vp_tma::cp_async16(dst, src);
+            src += sstep;
+            dst += rstep * W;
+        }
         vp_tma::cp_async_wait_all();
     } else {
         // row / column of element e advanced incrementally (no division per element)
         const int dr = blockDim.x / W, dc = blockDim.x - dr * W;
         int r = threadIdx.x / W, cc = threadIdx.x - r * W;
         for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
-            sm[W + e] = cc < wc ? base[(long long)r * geo.inner + cc] : T(0);
+            data[e] = cc < wc ? base[(long long)r * geo.inner + cc] : T(0);
             r += dr;
             cc += dc;
             if (cc >= W) {
@@ -89,16 +96,16 @@ __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
         }
     }
     __syncthreads();
-    const int cc = threadIdx.x % W;
-    const int seg = threadIdx.x / W;
-    if (cc < wc && seg < geo.nseg) {
+    const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
+    const int cc = (int)(threadIdx.x - seg * (unsigned)W);
+    if (cc < wc && (int)seg < geo.nseg) {
         const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
-        const int r0 = seg * L / geo.nseg;
-        const int r1 = (seg + 1) * L / geo.nseg;
+        const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+        const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         PtrStore<T> st{base + cc + (long long)i0 * geo.inner, (long long)sh.sigma * geo.inner};
-        walk<T, ORDER, PERIODIC, FULL>(sm + (PERIODIC ? W : 0) + cc, W, L, sh, r0, r1, (T)lp.alpha, lp.mp,
-                                 lp.pp, st);
+        walk<T, ORDER, PERIODIC, FULL, PERIODIC ? 1 : VP_GHOST>(data + cc, W, L, sh, r0, r1, (T)lp.alpha,
+                                                                 lp.mp, lp.pp, st);
     }
 }
 
@@ -110,8 +117,9 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
                                                     const LineShift<T> *__restrict__ tab,
                                                     SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int GP = PERIODIC ? 0 : VP_GHOST;
     const int L = geo.L, R = geo.R;
-    const int P = (L + 2) | 1;
+    const int P = (L + 2 * GP) | 1;
     const int Q = L | 1;
     T *in = reinterpret_cast<T *>(smraw);
     T *out = in + R * P;
@@ -119,9 +127,13 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     const int nl = (int)((geo.outer - l0) < R ? (geo.outer - l0) : R);
     T *base = f + l0 * L;
     const int tot = nl * L;
-    for (int r = threadIdx.x; r < nl; r += blockDim.x) {
-        in[r * P] = T(0);
-        in[r * P + L + 1] = T(0);
+    if (GP > 0) {
+        constexpr int G = GP > 0 ? GP : 1;
+        for (int e = threadIdx.x; e < nl * G; e += blockDim.x) {
+            const int r = e / G, k = e - r * G;
+            in[r * P + k] = T(0);
+            in[r * P + G + L + k] = T(0);
+        }
     }
     constexpr int VEC = 16 / sizeof(T);
     const bool vec = (L % VEC) == 0;
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
             for (int u = 0; u < U; ++u) {
                 const T *xv = reinterpret_cast<const T *>(&x[u]);
 #pragma unroll
-                for (int k = 0; k < VEC; ++k) in[r * P + 1 + pos + k] = xv[k];
+                for (int k = 0; k < VEC; ++k) in[r * P + GP + pos + k] = xv[k];
                 r += dr;
                 pos += dp;
                 if (pos >= L) {
@@ -154,7 +166,7 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
             const float4 x = *reinterpret_cast<const float4 *>(base + e);
             const T *xv = reinterpret_cast<const T *>(&x);
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) in[r * P + 1 + pos + k] = xv[k];
+            for (int k = 0; k < VEC; ++k) in[r * P + GP + pos + k] = xv[k];
             r += dr;
             pos += dp;
             if (pos >= L) {
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
         int r = threadIdx.x / L, pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            in[r * P + 1 + pos] = base[e];
+            in[r * P + GP + pos] = base[e];
             r += dr;
             pos += dp;
             if (pos >= L) {
@@ -176,16 +188,16 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         }
     }
     __syncthreads();
-    const int line = threadIdx.x % R;
-    const int seg = threadIdx.x / R;
-    if (line < nl && seg < geo.nseg) {
+    const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
+    const int line = (int)(threadIdx.x - seg * (unsigned)R);
+    if (line < nl && (int)seg < geo.nseg) {
         const LineShift<T> sh = tab[line_class(geo, (unsigned)(l0 + line), 0u)];
-        const int r0 = seg * L / geo.nseg;
-        const int r1 = (seg + 1) * L / geo.nseg;
+        const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+        const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         PtrStore<T> st{out + line * Q + i0, (long long)sh.sigma};
-        walk<T, ORDER, PERIODIC, FULL>(in + line * P + (PERIODIC ? 1 : 0), 1, L, sh, r0, r1, (T)lp.alpha,
-                                 lp.mp, lp.pp, st);
+        walk<T, ORDER, PERIODIC, FULL, PERIODIC ? 1 : VP_GHOST>(in + line * P + GP, 1, L, sh, r0, r1,
+                                                                 (T)lp.alpha, lp.mp, lp.pp, st);
     }
     __syncthreads();
     if (vec) {
@@ -229,31 +241,32 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
     extern __shared__ __align__(128) unsigned char smraw_tma[];
     unsigned char *smraw = smraw_tma;
     __shared__ __align__(8) uint64_t bar[2];
+    constexpr int GP = PERIODIC ? 0 : VP_GHOST;
     const int W = geo.W, L = geo.L;
-    const int itile = (L + 2) * W;  // input stage: zero row, L rows, zero row
+    const int itile = (L + 2 * GP) * W;  // input stage: GP zero rows, L rows, GP zero rows
     const int otile = L * W;
     // TMA tensor copies need 128-byte aligned shared-memory buffers: align
     // the dynamic region explicitly (the launch reserves 128 spare bytes)
     const uint32_t sbase = vp_tma::saddr(smraw);
     const uint32_t pad = (128u - (sbase & 127u)) & 127u;
-    T *in_buf = reinterpret_cast<T *>(smraw + pad);  // [2][L + 2][W]
+    T *in_buf = reinterpret_cast<T *>(smraw + pad);  // [2][L + 2 GP][W]
     T *out_buf = in_buf + 2 * itile;                  // [2][L][W]
-    const unsigned tpo = (unsigned)((geo.inner + W - 1) / W);
+    const unsigned tpo = geo.tpo;
     const unsigned ntiles = (unsigned)geo.outer * tpo;
     const uint32_t bytes = (uint32_t)(otile * sizeof(T));
     // self-check of every alignment the copies rely on; on failure report and
     // leave before issuing any copy
-    if (((vp_tma::saddr(in_buf + W) | vp_tma::saddr(in_buf + itile + W) | vp_tma::saddr(out_buf) |
+    if (((vp_tma::saddr(in_buf + GP * W) | vp_tma::saddr(in_buf + itile + GP * W) | vp_tma::saddr(out_buf) |
           vp_tma::saddr(out_buf + otile)) & 127u) != 0 ||
         ((W * sizeof(T)) & 127u) != 0) {
         if (threadIdx.x == 0) atomicExch(status, VP_EINVAL);
         return;
     }
-    for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        in_buf[c] = T(0);
-        in_buf[(L + 1) * W + c] = T(0);
-        in_buf[itile + c] = T(0);
-        in_buf[itile + (L + 1) * W + c] = T(0);
+    for (int e = threadIdx.x; e < GP * W; e += blockDim.x) {
+        in_buf[e] = T(0);
+        in_buf[(GP + L) * W + e] = T(0);
+        in_buf[itile + e] = T(0);
+        in_buf[itile + (GP + L) * W + e] = T(0);
     }
     if (threadIdx.x == 0) {
         vp_tma::mbar_init(&bar[0], 1);
@@ -266,15 +279,15 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
             const unsigned t = blockIdx.x + (unsigned)s * gridDim.x;
             if (t < ntiles) {
                 vp_tma::mbar_expect_tx(&bar[s], bytes);
-                vp_tma::load_3d(in_buf + s * itile + W, &tmap, &bar[s], (int)((t % tpo) * W), 0,
+                vp_tma::load_3d(in_buf + s * itile + GP * W, &tmap, &bar[s], (int)((t % tpo) * W), 0,
                                 (int)(t / tpo));
             }
         }
     }
-    const int cc = threadIdx.x % W;
-    const int seg = threadIdx.x / W;
-    const int r0 = seg * L / geo.nseg;
-    const int r1 = (seg + 1) * L / geo.nseg;
+    const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
+    const int cc = (int)(threadIdx.x - seg * (unsigned)W);
+    const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+    const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
     int k = 0;
     for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int s = k & 1;
@@ -289,15 +302,15 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
             }
             return;
         }
-        const unsigned o = t / tpo;
+        const unsigned o = fdiv(t, geo.fd_tpo);
         const unsigned c0 = (t - o * tpo) * (unsigned)W;
         const int wc = (int)((geo.inner - c0) < W ? (geo.inner - c0) : W);
-        if (cc < wc && seg < geo.nseg) {
+        if (cc < wc && (int)seg < geo.nseg) {
             const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
             const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
             PtrStore<T> st{out + cc + i0 * W, (long long)sh.sigma * W};
-            walk<T, ORDER, PERIODIC, FULL>(in + (PERIODIC ? W : 0) + cc, W, L, sh, r0, r1, (T)lp.alpha,
-                                     lp.mp, lp.pp, st);
+            walk<T, ORDER, PERIODIC, FULL, PERIODIC ? 1 : VP_GHOST>(in + GP * W + cc, W, L, sh, r0, r1,
+                                                                     (T)lp.alpha, lp.mp, lp.pp, st);
         }
         vp_tma::fence_async_smem();
         __syncthreads();
@@ -307,7 +320,8 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
             const unsigned tn = t + 2u * gridDim.x;
             if (tn < ntiles) {
                 vp_tma::mbar_expect_tx(&bar[s], bytes);
-                vp_tma::load_3d(in + W, &tmap, &bar[s], (int)((tn % tpo) * W), 0, (int)(tn / tpo));
+                const unsigned on = fdiv(tn, geo.fd_tpo);
+                vp_tma::load_3d(in + GP * W, &tmap, &bar[s], (int)((tn - on * tpo) * W), 0, (int)on);
             }
             vp_tma::wait_read<1>();  // the other output tile is free again
         }
@@ -398,6 +412,8 @@ SweepGeo make_geo(const vp_ctx *c, int kick, int dim) {
         geo.cdiv = vouter;
         geo.cmod = 1;
     }
+    geo.fd_cdiv = make_fastdiv((unsigned)geo.cdiv);
+    geo.fd_cmod = make_fastdiv((unsigned)geo.cmod);
     return geo;
 }
 
@@ -417,9 +433,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+// ghost rows staged on each side of a line
+inline int ghost_rows(const SweepGeo &geo) { return geo.periodic ? 0 : VP_GHOST; }
+
 template <typename T>
-size_t tma_smem(int L, int W) {
-    return (size_t)(2 * (L + 2) * W + 2 * L * W) * sizeof(T) + 128;
+size_t tma_smem(int L, int W, int gp) {
+    return (size_t)(2 * (L + 2 * gp) * W + 2 * L * W) * sizeof(T) + 128;
 }
 
 template <typename T>
@@ -427,13 +446,17 @@ bool tma_eligible(const vp_ctx *c, const SweepGeo &geo, int W) {
     constexpr int VEC = 16 / sizeof(T);
     return geo.inner > 1 && geo.inner % VEC == 0 && W % VEC == 0 && geo.inner < (1LL << 31) &&
            geo.outer < (1LL << 31) && geo.L <= 256 && W <= 256 &&
-           (W * sizeof(T)) % 128 == 0 && tma_smem<T>(geo.L, W) <= 200 * 1024 &&
+           (W * sizeof(T)) % 128 == 0 && tma_smem<T>(geo.L, W, ghost_rows(geo)) <= 200 * 1024 &&
            tensor_map_encoder() != nullptr &&
            (reinterpret_cast<uintptr_t>(c->f) & 15) == 0;
 }
 
+// line classes and tile coordinates are computed in 32-bit arithmetic
+inline bool geo_fits_32(const SweepGeo &geo) { return geo.outer < (1LL << 32) && geo.inner < (1LL << 32); }
+
 template <typename T>
 int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
+    if (!geo_fits_32(geo)) return vp_fail(c, VP_ENOTSUP, "sweep geometry exceeds 32-bit line indexing");
     const LineShift<T> *tab = static_cast<const LineShift<T> *>(c->d_shift);
     const LimParams lp{c->g.alpha, c->g.mp, c->g.pp};
     T *f = static_cast<T *>(c->f);
@@ -445,6 +468,10 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     const int threads = ((W * tu.nseg + 31) / 32) * 32;
     const long long tiles = geo.outer * ((geo.inner + W - 1) / W);
     if (tiles >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
+    geo.tpo = (unsigned)((geo.inner + W - 1) / W);
+    geo.fd_tpo = make_fastdiv(geo.tpo);
+    geo.fd_w = make_fastdiv((unsigned)W);
+    geo.fd_nseg = make_fastdiv((unsigned)tu.nseg);
     const int order = c->g.order;
     const bool per = geo.periodic != 0;
     const bool full = c->g.mp && c->g.pp;
@@ -461,7 +488,7 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
                                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return vp_fail(c, VP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-        const size_t smem = tma_smem<T>(L, W);
+        const size_t smem = tma_smem<T>(L, W, ghost_rows(geo));
         int per_sm = tu.ctas_per_sm;
         if (per_sm <= 0) {
 #define VP_OCC(O, P, F) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_cols_tma<T, O, P, F>, threads, smem)
@@ -476,7 +503,7 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
         VP_DISPATCH(order, per, full, VP_LAUNCH);
 #undef VP_LAUNCH
     } else {
-        const size_t smem = (size_t)(L + 2) * W * sizeof(T);
+        const size_t smem = (size_t)(L + 2 * ghost_rows(geo)) * W * sizeof(T);
         if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
 #define VP_LAUNCH(O, P, F) k_sweep_cols<T, O, P, F><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp)
         VP_DISPATCH(order, per, full, VP_LAUNCH);
@@ -488,12 +515,13 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
 }
 
 template <typename T>
-size_t rows_smem(int L, int R) {
-    return (size_t)R * (((L + 2) | 1) + (L | 1)) * sizeof(T);
+size_t rows_smem(int L, int R, int gp) {
+    return (size_t)R * (((L + 2 * gp) | 1) + (L | 1)) * sizeof(T);
 }
 
 template <typename T>
 int launch_rows(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
+    if (!geo_fits_32(geo)) return vp_fail(c, VP_ENOTSUP, "sweep geometry exceeds 32-bit line indexing");
     const LineShift<T> *tab = static_cast<const LineShift<T> *>(c->d_shift);
     const LimParams lp{c->g.alpha, c->g.mp, c->g.pp};
     T *f = static_cast<T *>(c->f);
@@ -502,9 +530,11 @@ int launch_rows(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     if (geo.outer < R) R = (int)geo.outer;
     geo.R = R;
     geo.nseg = tu.nseg;
+    geo.fd_w = make_fastdiv((unsigned)R);
+    geo.fd_nseg = make_fastdiv((unsigned)tu.nseg);
     const long long blocks = (geo.outer + R - 1) / R;
     if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
-    const size_t smem = rows_smem<T>(L, R);
+    const size_t smem = rows_smem<T>(L, R, ghost_rows(geo));
     if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
     const int threads = ((R * tu.nseg + 31) / 32) * 32;
     const bool per = geo.periodic != 0;
@@ -588,7 +618,7 @@ int tune_t(vp_ctx *c, int kick, int dim) {
             for (int nseg = 1; nseg <= 8; nseg *= 2) {
                 const int th = R * nseg;
                 if (th < 64 || th > 512 || nseg > geo.L) continue;
-                if (rows_smem<T>(geo.L, R) > 200 * 1024) continue;
+                if (rows_smem<T>(geo.L, R, ghost_rows(geo)) > 200 * 1024) continue;
                 if (nc < 32) cand[nc++] = SweepTune{1, 1, R, nseg, 0};
             }
     }

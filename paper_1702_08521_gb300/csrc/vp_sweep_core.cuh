@@ -30,6 +30,57 @@ __device__ __forceinline__ T mid3(T a, T b, T c) {
     return fmax(fmin(a, b), fmin(fmax(a, b), c));
 }
 
+// min / max of three (one three-input instruction in FP32 on sm_100 and later)
+__device__ __forceinline__ float min3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+
+// curvature d_j = u_{j-1} - 2 u_j + u_{j+1} (App. A)
+template <typename T>
+__device__ __forceinline__ T curv(T um, T u, T up) {
+    return (um + up) - T(2) * u;
+}
+
+// d^{M4} between cells with curvatures x and y (App. A):
+// minmod(4x - y, 4y - x, x, y).  With mn / mx the least / greatest of the
+// four, the minmod is mn if mn > 0, mx if mx < 0, else 0: the clamp of 0 into
+// [mn, mx].
+template <typename T>
+__device__ __forceinline__ T dm4(T x, T y) {
+    const T a = T(4) * x - y;
+    const T b = T(4) * y - x;
+    const T mn = min3(a, b, fmin(x, y));
+    const T mx = max3(a, b, fmax(x, y));
+    return fmin(fmax(T(0), mn), mx);
+}
+
+// The MP constraint as one clamp.  Steps 4-7 give phi_MP = median(phi, f_min,
+// f_max); step 3 keeps phi when it lies strictly between u0 and f^MP, and
+// that interval lies inside [f_min, f_max] (f_min <= u0; when the minmod of
+// step 2 is positive f_max >= min(u1, f_UL) = f^MP, and the mirror case), so
+// there the clamp returns phi as well.  Hence the constraint equals the clamp
+// of phi into [f_min, f_max] for every phi.  m4m / m4p are d^{M4} at the
+// upwind / downwind face of the upwind cell u0.
+template <typename T>
+__device__ __forceinline__ T mp_clamp(T phi, T um1, T u0, T u1, T alpha, T m4m, T m4p) {
+    const T back = u0 - um1;
+    const T ful = u0 + alpha * back;
+    const T fmd = T(0.5) * (u0 + u1) - T(0.5) * m4p;
+    const T flc = u0 + T(0.5) * back + (T(4) / T(3)) * m4m;
+    const T lo = fmax(min3(u0, u1, fmd), min3(u0, ful, flc));
+    const T hi = fmin(max3(u0, u1, fmd), max3(u0, ful, flc));
+    return fmin(fmax(phi, lo), hi);
+}
+
 // Steps 4-7 of the MP constraint (taken only when step 3 rejects phi).  The
 // median of step 7 is a clamp: both intervals of step 6 contain u0, so
 // f_min <= u0 <= f_max exactly.
@@ -137,29 +188,53 @@ __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T
     return phi;
 }
 
+// Interface flux for the line walker: the CSL interpolant, the MP constraint
+// as a clamp (no branch) with d^{M4} at both faces of u0 passed in, then PP.
+template <typename T, int ORDER, bool FULL>
+__device__ __forceinline__ T flux_walk(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
+                                       T alpha, T two_nu, int mp, int pp, T m4m, T m4p) {
+    T phi;
+    if (ORDER == 7) {
+        phi = sh.w[0] * um3;
+        phi = fma(sh.w[1], um2, phi);
+    } else {
+        phi = sh.w[1] * um2;
+    }
+    phi = fma(sh.w[2], um1, phi);
+    phi = fma(sh.w[3], u0, phi);
+    phi = fma(sh.w[4], u1, phi);
+    phi = fma(sh.w[5], u2, phi);
+    if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
+    if (FULL || mp) phi = mp_clamp(phi, um1, u0, u1, alpha, m4m, m4p);
+    if (FULL || pp) phi = pp_limit(phi, u0, u1, two_nu);
+    return phi;
+}
+
 // ---- line walker ---------------------------------------------------------------
 //
-// Advance cells [r0, r1) of one line staged in shared memory.  Row r of the
-// line is at sm[(r + PAD) * ss] with PAD = 1 for zero-inflow lines, whose
-// rows -1 and L hold zeros: reads outside the line are clamped onto them.
-// Periodic lines (PAD = 0) wrap; the walk is split into wrap-free chunks.
+// Advance cells [r0, r1) of one line staged in shared memory; row r of the
+// line is at sm0[r * ss].  Zero-inflow lines have GP >= 1 zero rows on each
+// side (rows -GP..-1 and L..L+GP-1); periodic lines wrap.
 // The walk goes upwind -> downwind so that each interface flux is computed
 // once; the 8-cell stencil window rotates through registers (unrolled by 8).
-// store(i, v) writes the new value of cell i.
+// The curvature of the upwind cell and d^{M4} at its upwind face carry over
+// from one interface to the next, so each interface adds one curvature and
+// one d^{M4}.  Where every active lane of a warp sits on a flat stencil
+// (u_{-1} = u_0 = u_1) the flux is u_0 exactly (all MP bounds collapse onto
+// u_0, d^{M4} at the downwind face is 0, the PP limiter keeps it) and the
+// warp skips the arithmetic.  store(i, v) writes the new value of cell i.
 
-template <typename T, int ORDER, bool PERIODIC, bool FULL, typename Store>
-__device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, const LineShift<T> &sh,
+template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, typename Store>
+__device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, const LineShift<T> &sh,
                                      int r0, int r1, T alpha, int mp, int pp, Store store) {
     if (r0 >= r1) return;
-    constexpr int PAD = PERIODIC ? 0 : 1;
     const int sg = sh.sigma;
     const T nu = sh.nu;
     const T two_nu = T(2) * nu;
     int i = sg > 0 ? r0 : r1 - 1;
     const int cnt = r1 - r0;
     // Source row of load k (k = 0, 1, ...) is p0 + k sg; load k feeds step
-    // k - 8 of the walk.  Zero-inflow lines read rows outside [-1, L] as the
-    // ghost row on that side; periodic lines wrap.
+    // k - 8 of the walk.
     int p0;
     if (PERIODIC) {
         const int n = sh.n % L;
@@ -168,6 +243,10 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, co
     } else {
         p0 = i - sh.n - 4 * sg;
     }
+    // A zero-inflow line whose shift keeps every load inside the staged zero
+    // rows walks with a plain pointer; otherwise the loads are handled in
+    // chunks (ghost rows, wrap-around).
+    const bool direct = !PERIODIC && GP >= 5 && sh.n <= GP - 4 && sh.n >= 4 - GP;
     auto row = [&](int q) -> const T * {
         if (PERIODIC) {
             q %= L;
@@ -175,21 +254,64 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, co
         } else {
             q = min(max(q, -1), L);
         }
-        return sm + (q + PAD) * ss;
+        return sm0 + q * ss;
     };
+    const T *src = sm0 + p0 * ss;
+    int inc = sg * ss;
     T w[8];
+    if (direct) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = *row(p0 + k * sg);
+        for (int k = 0; k < 8; ++k) {
+            w[k] = *src;
+            src += inc;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = *row(p0 + k * sg);
+    }
     // incoming flux of the first cell: upwind cell i - sg, stencil w[0..6]
-    T fin = flux<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, two_nu, mp, pp);
+    T dc = T(0), m4m = T(0);  // curvature at the next upwind cell, d^{M4} at its upwind face
+    T m4p = T(0);
+    if (FULL || mp) {
+        const T dm = curv(w[1], w[2], w[3]);
+        dc = curv(w[2], w[3], w[4]);
+        const T dp = curv(w[3], w[4], w[5]);
+        m4m = dm4(dm, dc);
+        m4p = dm4(dc, dp);
+    }
+    T fin = flux_walk<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, two_nu, mp, pp,
+                                      m4m, m4p);
+    if (FULL || mp) {
+        dc = curv(w[3], w[4], w[5]);
+        m4m = m4p;
+    }
 
     // one cell with the window rotated by K (u_k at w[(K + 4 + k) & 7]); the
     // next value enters from *src, which then moves by inc
 #define VP_WALK_STEP(K)                                                                           \
     {                                                                                             \
-        const T fout = flux<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7], w[(K + 3) & 7],   \
-                                      w[(K + 4) & 7], w[(K + 5) & 7], w[(K + 6) & 7],             \
-                                      w[(K + 7) & 7], alpha, two_nu, mp, pp);                     \
+        T fout;                                                                                   \
+        if (FULL || mp) {                                                                         \
+            const T u0_ = w[(K + 4) & 7], u1_ = w[(K + 5) & 7];                                   \
+            const T dp = curv(u0_, u1_, w[(K + 6) & 7]);                                          \
+            const bool flat = w[(K + 3) & 7] == u0_ && u0_ == u1_;                                \
+            if (__all_sync(__activemask(), flat)) {                                               \
+                fout = u0_;                                                                       \
+                m4m = T(0);                                                                       \
+            } else {                                                                              \
+                m4p = dm4(dc, dp);                                                                \
+                fout = flux_walk<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7],              \
+                                                 w[(K + 3) & 7], u0_, u1_, w[(K + 6) & 7],        \
+                                                 w[(K + 7) & 7], alpha, two_nu, mp, pp, m4m,      \
+                                                 m4p);                                            \
+                m4m = m4p;                                                                        \
+            }                                                                                     \
+            dc = dp;                                                                              \
+        } else {                                                                                  \
+            fout = flux_walk<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7], w[(K + 3) & 7],  \
+                                             w[(K + 4) & 7], w[(K + 5) & 7], w[(K + 6) & 7],      \
+                                             w[(K + 7) & 7], alpha, two_nu, mp, pp, T(0), T(0));  \
+        }                                                                                         \
         store(i, w[(K + 4) & 7] - nu * (fout - fin));                                             \
         fin = fout;                                                                               \
         i += sg;                                                                                  \
@@ -198,32 +320,34 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm, int ss, int L, co
     }
 
     // The walk runs in chunks over which the load pointer moves uniformly:
-    // inside the line it steps one row per cell; on a ghost it stays put.
+    // inside the line it steps one row per cell; on a ghost row it stays put.
+    // A direct walk is one chunk.
     int t = 0;
     while (t < cnt) {
-        const int k = t + 8;  // index of the next load
-        const int q = p0 + k * sg;
-        const T *src;
-        int inc, end;
-        if (PERIODIC) {
-            const int qq = ((q % L) + L) % L;
-            src = sm + qq * ss;
-            inc = sg * ss;
-            const int room = sg > 0 ? L - qq : qq + 1;  // loads before the wrap
-            end = t + room;
-        } else if (q < -1 || q > L) {
-            // on a ghost: stays there until the source row comes back inside
-            src = row(q);
-            inc = 0;
-            const int back = sg > 0 ? -1 - q : q - L;  // loads until row -1 / L
-            end = back > 0 ? t + back : cnt;
-        } else {
-            src = sm + (q + PAD) * ss;
-            inc = sg * ss;
-            const int room = sg > 0 ? L + 1 - q : q + 2;  // loads through the far ghost
-            end = t + room;
+        int end = cnt;
+        if (!direct) {
+            const int k = t + 8;  // index of the next load
+            const int q = p0 + k * sg;
+            if (PERIODIC) {
+                const int qq = ((q % L) + L) % L;
+                src = sm0 + qq * ss;
+                inc = sg * ss;
+                const int room = sg > 0 ? L - qq : qq + 1;  // loads before the wrap
+                end = t + room;
+            } else if (q < -1 || q > L) {
+                // on a ghost: stays there until the source row comes back inside
+                src = row(q);
+                inc = 0;
+                const int back = sg > 0 ? -1 - q : q - L;  // loads until row -1 / L
+                end = back > 0 ? t + back : cnt;
+            } else {
+                src = sm0 + q * ss;
+                inc = sg * ss;
+                const int room = sg > 0 ? L + 1 - q : q + 2;  // loads through the far ghost
+                end = t + room;
+            }
+            if (end > cnt) end = cnt;
         }
-        if (end > cnt) end = cnt;
         for (; t + 8 <= end; t += 8) {
             VP_WALK_STEP(0)
             VP_WALK_STEP(1)
@@ -278,7 +402,7 @@ __device__ __forceinline__ double cell_centre(double lo, double dvel, int j) {
 }
 
 __device__ __forceinline__ unsigned line_class(const SweepGeo &g, unsigned o, unsigned c) {
-    return g.cls_from_inner ? (c / (unsigned)g.cdiv) % (unsigned)g.cmod : o / (unsigned)g.cdiv;
+    return g.cls_from_inner ? fmod_u(fdiv(c, g.fd_cdiv), g.fd_cmod) : fdiv(o, g.fd_cdiv);
 }
 
 }  // namespace vp_core
