@@ -59,8 +59,9 @@ struct SweepGeo {
     long long cdiv, cmod;
     // column-kernel tile (W columns x full line), row-kernel lines per CTA
     int W, nseg, R;
-    // divisors of the launch: cdiv, cmod, tiles per outer index, W (or R), nseg
-    FastDiv fd_cdiv, fd_cmod, fd_tpo, fd_w, fd_nseg;
+    // divisors of the launch: cdiv, cmod, tiles per outer index, W (or R),
+    // nseg, L, 16-byte pieces per tile row
+    FastDiv fd_cdiv, fd_cmod, fd_tpo, fd_w, fd_nseg, fd_l, fd_wv;
     unsigned tpo;
 };
 

@@ -66,12 +66,12 @@ __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
     }
     constexpr int VEC = 16 / sizeof(T);
     const int wv = W / VEC;
-    if (wc == W && geo.inner % VEC == 0 && W % VEC == 0 && blockDim.x % wv == 0) {
+    if (wc == W && geo.inner % VEC == 0 && W % VEC == 0 && fmod_u(blockDim.x, geo.fd_wv) == 0) {
         // every 16-byte piece of the tile in flight at once (cp.async), so the
         // staging is not limited by one outstanding load per thread
-        const int r = threadIdx.x / wv;
+        const int r = (int)fdiv(threadIdx.x, geo.fd_wv);
         const int cv = threadIdx.x - r * wv;
-        const int rstep = blockDim.x / wv;
+        const int rstep = (int)fdiv(blockDim.x, geo.fd_wv);
         const T *src = base + (long long)r * geo.inner + cv * VEC;
         T *dst = data + r * W + cv * VEC;
         const long long sstep = (long long)rstep * geo.inner;
@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
         vp_tma::cp_async_wait_all();
     } else {
         // row / column of element e advanced incrementally (no division per element)
-        const int dr = blockDim.x / W, dc = blockDim.x - dr * W;
-        int r = threadIdx.x / W, cc = threadIdx.x - r * W;
+        const int dr = (int)fdiv(blockDim.x, geo.fd_w), dc = blockDim.x - dr * W;
+        int r = (int)fdiv(threadIdx.x, geo.fd_w), cc = threadIdx.x - r * W;
         for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
             data[e] = cc < wc ? base[(long long)r * geo.inner + cc] : T(0);
             r += dr;
@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     if (vec) {
         constexpr int U = 4;  // 16-byte loads in flight per thread
         const int st = blockDim.x * VEC;
-        const int dr = st / L, dp = st - dr * L;
-        int r = (threadIdx.x * VEC) / L, pos = threadIdx.x * VEC - r * L;
+        const int dr = (int)fdiv(st, geo.fd_l), dp = st - dr * L;
+        int r = (int)fdiv(threadIdx.x * VEC, geo.fd_l), pos = threadIdx.x * VEC - r * L;
         int e = threadIdx.x * VEC;
         for (; e + (U - 1) * st < tot; e += U * st) {
             float4 x[U];
@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
             }
         }
     } else {
-        const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
-        int r = threadIdx.x / L, pos = threadIdx.x - r * L;
+        const int dr = (int)fdiv(blockDim.x, geo.fd_l), dp = blockDim.x - dr * L;
+        int r = (int)fdiv(threadIdx.x, geo.fd_l), pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             in[r * P + GP + pos] = base[e];
             r += dr;
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     __syncthreads();
     if (vec) {
         const int st = blockDim.x * VEC;
-        const int dr = st / L, dp = st - dr * L;
-        int r = (threadIdx.x * VEC) / L, pos = threadIdx.x * VEC - r * L;
+        const int dr = (int)fdiv(st, geo.fd_l), dp = st - dr * L;
+        int r = (int)fdiv(threadIdx.x * VEC, geo.fd_l), pos = threadIdx.x * VEC - r * L;
         for (int e = threadIdx.x * VEC; e < tot; e += st) {
             float4 x;
             T *xv = reinterpret_cast<T *>(&x);
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
             }
         }
     } else {
-        const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
-        int r = threadIdx.x / L, pos = threadIdx.x - r * L;
+        const int dr = (int)fdiv(blockDim.x, geo.fd_l), dp = blockDim.x - dr * L;
+        int r = (int)fdiv(threadIdx.x, geo.fd_l), pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             base[e] = out[r * Q + pos];
             r += dr;
@@ -472,6 +472,7 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     geo.fd_tpo = make_fastdiv(geo.tpo);
     geo.fd_w = make_fastdiv((unsigned)W);
     geo.fd_nseg = make_fastdiv((unsigned)tu.nseg);
+    geo.fd_wv = make_fastdiv((unsigned)(W / (16 / sizeof(T)) > 0 ? W / (16 / sizeof(T)) : 1));
     const int order = c->g.order;
     const bool per = geo.periodic != 0;
     const bool full = c->g.mp && c->g.pp;
@@ -532,6 +533,7 @@ int launch_rows(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     geo.nseg = tu.nseg;
     geo.fd_w = make_fastdiv((unsigned)R);
     geo.fd_nseg = make_fastdiv((unsigned)tu.nseg);
+    geo.fd_l = make_fastdiv((unsigned)L);
     const long long blocks = (geo.outer + R - 1) / R;
     if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
     const size_t smem = rows_smem<T>(L, R, ghost_rows(geo));
