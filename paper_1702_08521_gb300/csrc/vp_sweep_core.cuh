@@ -51,15 +51,15 @@ __device__ __forceinline__ T curv(T um, T u, T up) {
 }
 
 // d^{M4} between cells with curvatures x and y (App. A):
-// minmod(4x - y, 4y - x, x, y).  With mn / mx the least / greatest of the
-// four, the minmod is mn if mn > 0, mx if mx < 0, else 0: the clamp of 0 into
-// [mn, mx].
+// minmod(4x - y, 4y - x, x, y).  With m = min(x, y) and M = max(x, y) the
+// least of the four is min(m, 4m - M) and the greatest max(M, 4M - m); the
+// minmod is the least if it is > 0, the greatest if it is < 0, else 0: the
+// clamp of 0 into [least, greatest].
 template <typename T>
 __device__ __forceinline__ T dm4(T x, T y) {
-    const T a = T(4) * x - y;
-    const T b = T(4) * y - x;
-    const T mn = min3(a, b, fmin(x, y));
-    const T mx = max3(a, b, fmax(x, y));
+    const T m = fmin(x, y), M = fmax(x, y);
+    const T mn = fmin(m, T(4) * m - M);
+    const T mx = fmax(M, T(4) * M - m);
     return fmin(fmax(T(0), mn), mx);
 }
 
@@ -243,32 +243,22 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
     } else {
         p0 = i - sh.n - 4 * sg;
     }
-    // A zero-inflow line whose shift keeps every load inside the staged zero
-    // rows walks with a plain pointer; otherwise the loads are handled in
-    // chunks (ghost rows, wrap-around).
-    const bool direct = !PERIODIC && GP >= 5 && sh.n <= GP - 4 && sh.n >= 4 - GP;
+    // Zero-inflow lines read rows outside the staged extent [-GP, L + GP) as
+    // the zero row at its edge; periodic lines wrap.
     auto row = [&](int q) -> const T * {
         if (PERIODIC) {
             q %= L;
             if (q < 0) q += L;
         } else {
-            q = min(max(q, -1), L);
+            q = min(max(q, -GP), L + GP - 1);
         }
         return sm0 + q * ss;
     };
-    const T *src = sm0 + p0 * ss;
-    int inc = sg * ss;
+    const T *src = sm0;
+    int inc = 0;
     T w[8];
-    if (direct) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            w[k] = *src;
-            src += inc;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = *row(p0 + k * sg);
-    }
+    for (int k = 0; k < 8; ++k) w[k] = *row(p0 + k * sg);
     // incoming flux of the first cell: upwind cell i - sg, stencil w[0..6]
     T dc = T(0), m4m = T(0);  // curvature at the next upwind cell, d^{M4} at its upwind face
     T m4p = T(0);
@@ -320,34 +310,30 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
     }
 
     // The walk runs in chunks over which the load pointer moves uniformly:
-    // inside the line it steps one row per cell; on a ghost row it stays put.
-    // A direct walk is one chunk.
+    // inside the staged extent it steps one row per cell; beyond it, it stays
+    // on the edge row (zero).  A zero-inflow line whose shift keeps every load
+    // inside the extent (|n| <= GP - 4) is a single chunk.
     int t = 0;
     while (t < cnt) {
-        int end = cnt;
-        if (!direct) {
-            const int k = t + 8;  // index of the next load
-            const int q = p0 + k * sg;
-            if (PERIODIC) {
-                const int qq = ((q % L) + L) % L;
-                src = sm0 + qq * ss;
-                inc = sg * ss;
-                const int room = sg > 0 ? L - qq : qq + 1;  // loads before the wrap
-                end = t + room;
-            } else if (q < -1 || q > L) {
-                // on a ghost: stays there until the source row comes back inside
-                src = row(q);
-                inc = 0;
-                const int back = sg > 0 ? -1 - q : q - L;  // loads until row -1 / L
-                end = back > 0 ? t + back : cnt;
-            } else {
-                src = sm0 + q * ss;
-                inc = sg * ss;
-                const int room = sg > 0 ? L + 1 - q : q + 2;  // loads through the far ghost
-                end = t + room;
-            }
-            if (end > cnt) end = cnt;
+        const int q = p0 + (t + 8) * sg;  // row of the next load
+        int end;
+        if (PERIODIC) {
+            const int qq = ((q % L) + L) % L;
+            src = sm0 + qq * ss;
+            inc = sg * ss;
+            end = t + (sg > 0 ? L - qq : qq + 1);  // loads before the wrap
+        } else if (q < -GP || q > L + GP - 1) {
+            src = row(q);
+            inc = 0;
+            const int back = sg > 0 ? -GP - q : q - (L + GP - 1);  // loads until the extent
+            end = back > 0 ? t + back : cnt;
+        } else {
+            src = sm0 + q * ss;
+            inc = sg * ss;
+            end = t + (sg > 0 ? L + GP - q : q + GP + 1);  // loads through the far edge
         }
+        if (end > cnt) end = cnt;
+#pragma unroll 1
         for (; t + 8 <= end; t += 8) {
             VP_WALK_STEP(0)
             VP_WALK_STEP(1)
@@ -358,6 +344,7 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
             VP_WALK_STEP(6)
             VP_WALK_STEP(7)
         }
+#pragma unroll 1
         for (; t < end; ++t) {
             VP_WALK_STEP(0)
             // restore the canonical order (u_-4 in w[0])
