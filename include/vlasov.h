@@ -310,9 +310,11 @@ int vp_restrict_velocity(const float *f_fine, float *f_coarse, long long NX, int
 /* Training pairs on the coarse grid of ctx: for every line and interface
  * (L + 1 per line), X (9 floats) and y = (Phi_target - Phi_CSL7) / s, where
  * Phi_target = (Gc - whole coarse cells swept) / nu; y = NaN where |zeta|
- * < zmin or the interface is the duplicate periodic end. */
+ * < zmin or the interface is the duplicate periodic end.  scale_dev (may be
+ * NULL) receives s per sample (0 where y is NaN), so that a caller can weight
+ * samples by the mass flux nu s they carry. */
 int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *accel_dev,
-                    const double *Gc_dev, double zmin, float *X_dev, float *y_dev);
+                    const double *Gc_dev, double zmin, float *X_dev, float *y_dev, float *scale_dev);
 
 /* loss += mean (g - y)^2 and grad += its gradient over nsamp samples
  * (straight-through bfloat16 rounding); all device arrays */

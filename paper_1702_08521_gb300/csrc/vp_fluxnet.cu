@@ -335,7 +335,7 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
                                int periodic, int kick, int from_inner, long long cdiv, long long cmod,
                                const double *__restrict__ accel, double lo, double dvel, double dt,
                                double h, WPoly wp, const double *__restrict__ Gc, double zmin,
-                               float *__restrict__ X, float *__restrict__ y) {
+                               float *__restrict__ X, float *__restrict__ y, float *__restrict__ sc) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nlines = outer * inner;
     if (t >= nlines * (L + 1)) return;
@@ -352,6 +352,7 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
     if (fabs(zeta) < zmin || (periodic && i == L)) {
         for (int k = 0; k < NF; ++k) xo[k] = 0.f;
         y[t] = __int_as_float(0x7fc00000);
+        if (sc) sc[t] = 0.f;
         return;
     }
     const int sg = sh.sigma;
@@ -385,6 +386,7 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
     const float s = net_features(u, sh.nu, x);
     for (int k = 0; k < NF; ++k) xo[k] = x[k];
     y[t] = (float)((phi_t - phi_c) / (double)s);
+    if (sc) sc[t] = s;
 }
 
 // coarse-interface masses from fine ones: mean over `group` fine lines of
@@ -672,7 +674,7 @@ int vp_fluxnet_line_map(const vp_grid *fine, const vp_grid *coarse, int factor, 
 }
 
 int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *accel_dev,
-                    const double *Gc_dev, double zmin, float *X_dev, float *y_dev) {
+                    const double *Gc_dev, double zmin, float *X_dev, float *y_dev, float *scale_dev) {
     vp_ctx *c = coarse;
     if (!c || !c->f || !Gc_dev || !X_dev || !y_dev) return VP_EINVAL;
     if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev)) return vp_fail(c, VP_EINVAL, "bad sample arguments");
@@ -680,7 +682,7 @@ int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *
     const long long n = q.outer * q.inner * (q.L + 1);
     k_make_samples<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(
         static_cast<const float *>(c->f), q.outer, q.L, q.inner, q.periodic, kick, q.from_inner, q.cdiv, q.cmod,
-        accel_dev, q.lo, q.dvel, dt, q.h, c->wp, Gc_dev, zmin, X_dev, y_dev);
+        accel_dev, q.lo, q.dvel, dt, q.h, c->wp, Gc_dev, zmin, X_dev, y_dev, scale_dev);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;

@@ -64,36 +64,53 @@ class Sampler:
             V.vp_restrict_velocity(self.fine.f, self.coarse.f, self.fine.NX, nv[0], 1, self.factor, 1,
                                    self.stream)
 
-    def samples(self, kick, d, dt, zmin, keep, rng):
-        """Pairs for the sweep (kick, d, dt) of the current fine state."""
+    def samples(self, kick, d, dt, zmin, keep, rng, importance: float = 0.0):
+        """Pairs for the sweep (kick, d, dt) of the current fine state.
+
+        keep: number of pairs kept (all when 0).  They are drawn without
+        replacement with probability proportional to (nu s)^importance, nu s
+        being the mass flux scale of the interface (s = stencil maximum), so
+        that importance > 0 favours the interfaces that move mass over the
+        near-empty tails; importance = 0 draws uniformly."""
         torch = self.torch
-        acc = self.fine.accel[d * self.fine.NX:] if kick else None
-        Lf = self.gf["nv"][d] if kick else self.gf["nx"][d]
-        every = self.factor if kick else 1
-        nlf = self.fine.NX * int(np.prod(self.gf["nv"])) // Lf
-        nout = Lf // every + 1
-        Gf = torch.empty(nlf * nout, dtype=torch.float64, device="cuda")
-        V.vp_fine_flux(self.fine.ctx, kick, d, dt, acc, every, Gf)
-        m, ncl, grp = self.maps[(kick, d)]
-        Gc = torch.empty(ncl * nout, dtype=torch.float64, device="cuda")
-        V.vp_group_mean(Gf, ncl, nout, m, grp, 1.0 / every, Gc, self.stream)
-        self.restrict()
-        ns = ncl * nout
-        X = torch.empty(ns * 9, dtype=torch.float32, device="cuda")
-        y = torch.empty(ns, dtype=torch.float32, device="cuda")
-        cacc = self.coarse.accel[d * self.coarse.NX:] if kick else None
-        if kick:
-            self.coarse.accel.copy_(self.fine.accel)
-        V.vp_make_samples(self.coarse.ctx, kick, d, dt, cacc, Gc, zmin, X, y)
+        # everything on the library stream: the acceleration copy below must
+        # follow the field solve that wrote it, and the buffers belong there
+        with torch.cuda.stream(self.stream):
+            acc = self.fine.accel[d * self.fine.NX:] if kick else None
+            Lf = self.gf["nv"][d] if kick else self.gf["nx"][d]
+            every = self.factor if kick else 1
+            nlf = self.fine.NX * int(np.prod(self.gf["nv"])) // Lf
+            nout = Lf // every + 1
+            Gf = torch.empty(nlf * nout, dtype=torch.float64, device="cuda")
+            V.vp_fine_flux(self.fine.ctx, kick, d, dt, acc, every, Gf)
+            m, ncl, grp = self.maps[(kick, d)]
+            Gc = torch.empty(ncl * nout, dtype=torch.float64, device="cuda")
+            V.vp_group_mean(Gf, ncl, nout, m, grp, 1.0 / every, Gc, self.stream)
+            self.restrict()
+            ns = ncl * nout
+            X = torch.empty(ns * 9, dtype=torch.float32, device="cuda")
+            y = torch.empty(ns, dtype=torch.float32, device="cuda")
+            sc = torch.empty(ns, dtype=torch.float32, device="cuda")
+            cacc = self.coarse.accel[d * self.coarse.NX:] if kick else None
+            if kick:
+                self.coarse.accel.copy_(self.fine.accel)
+            V.vp_make_samples(self.coarse.ctx, kick, d, dt, cacc, Gc, zmin, X, y, sc)
+            ok = torch.isfinite(y)
+            Xv, yv, sv = X.view(ns, 9)[ok], y[ok], sc[ok]
+            if keep and yv.numel() > keep:
+                if importance > 0:
+                    wgt = (Xv[:, 8].double() * sv.double()) ** importance
+                    p = (wgt / wgt.sum()).cpu().numpy()
+                    nz = int((p > 0).sum())
+                    sel = rng.choice(yv.numel(), size=min(keep, nz), replace=False, p=p)
+                else:
+                    sel = rng.choice(yv.numel(), size=keep, replace=False)
+                sel = torch.as_tensor(sel, device="cuda")
+                Xv, yv = Xv[sel], yv[sel]
         self.stream.synchronize()
-        ok = torch.isfinite(y)
-        Xv, yv = X.view(ns, 9)[ok], y[ok]
-        if keep and yv.numel() > keep:
-            sel = torch.as_tensor(rng.choice(yv.numel(), size=keep, replace=False), device="cuda")
-            Xv, yv = Xv[sel], yv[sel]
         return Xv, yv
 
-    def run_draw(self, k, alpha, dt, steps, every_step, zmin, keep, rng):
+    def run_draw(self, k, alpha, dt, steps, every_step, zmin, keep, rng, importance: float = 0.0):
         """Fine run from the Landau state (k, alpha); pairs of its velocity
         sweeps every `every_step` steps."""
         V.vp_init_f(self.fine.ctx, *_landau_ic(self.dims, k, alpha))
@@ -107,7 +124,7 @@ class Sampler:
                     continue
                 kick, d, fac = sw
                 if take and kick:
-                    X, y = self.samples(kick, d, fac * dt, zmin, keep, rng)
+                    X, y = self.samples(kick, d, fac * dt, zmin, keep, rng, importance)
                     Xs.append(X)
                     ys.append(y)
                 acc = self.fine.accel[d * self.fine.NX:] if kick else None

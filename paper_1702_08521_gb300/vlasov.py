@@ -126,7 +126,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_fluxnet_line_map": (I, [GP, GP, I, I, I, P, P, P]),
             "vp_group_mean": (I, [P, LL, I, P, I, D, P, P]),
             "vp_restrict_velocity": (I, [P, P, LL, I, I, I, I, P]),
-            "vp_make_samples": (I, [P, I, I, D, P, P, D, P, P]),
+            "vp_make_samples": (I, [P, I, I, D, P, P, D, P, P, P]),
             "vp_net_grad": (I, [P, P, LL, P, P, P, P]),
             "vp_net_adam": (I, [P, P, P, P, I, ctypes.c_float, P]),
         }
@@ -405,8 +405,9 @@ def vp_restrict_velocity(f_fine, f_coarse, NX: int, nf1: int, nf2: int, factor1:
                                     _sh(stream)), "restrict")
 
 
-def vp_make_samples(ctx, kick: int, dim: int, dt: float, accel, Gc, zmin: float, X, y) -> None:
-    _check(ctx, load().vp_make_samples(ctx, kick, dim, dt, _ptr(accel), _ptr(Gc), zmin, _ptr(X), _ptr(y)))
+def vp_make_samples(ctx, kick: int, dim: int, dt: float, accel, Gc, zmin: float, X, y, scale=None) -> None:
+    _check(ctx, load().vp_make_samples(ctx, kick, dim, dt, _ptr(accel), _ptr(Gc), zmin, _ptr(X), _ptr(y),
+                                       _ptr(scale)))
 
 
 def vp_net_grad(X, y, nsamp: int, wts, grad, loss, stream=None) -> None:
