@@ -263,25 +263,36 @@ int vp_ensemble_sync(vp_ens *ens);
 long long vp_ensemble_launch_count(const vp_ens *ens);
 
 /* ---- learned flux correction (not in the paper) --------------------------
- * A 9 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the CSL7 flux of a sweep
- * on a coarse velocity grid: Phi = Phi_CSL7 + s g(x), where s = max |u_k| + 1e-30
- * over the upwind-ordered 8-cell stencil u_{-3..4} of the interface and
- * x = ((u_k - u_0) / s for k = -3..4, nu).  The corrected flux then passes the
- * MP constraint (App. A) and the PP limiter (Sec. 2.1.1), and the update keeps
- * the flux form (Eq. 49), so mass conservation and f >= 0 hold as for the
- * plain scheme.  Weights and matrix inputs are rounded to bfloat16, sums are
- * FP32.  Parameters: VP_NET_NPARAM floats, W1[32][9] b1[32] W2[32][32] b2[32]
- * W3[32][32] b3[32] w4[32] b4[1] (FP32 master copy; rounded when used).
+ * A 17 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
+ * spatial sweep (drift) on a coarse velocity grid moves through each
+ * interface: M = nu Phi_MP + s g(x), where Phi_MP is the CSL7 flux after the
+ * MP constraint (App. A), s = max |u_k| + 1e-30 over the upwind-ordered 8-cell
+ * stencil u_{-3..4} of the interface and x = ((u_k - u_0) / s for k = -3..4,
+ * (u+_k - u-_k) / (2 s) for k = -3..4, nu); u+ / u- are the same cells of the
+ * lines in the neighbouring velocity cells along the sweep's axis (+: larger
+ * |v|; a neighbour outside the velocity box is zero).  The velocity
+ * difference is what a coarse velocity cell loses: its sub-cell spread of
+ * speeds moves the sub-cell gradient of f across x, also where the cell's
+ * own fractional shift nu is zero, hence a mass rather than a flux value.
+ * The PP limiter (Sec. 2.1.1) then acts on the total mass (u_0 - 2M >= 0,
+ * u_1 + 2M >= 0, blending with the upwind mass nu u_0) and the update keeps
+ * the flux form f'_i = f_{i-n} - (M_out - M_in) (Eq. 49), so mass conservation
+ * and f >= 0 hold as for the plain scheme.  Weights and matrix inputs are rounded to bfloat16, sums are
+ * FP32.  Parameters: VP_NET_NPARAM floats, W1[32][17] b1[32] W2[32][32]
+ * b2[32] W3[32][32] b3[32] w4[32] b4[1] (FP32 master copy; rounded when used).
  * Training pairs come from fine-grid runs of the method (vp_fine_flux,
  * vp_fluxnet_line_map, vp_group_mean, vp_restrict_velocity, vp_make_samples).
  */
-#define VP_NET_NPARAM 2465
+#define VP_NET_NPARAM 2721
 
 /* one sweep of the grid of ctx (FP32, order 7) with the network correction
- * (use_net = 1) or without it (use_net = 0: identical to vp_drift_sweep /
- * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); in place. */
+ * (use_net = 1, drifts only) or without it (use_net = 0: identical to
+ * vp_drift_sweep / vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device);
+ * f_snap_dev: a copy of f taken before the sweep (device, vp_num_cells
+ * floats), read for the velocity neighbours, required when use_net = 1 and
+ * ignored otherwise; in place.  VP_ENOTSUP for use_net with kick = 1. */
 int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
-                     const float *wts_dev, int use_net);
+                     const float *wts_dev, int use_net, const float *f_snap_dev);
 
 /* Mass that the sweep (kick, dim, dt) of ctx's current f moves through every
  * `every`-th interface of every line, in cell units: G[line][j] for the
@@ -308,18 +319,22 @@ int vp_restrict_velocity(const float *f_fine, float *f_coarse, long long NX, int
                          int factor2, void *cuda_stream);
 
 /* Training pairs on the coarse grid of ctx: for every line and interface
- * (L + 1 per line), X (9 floats) and y = (Phi_target - Phi_CSL7) / s, where
- * Phi_target = (Gc - whole coarse cells swept) / nu; y = NaN where |zeta|
- * < zmin or the interface is the duplicate periodic end.  scale_dev (may be
+ * (L + 1 per line), X (17 floats, zero velocity features for kick = 1) and
+ * y = (Gc - whole coarse cells swept - nu Phi_MP) / s, the mass the network
+ * should add; y = NaN where |zeta| < zmin or the interface is the duplicate
+ * periodic end.  scale_dev (may be
  * NULL) receives s per sample (0 where y is NaN), so that a caller can weight
  * samples by the mass flux nu s they carry. */
 int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *accel_dev,
                     const double *Gc_dev, double zmin, float *X_dev, float *y_dev, float *scale_dev);
 
-/* loss += mean (g - y)^2 and grad += its gradient over nsamp samples
- * (straight-through bfloat16 rounding); all device arrays */
-int vp_net_grad(const float *X_dev, const float *y_dev, long long nsamp, const float *wts_dev,
-                float *grad_dev, float *loss_dev, void *cuda_stream);
+/* loss += mean over groups of r^2 and grad += its gradient, where the nsamp
+ * samples form consecutive groups of `group` (1, or 2 for the two interfaces
+ * of one cell) with residual r = sum_k a_k (g(X_k) - y_k), a_k = coef_dev[k]
+ * (all 1 when coef_dev is NULL); straight-through bfloat16 rounding; all
+ * device arrays; nsamp must be a multiple of group. */
+int vp_net_grad(const float *X_dev, const float *y_dev, const float *coef_dev, long long nsamp, int group,
+                const float *wts_dev, float *grad_dev, float *loss_dev, void *cuda_stream);
 
 /* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the FP32 parameters; zeroes grad */
 int vp_net_adam(float *wts_dev, float *m_dev, float *v_dev, float *grad_dev, int step, float lr,

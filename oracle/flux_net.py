@@ -4,17 +4,24 @@ Not part of the paper: the learned correction is a spec addition to the
 method.  It is restated here in plain numpy, in double precision, so that the
 GPU training and inference kernels can be checked against it.
 
-Network (per interface, upwind-ordered stencil u_{-3..4}, u_0 = upwind cell):
+Network (per interface of a spatial sweep; upwind-ordered stencil u_{-3..4} of
+the line, u_0 = upwind cell; u+_k / u-_k: the same cells on the lines of the
+neighbouring velocity cells of the sweep's axis, + on the side of larger |v|):
     s    = max_k |u_k| + 1e-30
-    x    = [(u_k - u_0) / s for k = -3..4] + [nu]          (9 features)
-    h1   = relu(W1 x  + b1)      W1: 32 x 9
+    x    = [(u_k - u_0) / s for k = -3..4]
+         + [(u+_k - u-_k) / (2 s) for k = -3..4] + [nu]   (17 features)
+    h1   = relu(W1 x  + b1)      W1: 32 x 17
     h2   = relu(W2 h1 + b2)      W2: 32 x 32
     h3   = relu(W3 h2 + b3)      W3: 32 x 32
     g    = w4 . h3 + b4          w4: 32
-    Phi_net = Phi_CSL + s * g    (then the MP constraint and the PP limiter)
+    M    = nu * MP(Phi_CSL) + s * g   (mass through the interface; then the
+                                       PP limiter on M, update f - (M_out - M_in))
 Weights and every matrix input (x, h1, h2, h3) are rounded to bfloat16 as on
-the tensor cores; sums are exact here (FP64) and FP32 on the GPU.  Training
-loss: mean over samples of (g - y)^2 with y = (Phi_target - Phi_CSL) / s.
+the tensor cores; sums are exact here (FP64) and FP32 on the GPU.  Target of
+g at an interface: y = (M_target - nu MP(Phi_CSL)) / s.  Training loss: the
+mean over cells of r^2, r = (s_r (g_r - y_r) - s_l (g_l - y_l)) / max(s_l, s_r)
+over the cell's right / left interface, i.e. the error of the cell update
+(loss_and_grad with group = 2); group = 1 gives the per-interface error.
 The backward pass treats the bfloat16 rounding as the identity.
 """
 from __future__ import annotations
@@ -22,7 +29,7 @@ from __future__ import annotations
 import numpy as np
 
 HIDDEN = 32
-NFEAT = 9
+NFEAT = 17
 SHAPES = {"W1": (HIDDEN, NFEAT), "b1": (HIDDEN,), "W2": (HIDDEN, HIDDEN), "b2": (HIDDEN,),
           "W3": (HIDDEN, HIDDEN), "b3": (HIDDEN,), "w4": (HIDDEN,), "b4": (1,)}
 ORDER = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
@@ -40,11 +47,13 @@ def bf16(x) -> np.ndarray:
     return out
 
 
-def features(u, nu) -> tuple:
-    """u: (B, 8) upwind-ordered stencils u_{-3..4}; nu: (B,). Returns (X, s)."""
+def features(u, up, um, nu) -> tuple:
+    """u, up, um: (B, 8) upwind-ordered stencils u_{-3..4} of the line and of
+    its velocity neighbours (+: larger |v|); nu: (B,). Returns (X, s)."""
     u = np.asarray(u, dtype=np.float64)
     s = np.abs(u).max(axis=1) + 1e-30
-    X = np.concatenate([(u - u[:, 3:4]) / s[:, None], np.asarray(nu, dtype=np.float64)[:, None]], axis=1)
+    dv = (np.asarray(up, dtype=np.float64) - np.asarray(um, dtype=np.float64)) / (2.0 * s[:, None])
+    X = np.concatenate([(u - u[:, 3:4]) / s[:, None], dv, np.asarray(nu, dtype=np.float64)[:, None]], axis=1)
     return X, s
 
 
@@ -92,13 +101,18 @@ def forward(p: dict, X, *, round_bf16: bool = True):
     return g, (x0, z1, x1, z2, x2, z3, x3, W1, W2, W3, w4)
 
 
-def loss_and_grad(p: dict, X, y, *, round_bf16: bool = True):
-    """Mean squared error and its gradient (dict) over the batch."""
+def loss_and_grad(p: dict, X, y, *, round_bf16: bool = True, coef=None, group: int = 1):
+    """Loss and its gradient (dict) over the batch.  Samples form consecutive
+    groups of `group` with residual r = sum_k a_k (g_k - y_k) (a = coef, or
+    all 1); the loss is the mean of r^2 over groups (group 1, no coef: the
+    mean squared error)."""
     g, (x0, z1, x1, z2, x2, z3, x3, W1, W2, W3, w4) = forward(p, X, round_bf16=round_bf16)
     B = len(y)
-    r = g - np.asarray(y, dtype=np.float64)
+    a = np.ones(B) if coef is None else np.asarray(coef, dtype=np.float64)
+    term = a * (g - np.asarray(y, dtype=np.float64))
+    r = term.reshape(-1, group).sum(axis=1)
     loss = float(np.mean(r * r))
-    dg = 2.0 * r / B
+    dg = 2.0 * np.repeat(r, group) * a / (B // group)
     grads = {"w4": x3.T @ dg, "b4": np.array([dg.sum()])}
     dh3 = np.outer(dg, w4) * (z3 > 0)
     grads["W3"] = dh3.T @ x2

@@ -1,17 +1,24 @@
 // vp_fluxnet.cu -- learned flux correction on a coarser velocity grid
 // (a spec addition to the method, not in the paper).
 //
-// A 9 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the CSL7 flux of a
-// coarse-grid sweep: Phi = Phi_CSL7 + s g(x), s = max |u| over the 8-cell
-// upwind-ordered stencil u_{-3..4}, x = ((u_k - u_0) / s, nu).  Weights and
-// matrix inputs are bfloat16, sums FP32.  The corrected flux then passes the
-// MP constraint and the PP limiter unchanged, so conservation (flux form)
-// and f >= 0 hold exactly as for the plain scheme.
+// A 17 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
+// coarse-grid spatial sweep moves through an interface:
+//   M = nu Phi_MP + s g(x),
+// Phi_MP the CSL7 flux after the MP constraint, s = max |u| over the 8-cell
+// upwind-ordered stencil u_{-3..4}, x = ((u_k - u_0) / s, (u+_k - u-_k) / (2 s),
+// nu) with u+ / u- the same cells of the lines in the neighbouring velocity
+// cells (+: larger |v|).  The correction is a mass, not a flux value: the
+// sub-cell spread of speeds inside a coarse velocity cell moves mass even
+// where the cell's own fractional shift nu vanishes.  The PP limiter then acts
+// on the total mass (f_i - 2 M >= 0, f_{i+1} + 2 M >= 0) and the update keeps
+// the flux form f'_i = f_{i-n} - (M_out - M_in), so conservation and f >= 0
+// hold exactly as for the plain scheme.  Weights and matrix inputs are
+// bfloat16, sums FP32.
 //
 // Training data come from fine-grid runs of the method itself: for a sweep,
 // the fine-grid mass through every coarse interface (mean over the fine
-// lines a coarse line aggregates), minus the coarse integer-shift part,
-// divided by the coarse CFL number, is the target coarse flux.
+// lines a coarse line aggregates), minus the coarse integer-shift part and
+// the coarse MP-limited fractional mass, over s, is the target of g.
 // Training: per-sample forward/backward (FP32, bfloat16-rounded weights and
 // activations, straight-through backward), per-CTA weight-gradient
 // reductions, Adam.
@@ -80,8 +87,10 @@ __device__ __forceinline__ float net_forward(const float *__restrict__ w, const 
     return g;
 }
 
-// features of the upwind-ordered stencil u[0..7] = u_{-3..4}
-__device__ __forceinline__ float net_features(const float *u, float nu, float *x) {
+// features of the upwind-ordered stencil u[0..7] = u_{-3..4} and of the same
+// cells up / um of the velocity-neighbour lines (+: larger |v|)
+__device__ __forceinline__ float net_features(const float *u, const float *up, const float *um, float nu,
+                                              float *x) {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) s = fmaxf(s, fabsf(u[k]));
@@ -89,20 +98,51 @@ __device__ __forceinline__ float net_features(const float *u, float nu, float *x
     const float inv = 1.0f / s;
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = (u[k] - u[3]) * inv;
-    x[8] = nu;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[8 + k] = (up[k] - um[k]) * (0.5f * inv);
+    x[16] = nu;
     return s;
+}
+
+// PP limiter (Sec. 2.1.1, Eqs. 15-23) on the mass M through the interface
+// between the upwind cell u0 and u1: keep u0 - 2 M >= 0 and u1 + 2 M >= 0 by
+// blending M with the upwind mass nu u0 (theta as in the plain sweep, with
+// the same (1 - 8 eps) safety factor)
+__device__ __forceinline__ float pp_mass(float M, float u0, float u1, float nu) {
+    const float up = u0 - 2.f * M, um = u1 + 2.f * M;
+    if (fminf(up, um) >= 0.f) return M;
+    const float two_nu = 2.f * nu;
+    float th = 1.f;
+    if (up < 0.f) {
+        const float base = u0 - two_nu * u0;
+        const float den = base - up;
+        th = den > 0.f ? __fdividef(base, den) : 0.f;
+    }
+    if (um < 0.f) {
+        const float base = u1 + two_nu * u0;
+        const float den = base - um;
+        th = fminf(th, den > 0.f ? __fdividef(base, den) : 0.f);
+    }
+    th *= 1.0f - 8.0f * 5.9604644775390625e-08f;
+    th = fminf(fmaxf(th, 0.f), 1.f);
+    return th * M + (1.f - th) * (nu * u0);
 }
 
 // ---- training ----------------------------------------------------------------------
 
 constexpr int kTrainThreads = 128;
 
-// One CTA: kTrainThreads samples.  Loss and weight gradients accumulated in
-// global FP32 (per-CTA reductions, then one atomic per parameter).
+// One CTA: kTrainThreads samples.  Samples come in consecutive groups of
+// `group` (1 or 2; a pair = the two interfaces of one cell) whose residual is
+// r = sum_k a_k (g_k - y_k) (a_k = coef[k], 1 without coef); the loss is the
+// mean of r^2 over groups.  The two threads of a pair exchange their terms by
+// a warp shuffle.  Loss and weight gradients accumulated in global FP32
+// (per-CTA reductions, then one atomic per parameter).
 __global__ void __launch_bounds__(kTrainThreads) k_net_grad(const float *__restrict__ X,
                                                             const float *__restrict__ y,
+                                                            const float *__restrict__ coef,
                                                             const float *__restrict__ wts, long long nsamp,
-                                                            float *__restrict__ grad,
+                                                            int group, float *__restrict__ grad,
                                                             float *__restrict__ loss) {
     __shared__ float w[NPARAM];
     __shared__ float A0[kTrainThreads][NF + 1];
@@ -120,17 +160,22 @@ __global__ void __launch_bounds__(kTrainThreads) k_net_grad(const float *__restr
     const bool valid = sidx < nsamp;
     const int t = threadIdx.x;
     float x[NF], h1[H], h2[H], h3[H];
-    float r = 0.f;
+    float term = 0.f, a = 0.f;
     if (valid) {
         for (int k = 0; k < NF; ++k) x[k] = X[sidx * NF + k];
         const float g = net_forward(w, x, h1, h2, h3);
-        r = g - y[sidx];
+        a = coef ? coef[sidx] : 1.f;
+        term = a * (g - y[sidx]);
     } else {
         for (int k = 0; k < NF; ++k) x[k] = 0.f;
         for (int j = 0; j < H; ++j) h1[j] = h2[j] = h3[j] = 0.f;
     }
-    const float dg = valid ? 2.0f * r / (float)nsamp : 0.f;
-    red[t] = valid ? r * r / (float)nsamp : 0.f;
+    // group residual (pairs are threads 2k, 2k + 1 of the same warp)
+    float r = term;
+    if (group == 2) r += __shfl_xor_sync(0xffffffffu, term, 1);
+    const float ngroups = (float)(nsamp / group);
+    const float dg = valid ? 2.0f * r * a / ngroups : 0.f;
+    red[t] = (valid && (group == 1 || (t & 1) == 0)) ? r * r / ngroups : 0.f;
     for (int k = 0; k < NF; ++k) A0[t][k] = bfr(x[k]);
     for (int j = 0; j < H; ++j) {
         A1[t][j] = h1[j];
@@ -335,7 +380,8 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
                                int periodic, int kick, int from_inner, long long cdiv, long long cmod,
                                const double *__restrict__ accel, double lo, double dvel, double dt,
                                double h, WPoly wp, const double *__restrict__ Gc, double zmin,
-                               float *__restrict__ X, float *__restrict__ y, float *__restrict__ sc) {
+                               float *__restrict__ X, float *__restrict__ y, float *__restrict__ sc,
+                               float alpha) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nlines = outer * inner;
     if (t >= nlines * (L + 1)) return;
@@ -369,8 +415,31 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
     const int ip = sg > 0 ? i : L - i;
     const int n = sh.n * sg;
     const long long up = (long long)ip - 1 - n;
-    float u[8];
+    float u[8], unp[8], unm[8];
     for (int k = 0; k < 8; ++k) u[k] = val(up - 3 + k);
+    // velocity-neighbour lines of a spatial sweep (+: larger |v|), zero
+    // outside the velocity box; none for a velocity sweep
+    for (int k = 0; k < 8; ++k) unp[k] = unm[k] = 0.f;
+    if (!kick) {
+        const int sp = speed >= 0.0 ? 1 : -1;
+        const long long J = (c / cdiv) % cmod;
+        auto nval = [&](long long dj, long long k) -> float {
+            const long long Jn = J + dj;
+            if (Jn < 0 || Jn >= cmod) return 0.f;
+            if (periodic) {
+                k %= L;
+                if (k < 0) k += L;
+            } else if (k < 0 || k >= L) {
+                return 0.f;
+            }
+            const long long kk = sg > 0 ? k : L - 1 - k;
+            return base[kk * inner + dj * cdiv];
+        };
+        for (int k = 0; k < 8; ++k) {
+            unp[k] = nval(sp, up - 3 + k);
+            unm[k] = nval(-sp, up - 3 + k);
+        }
+    }
     // whole cells swept in the upwind frame, signed: sum_{m = ip - n}^{ip - 1} u_m
     // (n < 0 when the integer shift opposes the fractional one)
     double whole = 0.0;
@@ -379,13 +448,14 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
     else
         for (long long m = ip; m < ip - n; ++m) whole -= val(m);
     const double g = sg > 0 ? Gc[line * (L + 1) + i] : -Gc[line * (L + 1) + i];
-    const double phi_t = (g - whole) / (double)sh.nu;
-    double phi_c = 0.0;
-    for (int k = 0; k < 7; ++k) phi_c += (double)sh.w[k] * (double)u[k];
+    // coarse fractional mass as the plain sweep computes it: CSL7, then MP
+    float phi = sh.w[0] * u[0];
+    for (int k = 1; k < 7; ++k) phi = fmaf(sh.w[k], u[k], phi);
+    phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
     float x[NF];
-    const float s = net_features(u, sh.nu, x);
+    const float s = net_features(u, unp, unm, sh.nu, x);
     for (int k = 0; k < NF; ++k) xo[k] = x[k];
-    y[t] = (float)((phi_t - phi_c) / (double)s);
+    y[t] = (float)((g - whole - (double)sh.nu * (double)phi) / (double)s);
     if (sc) sc[t] = s;
 }
 
@@ -415,7 +485,7 @@ __global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, lo
                                                        const double *__restrict__ accel, double lo,
                                                        double dvel, double dt, double h, WPoly wp,
                                                        const float *__restrict__ wts, float alpha,
-                                                       int use_net) {
+                                                       int use_net, const float *__restrict__ fsnap) {
     extern __shared__ float lsm[];
     float *w = lsm;                       // NPARAM rounded weights
     float *line_buf = lsm + NPARAM + 3;   // [L + 2][blockDim] staged line (zero ghosts at 0, L+1)
@@ -438,7 +508,7 @@ __global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, lo
     const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
     const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, wp);
     const int sg = sh.sigma;
-    const float nu = sh.nu, two_nu = 2.f * nu;
+    const float nu = sh.nu;
     int n = sh.n;
     if (PERIODIC) {
         n %= L;
@@ -453,7 +523,27 @@ __global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, lo
         }
         return sl[(q + 1) * T];
     };
-    // flux through the interface whose upwind cell is q (upwind-ordered stencil)
+    // velocity-neighbour lines (+: larger |v|) in the snapshot taken before
+    // the sweep; a neighbour outside the velocity box reads as zero
+    const int sp = speed >= 0.0 ? 1 : -1;
+    const long long J = use_net && !kick ? (c / cdiv) % cmod : 0;
+    const float *snap_p = (use_net && !kick && J + sp >= 0 && J + sp < cmod) ? fsnap + o * L * inner + c + sp * cdiv
+                                                                            : nullptr;
+    const float *snap_m = (use_net && !kick && J - sp >= 0 && J - sp < cmod) ? fsnap + o * L * inner + c - sp * cdiv
+                                                                            : nullptr;
+    auto nld = [&](const float *nb, int q) -> float {  // row q of a neighbour line
+        if (!nb) return 0.f;
+        if (PERIODIC) {
+            q %= L;
+            if (q < 0) q += L;
+        } else if (q < 0 || q >= L) {
+            return 0.f;
+        }
+        return nb[(long long)q * inner];
+    };
+    // mass through the interface whose upwind cell is q (upwind-ordered
+    // stencil): nu times the MP-limited CSL7 flux, plus the network's mass
+    // correction, then the PP limiter on the total
     auto iface = [&](int q) -> float {
         float u[8];
 #pragma unroll
@@ -461,13 +551,19 @@ __global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, lo
         float phi = sh.w[0] * u[0];
 #pragma unroll
         for (int k = 1; k < 7; ++k) phi = fmaf(sh.w[k], u[k], phi);
-        if (use_net) {
-            float x[NF], h1[H], h2[H];
-            const float s = net_features(u, nu, x);
-            phi = fmaf(s, net_forward(w, x, h1, h2, nullptr), phi);
-        }
         phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
-        return vp_core::pp_limit(phi, u[3], u[4], two_nu);
+        float M = nu * phi;
+        if (use_net) {
+            float x[NF], h1[H], h2[H], unp[8], unm[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                unp[k] = nld(snap_p, q + sg * (k - 3));
+                unm[k] = nld(snap_m, q + sg * (k - 3));
+            }
+            const float s = net_features(u, unp, unm, nu, x);
+            M = fmaf(s, net_forward(w, x, h1, h2, nullptr), M);
+        }
+        return pp_mass(M, u[3], u[4], nu);
     };
     // new values into registers of the staged line is not possible in place
     // (neighbours still read old values): compute all, then write
@@ -475,7 +571,7 @@ __global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, lo
     for (int t = 0; t < L; ++t) {
         const int i = sg > 0 ? t : L - 1 - t;
         const float fout = iface(i - n);
-        base[(long long)i * inner] = ld(i - n) - nu * (fout - fin);
+        base[(long long)i * inner] = ld(i - n) - (fout - fin);
         fin = fout;
     }
 }
@@ -486,12 +582,13 @@ __global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, lo
 
 extern "C" {
 
-int vp_net_grad(const float *X, const float *y, long long nsamp, const float *wts, float *grad,
-                float *loss, void *stream) {
-    if (!X || !y || !wts || !grad || !loss || nsamp < 1) return VP_EINVAL;
+int vp_net_grad(const float *X, const float *y, const float *coef, long long nsamp, int group, const float *wts,
+                float *grad, float *loss, void *stream) {
+    if (!X || !y || !wts || !grad || !loss || nsamp < 1 || (group != 1 && group != 2) || nsamp % group)
+        return VP_EINVAL;
     const long long blocks = (nsamp + kTrainThreads - 1) / kTrainThreads;
-    k_net_grad<<<(unsigned)blocks, kTrainThreads, 0, static_cast<cudaStream_t>(stream)>>>(X, y, wts, nsamp,
-                                                                                         grad, loss);
+    k_net_grad<<<(unsigned)blocks, kTrainThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        X, y, coef, wts, nsamp, group, grad, loss);
     return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
 }
 
@@ -553,11 +650,13 @@ LineGeo line_geo(const vp_grid &g, long long NX, long long NV, int kick, int dim
 extern "C" {
 
 int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
-                     int use_net) {
+                     int use_net, const float *f_snap) {
     if (!c || !c->f) return VP_EINVAL;
     if (c->g.precision != VP_F32 || c->g.order != 7)
         return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
-    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
+    if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
+    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && (!wts || !f_snap)) ||
+        !std::isfinite(dt))
         return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
     const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
     const int T = 128;
@@ -570,11 +669,11 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     if (q.periodic)
         k_learned_sweep<true><<<blocks, T, smem, c->stream>>>(
             static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
-            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net);
+            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap);
     else
         k_learned_sweep<false><<<blocks, T, smem, c->stream>>>(
             static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
-            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net);
+            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
@@ -682,7 +781,7 @@ int vp_make_samples(vp_ctx *coarse, int kick, int dim, double dt, const double *
     const long long n = q.outer * q.inner * (q.L + 1);
     k_make_samples<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(
         static_cast<const float *>(c->f), q.outer, q.L, q.inner, q.periodic, kick, q.from_inner, q.cdiv, q.cmod,
-        accel_dev, q.lo, q.dvel, dt, q.h, c->wp, Gc_dev, zmin, X_dev, y_dev, scale_dev);
+        accel_dev, q.lo, q.dvel, dt, q.h, c->wp, Gc_dev, zmin, X_dev, y_dev, scale_dev, (float)c->g.alpha);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;

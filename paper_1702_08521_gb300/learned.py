@@ -1,10 +1,13 @@
 """Learned flux correction on a coarser velocity grid: data generation from
 fine-grid runs of the method, training, and coarse runs with the network.
 
-The correction acts on the velocity sweeps (kicks), where the coarse grid
-loses resolution; spatial sweeps (drifts) run the plain scheme: their
-coarse-grid error comes from the spread of speeds inside one coarse velocity
-cell, which the spatial stencil the network sees cannot resolve.
+The correction acts on the spatial sweeps (drifts): on a coarser velocity
+grid their error comes from the spread of speeds inside one velocity cell,
+which moves the sub-cell velocity gradient of f across x.  The network sees
+the spatial stencil of the line and the velocity difference of its
+neighbouring velocity cells at the same positions.  Velocity sweeps (kicks)
+run the plain scheme: on these grids their coarse-grid error is orders of
+magnitude below the drifts'.
 
 Orchestration only: every arithmetic step (sweeps, fine-flux extraction,
 restriction, sample construction, forward/backward, Adam, learned sweeps)
@@ -18,6 +21,8 @@ import math
 import numpy as np
 
 from . import vlasov as V
+
+NFEAT = 17  # network inputs: 8 stencil values, 8 velocity differences, nu
 
 
 def landau_grid(dims: int, nx: int, nv: int, k: float = 0.5, vmax: float = 6.0) -> dict:
@@ -65,13 +70,17 @@ class Sampler:
                                    self.stream)
 
     def samples(self, kick, d, dt, zmin, keep, rng, importance: float = 0.0):
-        """Pairs for the sweep (kick, d, dt) of the current fine state.
+        """Training pairs of cells for the sweep (kick, d, dt) of the current
+        fine state: for every cell of the coarse lines, its left and right
+        interfaces (rows 2m, 2m + 1 of X and y) with the coefficients of the
+        cell-update residual r = (s_r (g_r - y_r) - s_l (g_l - y_l)) / s_c,
+        s_c = max(s_l, s_r), s the stencil maximum of an interface.
 
-        keep: number of pairs kept (all when 0).  They are drawn without
-        replacement with probability proportional to (nu s)^importance, nu s
-        being the mass flux scale of the interface (s = stencil maximum), so
-        that importance > 0 favours the interfaces that move mass over the
-        near-empty tails; importance = 0 draws uniformly."""
+        keep: number of cells kept (all when 0), drawn without replacement
+        with probability proportional to s_c^importance, so that with
+        importance = 2 the mean squared residual weighs cells by the square
+        of their mass scale; importance = 0 draws uniformly.
+        Returns (X [2n][NFEAT], y [2n], coef [2n])."""
         torch = self.torch
         # everything on the library stream: the acceleration copy below must
         # follow the field solve that wrote it, and the buffers belong there
@@ -88,34 +97,49 @@ class Sampler:
             V.vp_group_mean(Gf, ncl, nout, m, grp, 1.0 / every, Gc, self.stream)
             self.restrict()
             ns = ncl * nout
-            X = torch.empty(ns * 9, dtype=torch.float32, device="cuda")
+            X = torch.empty(ns * NFEAT, dtype=torch.float32, device="cuda")
             y = torch.empty(ns, dtype=torch.float32, device="cuda")
             sc = torch.empty(ns, dtype=torch.float32, device="cuda")
             cacc = self.coarse.accel[d * self.coarse.NX:] if kick else None
             if kick:
                 self.coarse.accel.copy_(self.fine.accel)
             V.vp_make_samples(self.coarse.ctx, kick, d, dt, cacc, Gc, zmin, X, y, sc)
-            ok = torch.isfinite(y)
-            Xv, yv, sv = X.view(ns, 9)[ok], y[ok], sc[ok]
-            if keep and yv.numel() > keep:
+            # cells: left interface i, right interface i + 1 (interface 0 again
+            # at the end of a periodic line, whose interface L is not sampled)
+            Lc = nout - 1
+            yl = y.view(ncl, nout)
+            right = torch.arange(1, nout, device="cuda").expand(ncl, Lc).clone()
+            right[~torch.isfinite(yl[:, Lc]), Lc - 1] = 0
+            base = (torch.arange(ncl, device="cuda") * nout).unsqueeze(1)
+            li = (base + torch.arange(Lc, device="cuda")).reshape(-1)
+            ri = (base + right).reshape(-1)
+            ok = torch.isfinite(y[li]) & torch.isfinite(y[ri])
+            li, ri = li[ok], ri[ok]
+            sl, sr = sc[li].double(), sc[ri].double()
+            sm = torch.maximum(sl, sr)
+            if keep and li.numel() > keep:
                 if importance > 0:
-                    wgt = (Xv[:, 8].double() * sv.double()) ** importance
+                    wgt = sm ** importance
                     p = (wgt / wgt.sum()).cpu().numpy()
                     nz = int((p > 0).sum())
-                    sel = rng.choice(yv.numel(), size=min(keep, nz), replace=False, p=p)
+                    sel = rng.choice(li.numel(), size=min(keep, nz), replace=False, p=p)
                 else:
-                    sel = rng.choice(yv.numel(), size=keep, replace=False)
+                    sel = rng.choice(li.numel(), size=keep, replace=False)
                 sel = torch.as_tensor(sel, device="cuda")
-                Xv, yv = Xv[sel], yv[sel]
+                li, ri, sl, sr, sm = li[sel], ri[sel], sl[sel], sr[sel], sm[sel]
+            idx = torch.stack([li, ri], dim=1).reshape(-1)
+            Xv = X.view(ns, NFEAT)[idx]
+            yv = y[idx]
+            cv = torch.stack([-(sl / sm), sr / sm], dim=1).reshape(-1).float()
         self.stream.synchronize()
-        return Xv, yv
+        return Xv, yv, cv
 
     def run_draw(self, k, alpha, dt, steps, every_step, zmin, keep, rng, importance: float = 0.0):
-        """Fine run from the Landau state (k, alpha); pairs of its velocity
+        """Fine run from the Landau state (k, alpha); pairs of its spatial
         sweeps every `every_step` steps."""
         V.vp_init_f(self.fine.ctx, *_landau_ic(self.dims, k, alpha))
         self.fine.field()
-        Xs, ys = [], []
+        Xs, ys, cs = [], [], []
         for n in range(steps):
             take = (n + 1) % every_step == 0
             for sw in _sweeps(self.dims):
@@ -123,16 +147,17 @@ class Sampler:
                     self.fine.field()
                     continue
                 kick, d, fac = sw
-                if take and kick:
-                    X, y = self.samples(kick, d, fac * dt, zmin, keep, rng, importance)
+                if take and not kick:
+                    X, y, c = self.samples(kick, d, fac * dt, zmin, keep, rng, importance)
                     Xs.append(X)
                     ys.append(y)
+                    cs.append(c)
                 acc = self.fine.accel[d * self.fine.NX:] if kick else None
                 if kick:
                     V.vp_kick_sweep(self.fine.ctx, d, fac * dt, acc)
                 else:
                     V.vp_drift_sweep(self.fine.ctx, d, fac * dt)
-        return Xs, ys
+        return Xs, ys, cs
 
     def close(self):
         self.fine.close()
@@ -141,11 +166,11 @@ class Sampler:
 
 def he_init(seed: int = 0):
     """Initial parameters (W ~ N(0, 2 / fan_in), last layer x 0.1, zero biases),
-    laid out as W1[32][9] b1 W2[32][32] b2 W3[32][32] b3 w4[32] b4."""
+    laid out as W1[32][17] b1 W2[32][32] b2 W3[32][32] b3 w4[32] b4."""
     import torch
     g = torch.Generator().manual_seed(seed)
     parts = []
-    for rows, cols, scale in ((32, 9, 1.0), (32, 32, 1.0), (32, 32, 1.0), (1, 32, 0.1)):
+    for rows, cols, scale in ((32, NFEAT, 1.0), (32, 32, 1.0), (32, 32, 1.0), (1, 32, 0.1)):
         parts.append(torch.randn(rows * cols, generator=g) * math.sqrt(2.0 / cols) * scale)
         parts.append(torch.zeros(rows))
     w = torch.cat(parts)
@@ -154,8 +179,10 @@ def he_init(seed: int = 0):
 
 
 def train_net(X, y, iters: int = 1500, batch: int = 32768, lr: float = 2e-3, seed: int = 0, stream=None,
-              w0=None):
-    """Adam on the mean squared error over minibatches; returns (weights, losses).
+              w0=None, coef=None):
+    """Adam over minibatches; returns (weights, losses).  With coef the rows
+    are cell pairs (2m, 2m + 1) and the loss is the mean squared cell-update
+    residual sum_k coef_k (g_k - y_k); without, the mean squared error.
     w0: initial parameters (VP_NET_NPARAM floats, e.g. a He initialisation).
     Everything runs on the current torch stream (the minibatch gathers and
     the library's kernels must be ordered); `stream` is accepted for symmetry
@@ -172,14 +199,18 @@ def train_net(X, y, iters: int = 1500, batch: int = 32768, lr: float = 2e-3, see
     v = torch.zeros_like(w)
     grad = torch.zeros_like(w)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    n = y.numel()
+    group = 1 if coef is None else 2
+    n = y.numel() // group
     hist = []
     for it in range(1, iters + 1):
-        idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
+        idx = torch.randint(0, n, (min(batch // group, n),), device="cuda", generator=g)
+        if group == 2:
+            idx = torch.stack([2 * idx, 2 * idx + 1], dim=1).reshape(-1)
         Xb = X[idx].contiguous()
         yb = y[idx].contiguous()
+        cb = coef[idx].contiguous() if coef is not None else None
         loss.zero_()
-        V.vp_net_grad(Xb, yb, yb.numel(), w, grad, loss, stream)
+        V.vp_net_grad(Xb, yb, yb.numel(), w, grad, loss, stream, coef=cb, group=group)
         V.vp_net_adam(w, m, v, grad, it, lr * (0.1 ** (it / iters)), stream)
         if it % 50 == 0 or it == iters:
             hist.append(float(loss.item()))
@@ -211,7 +242,7 @@ def restricted_initial_state(dims: int, nx: int, nv_fine: int, factor: int, k: f
 
 def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision: int = V.VP_F32):
     """KDK run on `grid` from the state f0 with plain sweeps, or with learned
-    velocity sweeps when wts is given; returns the Simulation (caller closes)."""
+    spatial sweeps when wts is given; returns the Simulation (caller closes)."""
     sim = V.Simulation(grid, precision=precision, stream=stream)
     # f0 may still be in flight on the caller's stream
     sim.stream.wait_stream(sim.torch.cuda.current_stream())
@@ -219,6 +250,10 @@ def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision:
         sim.f.copy_(f0.to(sim.f.dtype))
     sim.field()
     dims = grid["dims"]
+    snap = None
+    if wts is not None:
+        with sim.torch.cuda.stream(sim.stream):
+            snap = sim.torch.empty_like(sim.f)  # f before each learned sweep (velocity neighbours)
     for _ in range(steps):
         for sw in _sweeps(dims):
             if sw is None:
@@ -226,10 +261,12 @@ def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision:
                 continue
             kick, d, fac = sw
             acc = sim.accel[d * sim.NX:] if kick else None
-            if kick and wts is not None:
-                V.vp_learned_sweep(sim.ctx, kick, d, fac * dt, acc, wts, 1)
-            elif kick:
+            if kick:
                 V.vp_kick_sweep(sim.ctx, d, fac * dt, acc)
+            elif wts is not None:
+                with sim.torch.cuda.stream(sim.stream):
+                    snap.copy_(sim.f)
+                V.vp_learned_sweep(sim.ctx, 0, d, fac * dt, None, wts, 1, snap)
             else:
                 V.vp_drift_sweep(sim.ctx, d, fac * dt)
     sim.sync()

@@ -121,13 +121,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_ensemble_step": (I, [P, D, I]),
             "vp_ensemble_sync": (I, [P]),
             "vp_ensemble_launch_count": (LL, [P]),
-            "vp_learned_sweep": (I, [P, I, I, D, P, P, I]),
+            "vp_learned_sweep": (I, [P, I, I, D, P, P, I, P]),
             "vp_fine_flux": (I, [P, I, I, D, P, I, P]),
             "vp_fluxnet_line_map": (I, [GP, GP, I, I, I, P, P, P]),
             "vp_group_mean": (I, [P, LL, I, P, I, D, P, P]),
             "vp_restrict_velocity": (I, [P, P, LL, I, I, I, I, P]),
             "vp_make_samples": (I, [P, I, I, D, P, P, D, P, P, P]),
-            "vp_net_grad": (I, [P, P, LL, P, P, P, P]),
+            "vp_net_grad": (I, [P, P, P, LL, I, P, P, P, P]),
             "vp_net_adam": (I, [P, P, P, P, I, ctypes.c_float, P]),
         }
         for name, (res, args) in sig.items():
@@ -360,7 +360,7 @@ def vp_ensemble_launch_count(ens) -> int:
 
 # ---- learned flux correction -----------------------------------------------------
 
-VP_NET_NPARAM = 2465
+VP_NET_NPARAM = 2721
 
 
 def _sh(stream):
@@ -372,8 +372,8 @@ def _rc(rc: int, what: str) -> None:
         raise VpError(rc, what)
 
 
-def vp_learned_sweep(ctx, kick: int, dim: int, dt: float, accel, wts, use_net: int = 1) -> None:
-    _check(ctx, load().vp_learned_sweep(ctx, kick, dim, dt, _ptr(accel), _ptr(wts), use_net))
+def vp_learned_sweep(ctx, kick: int, dim: int, dt: float, accel, wts, use_net: int = 1, f_snap=None) -> None:
+    _check(ctx, load().vp_learned_sweep(ctx, kick, dim, dt, _ptr(accel), _ptr(wts), use_net, _ptr(f_snap)))
 
 
 def vp_fine_flux(ctx, kick: int, dim: int, dt: float, accel, every: int, G) -> None:
@@ -410,8 +410,9 @@ def vp_make_samples(ctx, kick: int, dim: int, dt: float, accel, Gc, zmin: float,
                                        _ptr(scale)))
 
 
-def vp_net_grad(X, y, nsamp: int, wts, grad, loss, stream=None) -> None:
-    _rc(load().vp_net_grad(_ptr(X), _ptr(y), nsamp, _ptr(wts), _ptr(grad), _ptr(loss), _sh(stream)),
+def vp_net_grad(X, y, nsamp: int, wts, grad, loss, stream=None, coef=None, group: int = 1) -> None:
+    _rc(load().vp_net_grad(_ptr(X), _ptr(y), _ptr(coef), nsamp, group, _ptr(wts), _ptr(grad), _ptr(loss),
+                           _sh(stream)),
         "net grad")
 
 

@@ -22,6 +22,15 @@ def from_gpu(sim) -> np.ndarray:
     return sim.f.detach().cpu().numpy().astype(np.float64)
 
 
+def snapshot(sim):
+    """Copy of f once the library's queued work on it has finished."""
+    import torch
+    sim.sync()
+    s = sim.f.clone()
+    torch.cuda.synchronize()
+    return s
+
+
 def rel_max(a: np.ndarray, b: np.ndarray) -> float:
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 

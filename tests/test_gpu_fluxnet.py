@@ -1,5 +1,6 @@
 """Learned flux correction: training kernels against the FP64 reference,
-the learned sweep against the plain sweep and an oracle line update,
+the learned spatial sweep against the plain sweep and an oracle line update
+(with the velocity-neighbour features),
 conservation and positivity with the network on, the fine-flux extraction
 used to build training data, and what a trained network gains."""
 import math
@@ -12,7 +13,7 @@ from oracle import flux_net as N
 from paper_1702_08521_gb300 import inputs
 from paper_1702_08521_gb300 import vlasov as V
 
-from gpu_helpers import both, from_gpu, rel_l1, rel_max, to_gpu
+from gpu_helpers import both, from_gpu, rel_l1, rel_max, snapshot, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +47,28 @@ def test_net_gradients_match_reference():
     grad = torch.zeros_like(w)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     V.vp_net_grad(_t(X.ravel(), torch.float32), _t(y, torch.float32), B, w, grad, loss)
+    torch.cuda.synchronize()
+    assert loss.item() == pytest.approx(loss_ref, rel=1e-4)
+    gv = grad.double().cpu().numpy()
+    rv = N.pack(g_ref)
+    assert np.abs(gv - rv).max() <= 1e-2 * np.abs(rv).max()
+    assert np.linalg.norm(gv - rv) <= 1e-3 * np.linalg.norm(rv)
+
+
+def test_pair_loss_gradients_match_reference():
+    import torch
+    rng = np.random.default_rng(2)
+    p = _params(3)
+    B = 1000
+    X = _f32(rng.normal(size=(B, N.NFEAT)))
+    y = _f32(rng.normal(size=B))
+    a = _f32(rng.uniform(-1, 1, size=B))
+    loss_ref, g_ref = N.loss_and_grad(p, X, y, round_bf16=True, coef=a, group=2)
+    w = _t(N.pack(p), torch.float32)
+    grad = torch.zeros_like(w)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    V.vp_net_grad(_t(X.ravel(), torch.float32), _t(y, torch.float32), B, w, grad, loss,
+                  coef=_t(a, torch.float32), group=2)
     torch.cuda.synchronize()
     assert loss.item() == pytest.approx(loss_ref, rel=1e-4)
     gv = grad.double().cpu().numpy()
@@ -98,29 +121,34 @@ def test_learned_sweep_without_net_is_the_plain_sweep():
     sim.close()
 
 
-def _oracle_learned_line(line, s, p, bc):
-    """FP64 learned SL update of one line: CSL7 + s g, then MP, then PP (oracle)."""
+def _oracle_learned_line(line, up_line, um_line, s, p, bc):
+    """FP64 learned SL update of one line (oracle): mass nu MP(CSL7) + s g
+    through each interface, the PP limiter on that mass, flux-form update.
+    up_line / um_line: the velocity-neighbour lines (+: larger |v|)."""
     L = line.size
     n_int, zeta = O.shift_split(s)
     sg = -1 if zeta < 0 else 1
     nu = abs(zeta)
 
-    def val(k):
+    def val(a, k):
         if bc == O.BC_PERIODIC:
-            return line[k % L]
-        return line[k] if 0 <= k < L else 0.0
+            return a[k % L]
+        return a[k] if 0 <= k < L else 0.0
 
     def flux(q):  # upwind cell q of the shifted line, stencil in upwind order
-        u = np.array([val(q + sg * (k - 3)) for k in range(8)])
-        phi = O.csl_flux(7, nu, u[:7])
-        X, sc = N.features(u[None, :], np.array([nu]))
-        phi += sc[0] * N.forward(p, X)[0][0]
-        phi = O.mp_constraint(phi, u[:7], 4.0)
-        return O.pp_limiter(phi, u[3], u[4], nu)
+        idx = [q + sg * (k - 3) for k in range(8)]
+        u = np.array([val(line, i) for i in idx])
+        up = np.array([val(up_line, i) for i in idx])
+        um = np.array([val(um_line, i) for i in idx])
+        phi = O.mp_constraint(O.csl_flux(7, nu, u[:7]), u[:7], 4.0)
+        X, sc = N.features(u[None, :], up[None, :], um[None, :], np.array([nu]))
+        M = nu * phi + sc[0] * N.forward(p, X)[0][0]
+        # the PP limiter of the flux value M / nu (Eqs. 15-23), back to a mass
+        return nu * O.pp_limiter(M / nu, u[3], u[4], nu)
 
     out = np.empty(L)
     for i in range(L):
-        out[i] = val(i - n_int) - nu * (flux(i - n_int) - flux(i - n_int - sg))
+        out[i] = val(line, i - n_int) - (flux(i - n_int) - flux(i - n_int - sg))
     return out
 
 
@@ -132,14 +160,18 @@ def test_learned_sweep_matches_oracle_line_update():
     p = _params(7, scale=0.3)
     w = _t(N.pack(p), torch.float32)
     to_gpu(sim, f0)
-    V.vp_learned_sweep(sim.ctx, 0, 0, 0.37, None, w, 1)
+    V.vp_learned_sweep(sim.ctx, 0, 0, 0.37, None, w, 1, snapshot(sim))
     got = from_gpu(sim).reshape(24, 20)
     want = np.empty((24, 20))
     f2 = f0.reshape(24, 20)
     vc = og.v_centres(0)
+    zero = np.zeros(24)
     for j in range(20):
         s = vc[j] * 0.37 / (2.0 / 24)
-        want[:, j] = _oracle_learned_line(f2[:, j], s, p, O.BC_PERIODIC)
+        sp = 1 if vc[j] >= 0 else -1
+        up = f2[:, j + sp] if 0 <= j + sp < 20 else zero
+        um = f2[:, j - sp] if 0 <= j - sp < 20 else zero
+        want[:, j] = _oracle_learned_line(f2[:, j], up, um, s, p, O.BC_PERIODIC)
     # FP32 sums vs FP64 sums can move a bfloat16 rounding by one step
     assert rel_l1(got, want) <= 2e-3, rel_l1(got, want)
     sim.close()
@@ -156,7 +188,7 @@ def test_learned_sweep_conserves_mass_and_positivity():
     m0 = float(np.sum(f0, dtype=np.float64))
     for _ in range(3):
         for d in range(2):
-            V.vp_learned_sweep(sim.ctx, 0, d, 0.3, None, w, 1)
+            V.vp_learned_sweep(sim.ctx, 0, d, 0.3, None, w, 1, snapshot(sim))
     got = from_gpu(sim)
     assert got.min() >= 0.0
     assert abs(got.sum() - m0) / m0 <= 1e-6
@@ -199,4 +231,15 @@ def test_fine_flux_reproduces_the_sweep():
         got = np.empty(np.prod(shp))
         got[idx[rows].ravel()] = new.ravel()
         assert rel_max(got, ref) <= 1e-5, (kick, d, rel_max(got, ref))
+    sim.close()
+
+
+def test_learned_correction_rejects_velocity_sweeps():
+    import torch
+    g = _grid2d(8, 16)
+    sim, og = both(g, V.VP_F32)
+    w = torch.zeros(V.VP_NET_NPARAM, dtype=torch.float32, device="cuda")
+    acc = _t(inputs.random_accel(og.NX, 2, seed=4, amax=3.0)[0])
+    with pytest.raises(V.VpError):
+        V.vp_learned_sweep(sim.ctx, 1, 0, 0.4, acc, w, 1, snapshot(sim))
     sim.close()

@@ -58,10 +58,47 @@ def test_forward_closed_cases():
 
 def test_features_are_scale_invariant():
     rng = np.random.default_rng(4)
-    u = rng.random((10, 8))
+    u, up, um = rng.random((10, 8)), rng.random((10, 8)), rng.random((10, 8))
     nu = rng.uniform(0, 0.5, 10)
-    X1, s1 = N.features(u, nu)
-    X2, s2 = N.features(1e-6 * u, nu)
+    X1, s1 = N.features(u, up, um, nu)
+    X2, s2 = N.features(1e-6 * u, 1e-6 * up, 1e-6 * um, nu)
+    assert X1.shape == (10, N.NFEAT)
     assert np.allclose(X1, X2, rtol=1e-12, atol=1e-12)
     assert np.allclose(s2, 1e-6 * s1)
     assert np.all(X1[:, 3] == 0.0)
+    assert np.array_equal(X1[:, 16], nu)
+
+
+def test_features_velocity_difference():
+    # a line between neighbours that differ by a constant c has velocity
+    # features c / (2 s) everywhere; equal neighbours give zero
+    u = np.full((1, 8), 2.0)
+    X, s = N.features(u, u + 0.5, u - 0.5, np.array([0.25]))
+    assert np.allclose(X[0, 8:16], 0.5 / 2.0)
+    X, _ = N.features(u, u, u, np.array([0.25]))
+    assert np.all(X[0, 8:16] == 0.0)
+
+
+def test_pair_loss_gradients_match_finite_differences():
+    # the cell-update loss: groups of two with coefficients a_k
+    rng = np.random.default_rng(5)
+    p = N.init_params(6)
+    for k in p:
+        p[k] = p[k] + 0.05 * rng.normal(size=p[k].shape)
+    X = rng.normal(size=(30, N.NFEAT))
+    y = rng.normal(size=30)
+    a = rng.uniform(-1, 1, size=30)
+    loss, g = N.loss_and_grad(p, X, y, round_bf16=False, coef=a, group=2)
+    gx, _ = N.forward(p, X, round_bf16=False)
+    r = (a * (gx - y)).reshape(-1, 2).sum(axis=1)
+    assert loss == pytest.approx(float(np.mean(r * r)), rel=1e-12)
+    v, gv = N.pack(p), N.pack(g)
+    eps = 1e-6
+    for i in rng.choice(v.size, size=40, replace=False):
+        vp, vm = v.copy(), v.copy()
+        vp[i] += eps
+        vm[i] -= eps
+        lp, _ = N.loss_and_grad(N.unpack(vp), X, y, round_bf16=False, coef=a, group=2)
+        lm, _ = N.loss_and_grad(N.unpack(vm), X, y, round_bf16=False, coef=a, group=2)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - gv[i]) <= 1e-6 * (1 + abs(fd)), (i, fd, gv[i])
