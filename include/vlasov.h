@@ -289,8 +289,10 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
  * (use_net = 1, drifts only) or without it (use_net = 0: identical to
  * vp_drift_sweep / vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device);
  * f_snap_dev: a copy of f taken before the sweep (device, vp_num_cells
- * floats), read for the velocity neighbours, required when use_net = 1 and
- * ignored otherwise; in place.  VP_ENOTSUP for use_net with kick = 1. */
+ * floats), read for the velocity neighbours when use_net = 1; NULL: the
+ * library copies f into a buffer of its own (allocated on first use, freed
+ * by vp_destroy) on ctx's stream; ignored when use_net = 0; in place.
+ * VP_ENOTSUP for use_net with kick = 1. */
 int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
                      const float *wts_dev, int use_net, const float *f_snap_dev);
 

@@ -155,6 +155,7 @@ void free_buffers(vp_ctx *c) {
     cudaFree(c->d_diag);
     cudaFree(c->d_flag);
     cudaFree(c->d_status);
+    cudaFree(c->d_snap);
     if (c->graph.valid) cudaGraphExecDestroy(c->graph.exec);
 }
 

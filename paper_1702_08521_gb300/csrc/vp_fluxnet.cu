@@ -472,107 +472,277 @@ __global__ void k_group_mean(const double *__restrict__ Gf, long long ncl, int n
     Gc[t] = scale * s / group;
 }
 
-// ---- inference: the learned coarse sweep (strided or contiguous lines) ------------------
+// ---- inference: the learned coarse sweep, network on the tensor cores -------------------
 //
-// One thread per line of the coarse grid (coarse sweeps are small); the line
-// is read once into registers/shared memory; interface fluxes are computed
-// in the upwind direction as in the plain walk, with the network correction
-// added before the limiters.
-template <bool PERIODIC>
-__global__ void __launch_bounds__(128) k_learned_sweep(float *__restrict__ f, long long outer, int L,
-                                                       long long inner, int kick, int from_inner,
-                                                       long long cdiv, long long cmod,
-                                                       const double *__restrict__ accel, double lo,
-                                                       double dvel, double dt, double h, WPoly wp,
-                                                       const float *__restrict__ wts, float alpha,
-                                                       int use_net, const float *__restrict__ fsnap) {
-    extern __shared__ float lsm[];
-    float *w = lsm;                       // NPARAM rounded weights
-    float *line_buf = lsm + NPARAM + 3;   // [L + 2][blockDim] staged line (zero ghosts at 0, L+1)
-    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
-        w[i] = (i >= OFF_B4 || (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) ||
-                (i >= OFF_B3 && i < OFF_W4))
-                   ? wts[i]
-                   : bfr(wts[i]);
-    __syncthreads();
-    const int T = blockDim.x;
-    const long long line = (long long)blockIdx.x * T + threadIdx.x;
-    if (line >= outer * inner) return;
-    const long long o = line / inner, c = line % inner;
-    float *base = f + o * L * inner + c;
-    float *sl = line_buf + threadIdx.x;  // row r at sl[(r + 1) * T]
-    sl[0] = 0.f;
-    sl[(L + 1) * T] = 0.f;
-    for (int r = 0; r < L; ++r) sl[(r + 1) * T] = base[(long long)r * inner];
-    const long long cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
-    const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
-    const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, wp);
-    const int sg = sh.sigma;
-    const float nu = sh.nu;
-    int n = sh.n;
-    if (PERIODIC) {
-        n %= L;
-        if (n < 0) n += L;
-    }
-    auto ld = [&](int q) -> float {  // row q of the line (any integer)
-        if (PERIODIC) {
-            q %= L;
-            if (q < 0) q += L;
-        } else {
-            q = min(max(q, -1), L);
-        }
-        return sl[(q + 1) * T];
-    };
-    // velocity-neighbour lines (+: larger |v|) in the snapshot taken before
-    // the sweep; a neighbour outside the velocity box reads as zero
-    const int sp = speed >= 0.0 ? 1 : -1;
-    const long long J = use_net && !kick ? (c / cdiv) % cmod : 0;
-    const float *snap_p = (use_net && !kick && J + sp >= 0 && J + sp < cmod) ? fsnap + o * L * inner + c + sp * cdiv
-                                                                            : nullptr;
-    const float *snap_m = (use_net && !kick && J - sp >= 0 && J - sp < cmod) ? fsnap + o * L * inner + c - sp * cdiv
-                                                                            : nullptr;
-    auto nld = [&](const float *nb, int q) -> float {  // row q of a neighbour line
-        if (!nb) return 0.f;
-        if (PERIODIC) {
-            q %= L;
-            if (q < 0) q += L;
-        } else if (q < 0 || q >= L) {
-            return 0.f;
-        }
-        return nb[(long long)q * inner];
-    };
-    // mass through the interface whose upwind cell is q (upwind-ordered
-    // stencil): nu times the MP-limited CSL7 flux, plus the network's mass
-    // correction, then the PP limiter on the total
-    auto iface = [&](int q) -> float {
-        float u[8];
+// A CTA takes NL consecutive lines of the sweep.  Phase 0 stages the lines,
+// their velocity-difference lines (u+ - u-) / 2 from the snapshot and the
+// lines' shift decompositions in shared memory (consecutive threads read
+// consecutive lines: coalesced for strided sweeps).  Phase 1: warps take
+// 16-interface tiles; the four lanes of an MMA row group build that row's
+// features straight into the A fragments (lane t holds stencil positions
+// 2t, 2t + 1; the stencil maximum by a group shuffle), the network runs
+// with mma.sync (bf16 inputs, FP32 accumulation; each layer's accumulators
+// are re-packed as the next layer's A fragments in registers), and lanes 0 /
+// 1 of the group add the plain MP mass, apply the PP limiter and store the
+// interface mass.  Phase 2: one thread per cell writes the flux-form update.
+// Interface k of a line is the k-th one the upwind walk meets: its upwind
+// cell is q_k = q_0 + k sigma, q_0 = (sigma > 0 ? 0 : L - 1) - n - sigma;
+// the k-th cell of the walk (k >= 1) takes M_{k-1} in and M_k out.
+
+constexpr int kTcThreads = 128;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ReLU, round to bf16 and re-pack accumulators as the next layer's A fragments
+__device__ __forceinline__ void relu_pack(const float (&acc)[4][4], uint32_t (&a)[2][4]) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) u[k] = ld(q + sg * (k - 3));
+    for (int kb = 0; kb < 2; ++kb) {
+        a[kb][0] = pack_bf16(fmaxf(acc[2 * kb][0], 0.f), fmaxf(acc[2 * kb][1], 0.f));
+        a[kb][1] = pack_bf16(fmaxf(acc[2 * kb][2], 0.f), fmaxf(acc[2 * kb][3], 0.f));
+        a[kb][2] = pack_bf16(fmaxf(acc[2 * kb + 1][0], 0.f), fmaxf(acc[2 * kb + 1][1], 0.f));
+        a[kb][3] = pack_bf16(fmaxf(acc[2 * kb + 1][2], 0.f), fmaxf(acc[2 * kb + 1][3], 0.f));
+    }
+}
+
+// per-line data of a learned-sweep CTA
+struct LLine {
+    long long base;  // offset of row 0
+    int sp;          // +1 / -1: the velocity neighbour with larger |v| is at +sp
+    int has_p, has_m;
+    int q0;          // upwind cell of the walk's first interface (unwrapped)
+};
+
+constexpr int kLG = 8;  // staged rows on each side of a learned-sweep line
+
+template <bool PERIODIC>
+__global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict__ f, long long outer, int L,
+                                                              long long inner, int kick, int from_inner,
+                                                              long long cdiv, long long cmod,
+                                                              const double *__restrict__ accel, double lo,
+                                                              double dvel, double dt, double h, WPoly wp,
+                                                              const float *__restrict__ wts, float alpha,
+                                                              int use_net, const float *__restrict__ fsnap,
+                                                              int lgNL) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const int NL = 1 << lgNL;
+    const int NI = NL * (L + 1);  // interface e = k * NL + l (line l, k-th interface of its walk)
+    const int LP = L + 2 * kLG;   // staged rows: -kLG .. L + kLG - 1
+    uint32_t *wfrag = reinterpret_cast<uint32_t *>(tsm);  // [3][2][4][32 lanes][2] B fragments
+    float *wvec = reinterpret_cast<float *>(wfrag + 3 * 2 * 4 * 32 * 2);  // b1 b2 b3 w4(bf16) b4: 129
+    LineShift<float> *shs = reinterpret_cast<LineShift<float> *>(wvec + 132);
+    LLine *lls = reinterpret_cast<LLine *>(shs + NL);
+    float *lines = reinterpret_cast<float *>(lls + NL);  // [LP][NL], row r at (r + kLG)
+    float *dvl = lines + NL * LP;                         // [LP][NL] velocity differences
+    float *mass = dvl + NL * LP;                          // [L + 1][NL] interface masses
+    const long long nlines = outer * inner;
+    const long long l0 = (long long)blockIdx.x * NL;
+    const int nl = (int)(nlines - l0 < NL ? nlines - l0 : NL);
+    // phase 0: network fragments, per-line data, then lines and velocity differences
+    if (use_net) {
+        for (int e = threadIdx.x; e < 3 * 2 * 4 * 32; e += blockDim.x) {
+            const int lane = e & 31, frag = e >> 5;  // frag = (layer * 2 + kb) * 4 + nt
+            const int nt = frag & 3, kb = (frag >> 2) & 1, layer = frag >> 3;
+            const int off = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
+            const int kin = layer == 0 ? NF : H;
+            const int n = 8 * nt + (lane >> 2), k0 = 16 * kb + 2 * (lane & 3), k1 = k0 + 8;
+            auto wv = [&](int k) { return k < kin ? wts[off + n * kin + k] : 0.f; };
+            wfrag[2 * e] = pack_bf16(wv(k0), wv(k0 + 1));
+            wfrag[2 * e + 1] = pack_bf16(wv(k1), wv(k1 + 1));
+        }
+        for (int e = threadIdx.x; e < 4 * H + 1; e += blockDim.x) {
+            const int grp = e / H, n = e - grp * H;
+            wvec[e] = grp == 0 ? wts[OFF_B1 + n]
+                      : grp == 1 ? wts[OFF_B2 + n]
+                      : grp == 2 ? wts[OFF_B3 + n]
+                      : grp == 3 ? bfr(wts[OFF_W4 + n])
+                                 : wts[OFF_B4];
+        }
+    }
+    for (int l = threadIdx.x; l < NL; l += blockDim.x) {
+        LLine ll{0, 1, 0, 0, 0};
+        LineShift<float> sh{};
+        sh.sigma = 1;
+        if (l < nl) {
+            const long long line = l0 + l;
+            const long long o = line / inner, c = line % inner;
+            const long long cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
+            const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
+            sh = vp_core::make_shift<float>(speed, dt, h, wp);
+            ll.base = o * L * inner + c;
+            if (use_net && !kick) {
+                ll.sp = speed >= 0.0 ? 1 : -1;
+                ll.has_p = cls + ll.sp >= 0 && cls + ll.sp < cmod;
+                ll.has_m = cls - ll.sp >= 0 && cls - ll.sp < cmod;
+            }
+            int n = sh.n;
+            if (PERIODIC) {  // the shift modulo L, nearest to zero
+                n %= L;
+                if (n > L / 2) n -= L;
+                if (n < -(L / 2)) n += L;
+                sh.n = n;
+            }
+            ll.q0 = (sh.sigma > 0 ? 0 : L - 1) - n - sh.sigma;
+        }
+        shs[l] = sh;
+        lls[l] = ll;
+    }
+    __syncthreads();
+    const int lt = threadIdx.x & (NL - 1), rt = threadIdx.x >> lgNL, rstep = blockDim.x >> lgNL;
+    if (lt < nl) {
+        const LLine ll = lls[lt];
+        for (int r = rt; r < LP; r += rstep) {
+            int rr = r - kLG;  // line row
+            bool in = true;
+            if (PERIODIC) {
+                while (rr < 0) rr += L;
+                while (rr >= L) rr -= L;
+            } else {
+                in = rr >= 0 && rr < L;
+            }
+            float v = 0.f, d = 0.f;
+            if (in) {
+                const long long a = ll.base + (long long)rr * inner;
+                v = f[a];
+                if (use_net && !kick) {
+                    const float up = ll.has_p ? fsnap[a + ll.sp * cdiv] : 0.f;
+                    const float um = ll.has_m ? fsnap[a - ll.sp * cdiv] : 0.f;
+                    d = 0.5f * (up - um);
+                }
+            }
+            lines[r * NL + lt] = v;
+            dvl[r * NL + lt] = d;
+        }
+    }
+    __syncthreads();
+    // row q of staged line l: direct inside the staged rows, wrapped (periodic)
+    // or zero (outflow) beyond them (only for shifts of more than kLG - 5 cells)
+    auto row = [&](const float *ln, int l, int q) -> float {
+        if (q < -kLG || q >= L + kLG) {
+            if (!PERIODIC) return 0.f;
+            while (q < 0) q += L;
+            while (q >= L) q -= L;
+        }
+        return ln[(q + kLG) * NL + l];
+    };
+    // phase 1a: plain mass of every interface (CSL7, MP); without the
+    // network also the PP limiter
+    for (int e = threadIdx.x; e < NI; e += blockDim.x) {
+        const int l = e & (NL - 1), k = e >> lgNL;
+        if (l >= nl) continue;
+        const LineShift<float> &sh = shs[l];
+        const int sg = sh.sigma;
+        const int q = lls[l].q0 + k * sg;
+        float u[7];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) u[m] = row(lines, l, q + sg * (m - 3));
         float phi = sh.w[0] * u[0];
 #pragma unroll
-        for (int k = 1; k < 7; ++k) phi = fmaf(sh.w[k], u[k], phi);
+        for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
         phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
-        float M = nu * phi;
-        if (use_net) {
-            float x[NF], h1[H], h2[H], unp[8], unm[8];
+        const float M = sh.nu * phi;
+        mass[e] = use_net ? M : pp_mass(M, u[3], u[4], sh.nu);
+    }
+    __syncthreads();
+    // phase 1b: the network on the tensor cores adds s g, then the PP limiter
+    if (use_net) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, t = lane & 3;
+        const uint2 *wf2 = reinterpret_cast<const uint2 *>(wfrag);
+        const int ntiles = (NI + 15) / 16;
+        for (int tile = warp; tile < ntiles; tile += blockDim.x / 32) {
+            uint32_t a[2][4];
+            float sr[2];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                unp[k] = nld(snap_p, q + sg * (k - 3));
-                unm[k] = nld(snap_m, q + sg * (k - 3));
+            for (int hr = 0; hr < 2; ++hr) {  // rows gq and gq + 8 of the tile
+                const int e = tile * 16 + gq + 8 * hr;
+                const int l = e & (NL - 1), k = e >> lgNL;
+                float x0 = 0.f, x1 = 0.f, d0 = 0.f, d1 = 0.f, nu = 0.f;
+                if (e < NI && l < nl) {
+                    const int sg = shs[l].sigma;
+                    const int q = lls[l].q0 + k * sg;
+                    x0 = row(lines, l, q + sg * (2 * t - 3));
+                    x1 = row(lines, l, q + sg * (2 * t - 2));
+                    d0 = row(dvl, l, q + sg * (2 * t - 3));
+                    d1 = row(dvl, l, q + sg * (2 * t - 2));
+                    nu = shs[l].nu;
+                }
+                float s = fmaxf(fabsf(x0), fabsf(x1));
+                s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, 1));
+                s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, 2));
+                s += 1e-30f;
+                // u_0 of the stencil is position 3: lane t = 1, second value
+                const float u0 = __shfl_sync(0xffffffffu, x1, (lane & ~3) | 1);
+                const float inv = 1.0f / s;
+                a[0][hr] = pack_bf16((x0 - u0) * inv, (x1 - u0) * inv);
+                a[0][2 + hr] = pack_bf16(d0 * inv, d1 * inv);
+                a[1][hr] = pack_bf16(t == 0 ? nu : 0.f, 0.f);
+                a[1][2 + hr] = 0u;
+                sr[hr] = s;
             }
-            const float s = net_features(u, unp, unm, nu, x);
-            M = fmaf(s, net_forward(w, x, h1, h2, nullptr), M);
+            float acc[4][4];
+#pragma unroll
+            for (int layer = 0; layer < 3; ++layer) {
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const float b0 = wvec[layer * H + 8 * nt + 2 * t], b1v = wvec[layer * H + 8 * nt + 2 * t + 1];
+                    acc[nt][0] = acc[nt][2] = b0;
+                    acc[nt][1] = acc[nt][3] = b1v;
+#pragma unroll
+                    for (int kb = 0; kb < 2; ++kb) {
+                        const uint2 bb = wf2[((layer * 2 + kb) * 4 + nt) * 32 + lane];
+                        mma_bf16(acc[nt], a[kb], bb.x, bb.y);
+                    }
+                }
+                if (layer < 2) relu_pack(acc, a);
+            }
+            // output g = b4 + w4 . bf16(relu(h3)) for rows gq and gq + 8
+            float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float w4v = wvec[3 * H + 8 * nt + 2 * t + j];
+                    p0 = fmaf(w4v, bfr(fmaxf(acc[nt][j], 0.f)), p0);
+                    p1 = fmaf(w4v, bfr(fmaxf(acc[nt][2 + j], 0.f)), p1);
+                }
+            p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+            p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+            if (t < 2) {
+                const int e = tile * 16 + gq + 8 * t;
+                const int l = e & (NL - 1), k = e >> lgNL;
+                if (e < NI && l < nl) {
+                    const int sg = shs[l].sigma;
+                    const int q = lls[l].q0 + k * sg;
+                    mass[e] = pp_mass(fmaf(sr[t], wvec[4 * H] + (t == 0 ? p0 : p1), mass[e]), row(lines, l, q),
+                                      row(lines, l, q + sg), shs[l].nu);
+                }
+            }
         }
-        return pp_mass(M, u[3], u[4], nu);
-    };
-    // new values into registers of the staged line is not possible in place
-    // (neighbours still read old values): compute all, then write
-    float fin = iface((sg > 0 ? 0 : L - 1) - n - sg);
-    for (int t = 0; t < L; ++t) {
-        const int i = sg > 0 ? t : L - 1 - t;
-        const float fout = iface(i - n);
-        base[(long long)i * inner] = ld(i - n) - (fout - fin);
-        fin = fout;
+    }
+    __syncthreads();
+    // phase 2: the flux-form update, one thread per cell (consecutive
+    // threads: consecutive lines)
+    if (lt < nl) {
+        const int sg = shs[lt].sigma, q0 = lls[lt].q0;
+        const long long base = lls[lt].base;
+        for (int kr = rt; kr < L; kr += rstep) {
+            const int k = kr + 1;                  // the cell between interfaces k - 1 and k
+            const int i = sg > 0 ? k - 1 : L - k;  // the k-th cell of the walk
+            const float v = row(lines, lt, q0 + k * sg) - (mass[k * NL + lt] - mass[(k - 1) * NL + lt]);
+            f[base + (long long)i * inner] = v;
+        }
     }
 }
 
@@ -655,25 +825,40 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     if (c->g.precision != VP_F32 || c->g.order != 7)
         return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
     if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
-    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && (!wts || !f_snap)) ||
-        !std::isfinite(dt))
+    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
         return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
+    if (use_net && !f_snap) {
+        // snapshot of f before the sweep in a library-owned buffer
+        const size_t bytes = (size_t)c->ncell * sizeof(float);
+        if (!c->d_snap) VP_CUDA_TRY(c, cudaMalloc(&c->d_snap, bytes));
+        VP_CUDA_TRY(c, cudaMemcpyAsync(c->d_snap, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        f_snap = static_cast<const float *>(c->d_snap);
+    }
     const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
-    const int T = 128;
-    const size_t smem = (size_t)(NPARAM + 3 + (q.L + 2) * T) * sizeof(float);
+    // lines per CTA: a power of two, at most 16, within ~24 KB of shared memory
+    // (several CTAs per SM hide the latency of the layer chain)
+    auto smem_for = [&](int nl) {
+        return (size_t)3 * 2 * 4 * 32 * 2 * sizeof(uint32_t) + 132 * sizeof(float) +
+               nl * (sizeof(LineShift<float>) + sizeof(LLine)) + 2 * (size_t)nl * (q.L + 2 * kLG) * sizeof(float) +
+               (size_t)nl * (q.L + 1) * sizeof(float);
+    };
+    int lgNL = 4;
+    while (lgNL > 0 && smem_for(1 << lgNL) > 24 * 1024) --lgNL;
+    const int NL = 1 << lgNL;
+    const size_t smem = smem_for(NL);
     if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line too long for the learned sweep");
     const long long nl = q.outer * q.inner;
-    const unsigned blocks = (unsigned)((nl + T - 1) / T);
+    const unsigned blocks = (unsigned)((nl + NL - 1) / NL);
     cudaFuncSetAttribute(k_learned_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_learned_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (q.periodic)
-        k_learned_sweep<true><<<blocks, T, smem, c->stream>>>(
+        k_learned_sweep<true><<<blocks, kTcThreads, smem, c->stream>>>(
             static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
-            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap);
+            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap, lgNL);
     else
-        k_learned_sweep<false><<<blocks, T, smem, c->stream>>>(
+        k_learned_sweep<false><<<blocks, kTcThreads, smem, c->stream>>>(
             static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
-            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap);
+            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap, lgNL);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;

@@ -120,6 +120,7 @@ struct vp_ctx {
     int *d_flag;                        // non-finite flag
     long long launches;
     int *d_status;                      // device-side error word (bounded waits)
+    void *d_snap;                       // copy of f before a learned sweep (allocated on first use)
     int opt_impl;                       // 0 auto, 1 staged, 2 TMA
     int opt_autotune;                   // 1: time candidate tiles on first use
     SweepTune tune[2][3];               // [kick][dim]

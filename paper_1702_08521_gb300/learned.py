@@ -250,10 +250,6 @@ def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision:
         sim.f.copy_(f0.to(sim.f.dtype))
     sim.field()
     dims = grid["dims"]
-    snap = None
-    if wts is not None:
-        with sim.torch.cuda.stream(sim.stream):
-            snap = sim.torch.empty_like(sim.f)  # f before each learned sweep (velocity neighbours)
     for _ in range(steps):
         for sw in _sweeps(dims):
             if sw is None:
@@ -264,9 +260,8 @@ def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision:
             if kick:
                 V.vp_kick_sweep(sim.ctx, d, fac * dt, acc)
             elif wts is not None:
-                with sim.torch.cuda.stream(sim.stream):
-                    snap.copy_(sim.f)
-                V.vp_learned_sweep(sim.ctx, 0, d, fac * dt, None, wts, 1, snap)
+                # the library takes the snapshot of f the velocity neighbours need
+                V.vp_learned_sweep(sim.ctx, 0, d, fac * dt, None, wts, 1)
             else:
                 V.vp_drift_sweep(sim.ctx, d, fac * dt)
     sim.sync()
