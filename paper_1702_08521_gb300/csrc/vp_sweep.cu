@@ -569,6 +569,7 @@ SweepTune default_tune(const vp_ctx *c, const SweepGeo &geo) {
     } else {
         int R = 4096 / L;
         R = R < 32 ? 32 : (R > 128 ? 128 : R);
+        while (R > 1 && rows_smem<T>(L, R, ghost_rows(geo)) > 96 * 1024) R /= 2;  // long lines
         int nseg = L / 16;
         const int maxseg = 256 / R > 0 ? 256 / R : 1;
         nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
@@ -599,7 +600,8 @@ int tune_t(vp_ctx *c, int kick, int dim) {
     if (kick) VP_CUDA_TRY(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * c->NX, c->stream));
     int rc = vp_launch_shift_table(c, kick, dim, 0.0, kick ? c->d_acc : nullptr);
     if (rc) return rc;
-    SweepTune cand[32];
+    constexpr int kMaxCand = 48;
+    SweepTune cand[kMaxCand];
     int nc = 0;
     if (geo.inner > 1) {
         const int impls[2] = {2, 1};
@@ -611,17 +613,20 @@ int tune_t(vp_ctx *c, int kick, int dim) {
                     if (th < 64 || th > 512 || nseg > geo.L) continue;
                     const int Weff = geo.inner < W ? (int)geo.inner : W;
                     if (impls[ii] == 2 && !tma_eligible<T>(c, geo, Weff)) continue;
-                    if (impls[ii] == 1 && (size_t)(geo.L + 2) * W * sizeof(T) > 200 * 1024) continue;
-                    if (nc < 32) cand[nc++] = SweepTune{1, impls[ii], W, nseg, 0};
+                    if (impls[ii] == 1 && (size_t)(geo.L + 2 * ghost_rows(geo)) * W * sizeof(T) > 200 * 1024)
+                        continue;
+                    if (nc < kMaxCand) cand[nc++] = SweepTune{1, impls[ii], W, nseg, 0};
                 }
         }
     } else {
-        for (int R = 32; R <= 128; R *= 2)
-            for (int nseg = 1; nseg <= 8; nseg *= 2) {
+        // long lines take fewer lines per CTA (the staged tile must fit) and
+        // more segments per line (segments of at least 8 cells)
+        for (int R = 8; R <= 128; R *= 2)
+            for (int nseg = 1; nseg <= 64; nseg *= 2) {
                 const int th = R * nseg;
-                if (th < 64 || th > 512 || nseg > geo.L) continue;
+                if (th < 64 || th > 512 || nseg * 8 > geo.L) continue;
                 if (rows_smem<T>(geo.L, R, ghost_rows(geo)) > 200 * 1024) continue;
-                if (nc < 32) cand[nc++] = SweepTune{1, 1, R, nseg, 0};
+                if (nc < kMaxCand) cand[nc++] = SweepTune{1, 1, R, nseg, 0};
             }
     }
     if (nc == 0) {

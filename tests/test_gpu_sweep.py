@@ -28,6 +28,7 @@ CASES = [
     (1, [37], [45]),
     (1, [64], [130]),
     (1, [300], [33]),
+    (1, [6], [1024]),  # long contiguous lines: few lines per CTA, many segments
     (2, [9, 7], [10, 12]),
     (2, [16, 5], [33, 8]),
     (3, [5, 6, 4], [6, 5, 8]),
