@@ -72,6 +72,7 @@ struct EnsParams {
     int W, R;          // tile widths of strided / contiguous sweeps
     int xpt;           // spatial points per density tile
     WPoly wp;
+    float wpf[7][7];   // the weight polynomials' coefficients in FP32 (wp.c)
 };
 
 // ---- device helpers ----------------------------------------------------------------
@@ -92,9 +93,34 @@ __device__ bool wait_count(const unsigned *ctr, unsigned target) {
     return false;
 }
 
+// Shift decomposition of one line as in the single-run sweeps (reading R2:
+// s = c dt / h and its integer split in FP64, so the integer part is exact),
+// with the CSL weight polynomials evaluated in FP32 at nu: the FP64 pipe of
+// this GPU is narrow and every tile recomputes its lines' shifts.
+__device__ __forceinline__ LineShift<float> ens_shift(double speed, double dt, double h, const EnsParams &P) {
+    const double sv = __ddiv_rn(__dmul_rn(speed, dt), h);
+    double n = round(sv);
+    const double z = __dadd_rn(sv, -n);
+    const float nu = (float)fabs(z);
+    LineShift<float> sh;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        float acc = 0.f;
+        for (int j = P.wp.nterm - 1; j >= 0; --j) acc = fmaf(acc, nu, P.wpf[j][k]);
+        sh.w[k] = acc;
+    }
+    n = fmin(fmax(n, -1.0e9), 1.0e9);
+    sh.nu = nu;
+    sh.n = (int)n;
+    sh.sigma = z < 0.0 ? -1 : 1;
+    return sh;
+}
+
 template <int ORDER, bool PER>
 __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int tile,
                           const double *acc_pool, const EnsParams &P, float *sm) {
+    // zero-inflow lines get VP_GHOST zero rows on each side (direct walks)
+    constexpr int GP = PER ? 0 : VP_GHOST;
     const int L = s.L;
     const int W = s.tw;
     const long long tpo = (s.inner + W - 1) / W;
@@ -102,13 +128,35 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
     const long long c0 = (tile % tpo) * W;
     const int wc = (int)((s.inner - c0) < W ? (s.inner - c0) : W);
     float *base = pool + r.f_off + o * L * s.inner + c0;
-    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    float *data = sm + GP * W;  // row 0
+    for (int c = threadIdx.x; c < GP * W; c += blockDim.x) {
         sm[c] = 0.f;
-        sm[(L + 1) * W + c] = 0.f;
+        data[L * W + c] = 0.f;
     }
-    for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
-        const int row = e / W, cc = e - row * W;
-        sm[W + e] = cc < wc ? ldcg(base + (long long)row * s.inner + cc) : 0.f;
+    // staging: four rows per thread in flight; (row, column) advanced
+    // incrementally
+    {
+        const int dr = blockDim.x / W, dc = blockDim.x - dr * W;
+        int row = threadIdx.x / W, cc = threadIdx.x - row * W;
+        for (int e = threadIdx.x; e < L * W; e += 4 * blockDim.x) {
+            float v[4];
+            int rr[4], cq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                rr[u] = row;
+                cq[u] = cc;
+                v[u] = (e + u * (int)blockDim.x < L * W && cc < wc) ? ldcg(base + (long long)row * s.inner + cc) : 0.f;
+                row += dr;
+                cc += dc;
+                if (cc >= W) {
+                    cc -= W;
+                    ++row;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u * (int)blockDim.x < L * W) data[rr[u] * W + cq[u]] = v[u];
+        }
     }
     __syncthreads();
     const int nseg = blockDim.x / W;
@@ -124,7 +172,7 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
             speed = vp_core::cell_centre(r.vlo[s.axis], r.hv[s.axis], (int)cls);
             h = r.hx[s.axis];
         }
-        const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, h, P.wp);
+        const LineShift<float> sh = ens_shift(speed, dt, h, P);
         const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         struct St {
@@ -135,27 +183,50 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
                 p += step;
             }
         } st{base + cc + (long long)i0 * s.inner, (long long)sh.sigma * s.inner};
-        vp_core::walk<float, ORDER, PER, true, 1>(sm + W + cc, W, L, sh, r0, r1, (float)P.alpha, P.mp, P.pp, st);
+        vp_core::walk<float, ORDER, PER, true, PER ? 1 : VP_GHOST>(data + cc, W, L, sh, r0, r1, (float)P.alpha,
+                                                                    P.mp, P.pp, st);
     }
 }
 
 template <int ORDER>
 __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int tile,
                           const double *acc_pool, const EnsParams &P, float *sm) {
+    constexpr int GP = VP_GHOST;  // velocity lines: zero inflow
     const int L = s.L;
     const int R = s.tw;
-    const int Pp = (L + 2) | 1, Q = L | 1;
+    const int Pp = (L + 2 * GP) | 1, Q = L | 1;
     float *in = sm, *out = sm + R * Pp;
     const long long l0 = (long long)tile * R;
     const int nl = (int)((s.outer - l0) < R ? (s.outer - l0) : R);
     float *base = pool + r.f_off + l0 * L;
-    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
-        in[k * Pp] = 0.f;
-        in[k * Pp + L + 1] = 0.f;
+    for (int k = threadIdx.x; k < nl * GP; k += blockDim.x) {
+        const int ln = k / GP, g = k - ln * GP;
+        in[ln * Pp + g] = 0.f;
+        in[ln * Pp + GP + L + g] = 0.f;
     }
-    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
-        const int row = e / L, pos = e - row * L;
-        in[row * Pp + 1 + pos] = ldcg(base + e);
+    const int tot = nl * L;
+    const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
+    {
+        int row = threadIdx.x / L, pos = threadIdx.x - row * L;
+        for (int e = threadIdx.x; e < tot; e += 4 * blockDim.x) {
+            float v[4];
+            int at[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int eu = e + u * (int)blockDim.x;
+                at[u] = row * Pp + GP + pos;
+                v[u] = eu < tot ? ldcg(base + eu) : 0.f;
+                row += dr;
+                pos += dp;
+                if (pos >= L) {
+                    pos -= L;
+                    ++row;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u * (int)blockDim.x < tot) in[at[u]] = v[u];
+        }
     }
     __syncthreads();
     const int nseg = blockDim.x / R;
@@ -164,7 +235,7 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
         const unsigned cls = (unsigned)((l0 + line) / s.cdiv);
         const double dt = s.half ? 0.5 * P.dt : P.dt;
         const double speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
-        const LineShift<float> sh = vp_core::make_shift<float>(speed, dt, r.hv[s.axis], P.wp);
+        const LineShift<float> sh = ens_shift(speed, dt, r.hv[s.axis], P);
         const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         struct St {
@@ -175,13 +246,21 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
                 p += step;
             }
         } st{out + line * Q + i0, sh.sigma};
-        vp_core::walk<float, ORDER, false, true, 1>(in + line * Pp + 1, 1, L, sh, r0, r1, (float)P.alpha, P.mp,
-                                                    P.pp, st);
+        vp_core::walk<float, ORDER, false, true, GP>(in + line * Pp + GP, 1, L, sh, r0, r1, (float)P.alpha, P.mp,
+                                                     P.pp, st);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
-        const int row = e / L, pos = e - row * L;
-        base[e] = out[row * Q + pos];
+    {
+        int row = threadIdx.x / L, pos = threadIdx.x - row * L;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            base[e] = out[row * Q + pos];
+            row += dr;
+            pos += dp;
+            if (pos >= L) {
+                pos -= L;
+                ++row;
+            }
+        }
     }
 }
 
@@ -381,9 +460,9 @@ size_t smem_need(const std::vector<RunDesc> &runs) {
             const StageDesc &s = r.st[k];
             size_t b = 0;
             if (s.kind == ST_COLS) {
-                b = (size_t)(s.L + 2) * s.tw * sizeof(float);
+                b = (size_t)(s.L + (s.periodic ? 0 : 2 * VP_GHOST)) * s.tw * sizeof(float);
             } else if (s.kind == ST_ROWS) {
-                b = (size_t)s.tw * (((s.L + 2) | 1) + (s.L | 1)) * sizeof(float);
+                b = (size_t)s.tw * (((s.L + 2 * VP_GHOST) | 1) + (s.L | 1)) * sizeof(float);
             } else if (s.kind == ST_POISSON) {
                 b = (size_t)r.NX * sizeof(double2);
             }
@@ -446,7 +525,7 @@ static int build_stages(RunDesc &r, int W, int R, int xpt, int &slot) {
         s.cmod = cmod;
         // tile width: the requested W, halved until the staged tile fits 36 KB
         int w = W;
-        while (w > 8 && (size_t)(L + 2) * w * sizeof(float) > 36 * 1024) w /= 2;
+        while (w > 8 && (size_t)(L + (per ? 0 : 2 * VP_GHOST)) * w * sizeof(float) > 36 * 1024) w /= 2;
         if (inner < w) w = (int)inner;
         s.tw = w;
         s.tiles = (int)(outer * ((inner + w - 1) / w));
@@ -464,7 +543,7 @@ static int build_stages(RunDesc &r, int W, int R, int xpt, int &slot) {
         s.cdiv = cdiv;
         s.cmod = 1;
         int rr = R;
-        while (rr > 8 && (size_t)rr * (((L + 2) | 1) + (L | 1)) * sizeof(float) > 36 * 1024) rr /= 2;
+        while (rr > 8 && (size_t)rr * (((L + 2 * VP_GHOST) | 1) + (L | 1)) * sizeof(float) > 36 * 1024) rr /= 2;
         s.tw = rr;
         s.tiles = (int)((outer + rr - 1) / rr);
         return s;
@@ -581,6 +660,8 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
     e->P.R = 32;
     e->P.xpt = 8;
     e->P.wp = vp_csl_weight_polys(order);
+    for (int j = 0; j < 7; ++j)
+        for (int k = 0; k < 7; ++k) e->P.wpf[j][k] = (float)e->P.wp.c[j][k];
     long long off = 0, aoff = 0, roff = 0;
     int slot = 0;
     for (int i = 0; i < nruns; ++i) {
