@@ -30,6 +30,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxStages = 8;
+// shared-memory budget of one sweep tile (three CTAs per SM at 256 threads)
+constexpr size_t kTileBytes = 56 * 1024;
 
 enum StageKind { ST_COLS = 0, ST_ROWS = 1, ST_MOMENT = 2, ST_POISSON = 3 };
 
@@ -94,11 +96,11 @@ __device__ bool wait_count(const unsigned *ctr, unsigned target) {
 }
 
 // Shift decomposition of one line as in the single-run sweeps (reading R2:
-// s = c dt / h and its integer split in FP64, so the integer part is exact),
+// s = c (dt / h) and its integer split in FP64, so the integer part is exact),
 // with the CSL weight polynomials evaluated in FP32 at nu: the FP64 pipe of
 // this GPU is narrow and every tile recomputes its lines' shifts.
-__device__ __forceinline__ LineShift<float> ens_shift(double speed, double dt, double h, const EnsParams &P) {
-    const double sv = __ddiv_rn(__dmul_rn(speed, dt), h);
+__device__ __forceinline__ LineShift<float> ens_shift(double speed, double dth, const EnsParams &P) {
+    const double sv = __dmul_rn(speed, dth);  // dth = dt / h, one division per tile
     double n = round(sv);
     const double z = __dadd_rn(sv, -n);
     const float nu = (float)fabs(z);
@@ -129,6 +131,11 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
     const int wc = (int)((s.inner - c0) < W ? (s.inner - c0) : W);
     float *base = pool + r.f_off + o * L * s.inner + c0;
     float *data = sm + GP * W;  // row 0
+    __shared__ double s_dth;
+    if (threadIdx.x == 0) {
+        const double dt = s.half ? 0.5 * P.dt : P.dt;
+        s_dth = dt / (s.kick ? r.hv[s.axis] : r.hx[s.axis]);
+    }
     for (int c = threadIdx.x; c < GP * W; c += blockDim.x) {
         sm[c] = 0.f;
         data[L * W + c] = 0.f;
@@ -163,16 +170,12 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
     const int cc = threadIdx.x % W, seg = threadIdx.x / W;
     if (cc < wc && seg < nseg) {
         const unsigned cls = s.cls_from_inner ? (unsigned)(((c0 + cc) / s.cdiv) % s.cmod) : (unsigned)(o / s.cdiv);
-        const double dt = s.half ? 0.5 * P.dt : P.dt;
-        double speed, h;
-        if (s.kick) {
+        double speed;
+        if (s.kick)
             speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
-            h = r.hv[s.axis];
-        } else {
+        else
             speed = vp_core::cell_centre(r.vlo[s.axis], r.hv[s.axis], (int)cls);
-            h = r.hx[s.axis];
-        }
-        const LineShift<float> sh = ens_shift(speed, dt, h, P);
+        const LineShift<float> sh = ens_shift(speed, s_dth, P);
         const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         struct St {
@@ -199,6 +202,8 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
     const long long l0 = (long long)tile * R;
     const int nl = (int)((s.outer - l0) < R ? (s.outer - l0) : R);
     float *base = pool + r.f_off + l0 * L;
+    __shared__ double s_dth;
+    if (threadIdx.x == 0) s_dth = (s.half ? 0.5 * P.dt : P.dt) / r.hv[s.axis];
     for (int k = threadIdx.x; k < nl * GP; k += blockDim.x) {
         const int ln = k / GP, g = k - ln * GP;
         in[ln * Pp + g] = 0.f;
@@ -233,9 +238,8 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
     const int line = threadIdx.x % R, seg = threadIdx.x / R;
     if (line < nl && seg < nseg) {
         const unsigned cls = (unsigned)((l0 + line) / s.cdiv);
-        const double dt = s.half ? 0.5 * P.dt : P.dt;
         const double speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
-        const LineShift<float> sh = ens_shift(speed, dt, r.hv[s.axis], P);
+        const LineShift<float> sh = ens_shift(speed, s_dth, P);
         const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         struct St {
@@ -525,7 +529,7 @@ static int build_stages(RunDesc &r, int W, int R, int xpt, int &slot) {
         s.cmod = cmod;
         // tile width: the requested W, halved until the staged tile fits 36 KB
         int w = W;
-        while (w > 8 && (size_t)(L + (per ? 0 : 2 * VP_GHOST)) * w * sizeof(float) > 36 * 1024) w /= 2;
+        while (w > 8 && (size_t)(L + (per ? 0 : 2 * VP_GHOST)) * w * sizeof(float) > kTileBytes) w /= 2;
         if (inner < w) w = (int)inner;
         s.tw = w;
         s.tiles = (int)(outer * ((inner + w - 1) / w));
@@ -543,7 +547,7 @@ static int build_stages(RunDesc &r, int W, int R, int xpt, int &slot) {
         s.cdiv = cdiv;
         s.cmod = 1;
         int rr = R;
-        while (rr > 8 && (size_t)rr * (((L + 2 * VP_GHOST) | 1) + (L | 1)) * sizeof(float) > 36 * 1024) rr /= 2;
+        while (rr > 8 && (size_t)rr * (((L + 2 * VP_GHOST) | 1) + (L | 1)) * sizeof(float) > kTileBytes) rr /= 2;
         s.tw = rr;
         s.tiles = (int)((outer + rr - 1) / rr);
         return s;
