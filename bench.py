@@ -480,7 +480,8 @@ def main():
                 "traffic": (traffic_cell * ncell if traffic_cell is not None else None),
                 "kernel": "k_sweep_cols/k_sweep_rows (one sweep, all kinds averaged)",
                 "algorithmic_bytes_per_launch": 2 * esize * ncell,
-                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "frac_of_spec_8tbs": round(achieved / 8000.0, 4)}
 
     # end to end through the C ABI with host buffers: H2D f, one step, D2H f
     e2e = None
