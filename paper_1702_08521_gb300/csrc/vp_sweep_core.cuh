@@ -9,13 +9,6 @@ namespace vp_core {
 
 // ---- limiter arithmetic (Appendix A and Sec. 2.1.1) -------------------------
 
-// minmod(a, b): the argument of smaller magnitude if both share a sign, else 0
-// (written as a clamp of a into [min(0, b), max(0, b)], which returns a, b or 0)
-template <typename T>
-__device__ __forceinline__ T mm2(T a, T b) {
-    return fmin(fmax(a, fmin(T(0), b)), fmax(T(0), b));
-}
-
 // minmod of four: min if all > 0, max if all < 0, else 0 (= max(min,0) + min(max,0))
 template <typename T>
 __device__ __forceinline__ T mm4(T a, T b, T c, T d) {
@@ -24,13 +17,8 @@ __device__ __forceinline__ T mm4(T a, T b, T c, T d) {
     return fmax(mn, T(0)) + fmin(mx, T(0));
 }
 
-// middle value of three
-template <typename T>
-__device__ __forceinline__ T mid3(T a, T b, T c) {
-    return fmax(fmin(a, b), fmin(fmax(a, b), c));
-}
-
-// min / max of three (one three-input instruction in FP32 on sm_100 and later)
+// min / max of three (the three-input PTX form for FP32; measured here at the
+// throughput of two two-input operations)
 __device__ __forceinline__ float min3(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
