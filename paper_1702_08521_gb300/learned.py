@@ -118,14 +118,12 @@ class Sampler:
             sl, sr = sc[li].double(), sc[ri].double()
             sm = torch.maximum(sl, sr)
             if keep and li.numel() > keep:
-                if importance > 0:
-                    wgt = sm ** importance
-                    p = (wgt / wgt.sum()).cpu().numpy()
-                    nz = int((p > 0).sum())
-                    sel = rng.choice(li.numel(), size=min(keep, nz), replace=False, p=p)
-                else:
-                    sel = rng.choice(li.numel(), size=keep, replace=False)
-                sel = torch.as_tensor(sel, device="cuda")
+                # draw on the GPU, seeded from the caller's generator
+                gen = torch.Generator(device="cuda")
+                gen.manual_seed(int(rng.integers(0, 2 ** 62)))
+                wgt = sm ** importance if importance > 0 else torch.ones_like(sm)
+                nz = int((wgt > 0).sum())
+                sel = torch.multinomial(wgt, min(keep, nz), replacement=False, generator=gen)
                 li, ri, sl, sr, sm = li[sel], ri[sel], sl[sel], sr[sel], sm[sel]
             idx = torch.stack([li, ri], dim=1).reshape(-1)
             Xv = X.view(ns, NFEAT)[idx]
