@@ -263,12 +263,13 @@ int vp_ensemble_sync(vp_ens *ens);
 long long vp_ensemble_launch_count(const vp_ens *ens);
 
 /* ---- learned flux correction (not in the paper) --------------------------
- * A 17 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
+ * A 25 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
  * spatial sweep (drift) on a coarse velocity grid moves through each
  * interface: M = nu Phi_MP + s g(x), where Phi_MP is the CSL7 flux after the
  * MP constraint (App. A), s = max |u_k| + 1e-30 over the upwind-ordered 8-cell
  * stencil u_{-3..4} of the interface and x = ((u_k - u_0) / s for k = -3..4,
- * (u+_k - u-_k) / (2 s) for k = -3..4, nu); u+ / u- are the same cells of the
+ * (u+_k - u-_k) / (2 s) and (u+_k + u-_k - 2 u_k) / (2 s) for k = -3..4, nu);
+ * u+ / u- are the same cells of the
  * lines in the neighbouring velocity cells along the sweep's axis (+: larger
  * |v|; a neighbour outside the velocity box is zero).  The velocity
  * difference is what a coarse velocity cell loses: its sub-cell spread of
@@ -278,12 +279,12 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
  * u_1 + 2M >= 0, blending with the upwind mass nu u_0) and the update keeps
  * the flux form f'_i = f_{i-n} - (M_out - M_in) (Eq. 49), so mass conservation
  * and f >= 0 hold as for the plain scheme.  Weights and matrix inputs are rounded to bfloat16, sums are
- * FP32.  Parameters: VP_NET_NPARAM floats, W1[32][17] b1[32] W2[32][32]
+ * FP32.  Parameters: VP_NET_NPARAM floats, W1[32][25] b1[32] W2[32][32]
  * b2[32] W3[32][32] b3[32] w4[32] b4[1] (FP32 master copy; rounded when used).
  * Training pairs come from fine-grid runs of the method (vp_fine_flux,
  * vp_fluxnet_line_map, vp_group_mean, vp_restrict_velocity, vp_make_samples).
  */
-#define VP_NET_NPARAM 2721
+#define VP_NET_NPARAM 2977
 
 /* one sweep of the grid of ctx (FP32, order 7) with the network correction
  * (use_net = 1, drifts only) or without it (use_net = 0: identical to
@@ -321,7 +322,7 @@ int vp_restrict_velocity(const float *f_fine, float *f_coarse, long long NX, int
                          int factor2, void *cuda_stream);
 
 /* Training pairs on the coarse grid of ctx: for every line and interface
- * (L + 1 per line), X (17 floats, zero velocity features for kick = 1) and
+ * (L + 1 per line), X (25 floats, zero velocity features for kick = 1) and
  * y = (Gc - whole coarse cells swept - nu Phi_MP) / s, the mass the network
  * should add; y = NaN where |zeta| < zmin or the interface is the duplicate
  * periodic end.  scale_dev (may be

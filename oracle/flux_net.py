@@ -9,8 +9,9 @@ the line, u_0 = upwind cell; u+_k / u-_k: the same cells on the lines of the
 neighbouring velocity cells of the sweep's axis, + on the side of larger |v|):
     s    = max_k |u_k| + 1e-30
     x    = [(u_k - u_0) / s for k = -3..4]
-         + [(u+_k - u-_k) / (2 s) for k = -3..4] + [nu]   (17 features)
-    h1   = relu(W1 x  + b1)      W1: 32 x 17
+         + [(u+_k - u-_k) / (2 s) for k = -3..4]
+         + [(u+_k + u-_k - 2 u_k) / (2 s) for k = -3..4] + [nu]   (25 features)
+    h1   = relu(W1 x  + b1)      W1: 32 x 25
     h2   = relu(W2 h1 + b2)      W2: 32 x 32
     h3   = relu(W3 h2 + b3)      W3: 32 x 32
     g    = w4 . h3 + b4          w4: 32
@@ -29,7 +30,7 @@ from __future__ import annotations
 import numpy as np
 
 HIDDEN = 32
-NFEAT = 17
+NFEAT = 25
 SHAPES = {"W1": (HIDDEN, NFEAT), "b1": (HIDDEN,), "W2": (HIDDEN, HIDDEN), "b2": (HIDDEN,),
           "W3": (HIDDEN, HIDDEN), "b3": (HIDDEN,), "w4": (HIDDEN,), "b4": (1,)}
 ORDER = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
@@ -49,11 +50,17 @@ def bf16(x) -> np.ndarray:
 
 def features(u, up, um, nu) -> tuple:
     """u, up, um: (B, 8) upwind-ordered stencils u_{-3..4} of the line and of
-    its velocity neighbours (+: larger |v|); nu: (B,). Returns (X, s)."""
+    its velocity neighbours (+: larger |v|); nu: (B,). Returns (X, s): the
+    stencil relative to u_0, the velocity difference and the velocity
+    curvature at the 8 cells, all over s = max |u|, and nu."""
     u = np.asarray(u, dtype=np.float64)
+    up = np.asarray(up, dtype=np.float64)
+    um = np.asarray(um, dtype=np.float64)
     s = np.abs(u).max(axis=1) + 1e-30
-    dv = (np.asarray(up, dtype=np.float64) - np.asarray(um, dtype=np.float64)) / (2.0 * s[:, None])
-    X = np.concatenate([(u - u[:, 3:4]) / s[:, None], dv, np.asarray(nu, dtype=np.float64)[:, None]], axis=1)
+    dv = (up - um) / (2.0 * s[:, None])
+    cv = (up + um - 2.0 * u) / (2.0 * s[:, None])
+    X = np.concatenate([(u - u[:, 3:4]) / s[:, None], dv, cv, np.asarray(nu, dtype=np.float64)[:, None]],
+                       axis=1)
     return X, s
 
 

@@ -1,13 +1,13 @@
 // vp_fluxnet.cu -- learned flux correction on a coarser velocity grid
 // (a spec addition to the method, not in the paper).
 //
-// A 17 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
+// A 25 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
 // coarse-grid spatial sweep moves through an interface:
 //   M = nu Phi_MP + s g(x),
 // Phi_MP the CSL7 flux after the MP constraint, s = max |u| over the 8-cell
 // upwind-ordered stencil u_{-3..4}, x = ((u_k - u_0) / s, (u+_k - u-_k) / (2 s),
-// nu) with u+ / u- the same cells of the lines in the neighbouring velocity
-// cells (+: larger |v|).  The correction is a mass, not a flux value: the
+// (u+_k + u-_k - 2 u_k) / (2 s), nu) with u+ / u- the same cells of the lines in
+// the neighbouring velocity cells (+: larger |v|).  The correction is a mass, not a flux value: the
 // sub-cell spread of speeds inside a coarse velocity cell moves mass even
 // where the cell's own fractional shift nu vanishes.  The PP limiter then acts
 // on the total mass (f_i - 2 M >= 0, f_{i+1} + 2 M >= 0) and the update keeps
@@ -88,7 +88,8 @@ __device__ __forceinline__ float net_forward(const float *__restrict__ w, const 
 }
 
 // features of the upwind-ordered stencil u[0..7] = u_{-3..4} and of the same
-// cells up / um of the velocity-neighbour lines (+: larger |v|)
+// cells up / um of the velocity-neighbour lines (+: larger |v|): velocity
+// difference and curvature
 __device__ __forceinline__ float net_features(const float *u, const float *up, const float *um, float nu,
                                               float *x) {
     float s = 0.f;
@@ -100,7 +101,9 @@ __device__ __forceinline__ float net_features(const float *u, const float *up, c
     for (int k = 0; k < 8; ++k) x[k] = (u[k] - u[3]) * inv;
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[8 + k] = (up[k] - um[k]) * (0.5f * inv);
-    x[16] = nu;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[16 + k] = (0.5f * (up[k] + um[k]) - u[k]) * inv;
+    x[24] = nu;
     return s;
 }
 
@@ -474,20 +477,17 @@ __global__ void k_group_mean(const double *__restrict__ Gf, long long ncl, int n
 
 // ---- inference: the learned coarse sweep, network on the tensor cores -------------------
 //
-// A CTA takes NL consecutive lines of the sweep.  Phase 0 stages the lines,
-// their velocity-difference lines (u+ - u-) / 2 from the snapshot and the
-// lines' shift decompositions in shared memory (consecutive threads read
-// consecutive lines: coalesced for strided sweeps).  Phase 1: warps take
-// 16-interface tiles; the four lanes of an MMA row group build that row's
-// features straight into the A fragments (lane t holds stencil positions
-// 2t, 2t + 1; the stencil maximum by a group shuffle), the network runs
-// with mma.sync (bf16 inputs, FP32 accumulation; each layer's accumulators
-// are re-packed as the next layer's A fragments in registers), and lanes 0 /
-// 1 of the group add the plain MP mass, apply the PP limiter and store the
-// interface mass.  Phase 2: one thread per cell writes the flux-form update.
-// Interface k of a line is the k-th one the upwind walk meets: its upwind
-// cell is q_k = q_0 + k sigma, q_0 = (sigma > 0 ? 0 : L - 1) - n - sigma;
-// the k-th cell of the walk (k >= 1) takes M_{k-1} in and M_k out.
+// A CTA takes NL consecutive lines of the sweep.  Phase 0 stages the lines
+// and, from the snapshot, their velocity-difference lines (u+ - u-) / 2 and
+// velocity-curvature lines (u+ + u-) / 2 - u in shared memory (consecutive
+// threads read consecutive lines: coalesced for strided sweeps), with the
+// lines' shift decompositions.  Phase 1 computes every interface's limited
+// mass: the plain MP mass, plus s g from the network on the tensor cores
+// (described at the loop), then the PP limiter.  Phase 2: one thread per
+// cell writes the flux-form update.  Interface k of a line is the k-th one
+// the upwind walk meets: its upwind cell is q_k = q_0 + k sigma,
+// q_0 = (sigma > 0 ? 0 : L - 1) - n - sigma; the k-th cell of the walk
+// (k >= 1) takes M_{k-1} in and M_k out.
 
 constexpr int kTcThreads = 128;
 
@@ -504,14 +504,37 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// D = A B + C with C = (c.x, c.y) in both row halves of the lane's fragment
+__device__ __forceinline__ void mma_bf16_c(float (&d)[4], const uint32_t (&a)[4], uint2 b, float2 c) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%10,%11};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y), "f"(c.x), "f"(c.y));
+}
+
+// bf16(max(lo, 0)) in the low half, bf16(max(hi, 0)) in the high half
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// four 8x8 bf16 matrices from shared memory, one row address per lane
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
 // ReLU, round to bf16 and re-pack accumulators as the next layer's A fragments
 __device__ __forceinline__ void relu_pack(const float (&acc)[4][4], uint32_t (&a)[2][4]) {
 #pragma unroll
     for (int kb = 0; kb < 2; ++kb) {
-        a[kb][0] = pack_bf16(fmaxf(acc[2 * kb][0], 0.f), fmaxf(acc[2 * kb][1], 0.f));
-        a[kb][1] = pack_bf16(fmaxf(acc[2 * kb][2], 0.f), fmaxf(acc[2 * kb][3], 0.f));
-        a[kb][2] = pack_bf16(fmaxf(acc[2 * kb + 1][0], 0.f), fmaxf(acc[2 * kb + 1][1], 0.f));
-        a[kb][3] = pack_bf16(fmaxf(acc[2 * kb + 1][2], 0.f), fmaxf(acc[2 * kb + 1][3], 0.f));
+        a[kb][0] = pack_relu_bf16(acc[2 * kb][0], acc[2 * kb][1]);
+        a[kb][1] = pack_relu_bf16(acc[2 * kb][2], acc[2 * kb][3]);
+        a[kb][2] = pack_relu_bf16(acc[2 * kb + 1][0], acc[2 * kb + 1][1]);
+        a[kb][3] = pack_relu_bf16(acc[2 * kb + 1][2], acc[2 * kb + 1][3]);
     }
 }
 
@@ -523,51 +546,85 @@ struct LLine {
     int q0;          // upwind cell of the walk's first interface (unwrapped)
 };
 
-constexpr int kLG = 8;  // staged rows on each side of a learned-sweep line
+constexpr int kLG = 8;   // staged rows on each side of a learned-sweep line
+constexpr int kFS = 80;  // bytes per feature row (32 bf16 + 16 pad: conflict-free ldmatrix)
+
+// network weights in the order the learned sweep keeps them in shared memory:
+// B fragments of the three hidden layers [layer][k block][n tile][lane][2],
+// the w4 fragments [k block][lane] (w4 in column 0 of B), then b1 b2 b3,
+// bf16(w4) and b4 (129 floats, padded to 132)
+constexpr int kFragWords = 3 * 2 * 4 * 32 * 2 + 2 * 32 * 2 + 132;
+static_assert(kFragWords % 4 == 0, "fragment block is copied in 16-byte units");
+
+__global__ void k_net_frags(const float *__restrict__ wts, uint32_t *__restrict__ out) {
+    uint2 *w4f = reinterpret_cast<uint2 *>(out + 3 * 2 * 4 * 32 * 2);
+    float *wvec = reinterpret_cast<float *>(w4f + 2 * 32);
+    for (int e = threadIdx.x; e < 3 * 2 * 4 * 32; e += blockDim.x) {
+        const int lane = e & 31, frag = e >> 5;  // frag = (layer * 2 + kb) * 4 + nt
+        const int nt = frag & 3, kb = (frag >> 2) & 1, layer = frag >> 3;
+        const int off = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
+        const int kin = layer == 0 ? NF : H;
+        const int n = 8 * nt + (lane >> 2), k0 = 16 * kb + 2 * (lane & 3), k1 = k0 + 8;
+        auto wv = [&](int k) { return k < kin ? wts[off + n * kin + k] : 0.f; };
+        out[2 * e] = pack_bf16(wv(k0), wv(k0 + 1));
+        out[2 * e + 1] = pack_bf16(wv(k1), wv(k1 + 1));
+    }
+    for (int e = threadIdx.x; e < 2 * 32; e += blockDim.x) {
+        const int lane = e & 31, kb = e >> 5, k0 = 16 * kb + 2 * (lane & 3);
+        const float *w4 = wts + OFF_W4;
+        w4f[e] = (lane >> 2) == 0 ? make_uint2(pack_bf16(w4[k0], w4[k0 + 1]), pack_bf16(w4[k0 + 8], w4[k0 + 9]))
+                                  : make_uint2(0u, 0u);
+    }
+    for (int e = threadIdx.x; e < 132; e += blockDim.x) {
+        const int grp = e / H, n = e - grp * H;
+        wvec[e] = grp == 0   ? wts[OFF_B1 + n]
+                  : grp == 1 ? wts[OFF_B2 + n]
+                  : grp == 2 ? wts[OFF_B3 + n]
+                  : grp == 3 ? bfr(wts[OFF_W4 + n])
+                  : e == 4 * H ? wts[OFF_B4]
+                               : 0.f;
+    }
+}
+
+// divisors of the line index (host-precomputed; used when every line index fits 32 bits)
+struct LineDiv {
+    FastDiv inner, cdiv, cmod;
+    int fast;
+};
 
 template <bool PERIODIC>
 __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict__ f, long long outer, int L,
-                                                              long long inner, int kick, int from_inner,
-                                                              long long cdiv, long long cmod,
-                                                              const double *__restrict__ accel, double lo,
-                                                              double dvel, double dt, double h, WPoly wp,
-                                                              const float *__restrict__ wts, float alpha,
+                                                              long long inner, int from_inner, long long cdiv,
+                                                              long long cmod,
+                                                              const LineShift<float> *__restrict__ tab,
+                                                              const uint4 *__restrict__ netfrag, double lo,
+                                                              double dvel, float alpha,
                                                               int use_net, const float *__restrict__ fsnap,
-                                                              int lgNL) {
+                                                              int lgNL, LineDiv ldv) {
     extern __shared__ __align__(16) unsigned char tsm[];
     const int NL = 1 << lgNL;
     const int NI = NL * (L + 1);  // interface e = k * NL + l (line l, k-th interface of its walk)
     const int LP = L + 2 * kLG;   // staged rows: -kLG .. L + kLG - 1
     uint32_t *wfrag = reinterpret_cast<uint32_t *>(tsm);  // [3][2][4][32 lanes][2] B fragments
-    float *wvec = reinterpret_cast<float *>(wfrag + 3 * 2 * 4 * 32 * 2);  // b1 b2 b3 w4(bf16) b4: 129
+    uint2 *w4f = reinterpret_cast<uint2 *>(wfrag + 3 * 2 * 4 * 32 * 2);  // [2][32 lanes] w4 in column 0
+    float *wvec = reinterpret_cast<float *>(w4f + 2 * 32);  // b1 b2 b3 w4(bf16) b4: 129
     LineShift<float> *shs = reinterpret_cast<LineShift<float> *>(wvec + 132);
     LLine *lls = reinterpret_cast<LLine *>(shs + NL);
     float *lines = reinterpret_cast<float *>(lls + NL);  // [LP][NL], row r at (r + kLG)
     float *dvl = lines + NL * LP;                         // [LP][NL] velocity differences
-    float *mass = dvl + NL * LP;                          // [L + 1][NL] interface masses
+    float *cvl = dvl + NL * LP;                           // [LP][NL] velocity curvatures
+    float *mass = cvl + NL * LP;                          // [L + 1][NL] interface masses
+    // per warp: 32 feature rows of kFS bytes
+    unsigned char *fbuf = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(mass + (size_t)NL * (L + 1)) + 15) & ~static_cast<uintptr_t>(15));
     const long long nlines = outer * inner;
     const long long l0 = (long long)blockIdx.x * NL;
     const int nl = (int)(nlines - l0 < NL ? nlines - l0 : NL);
-    // phase 0: network fragments, per-line data, then lines and velocity differences
+    // phase 0: network fragments, per-line data, then the lines and their
+    // velocity-difference and velocity-curvature lines
     if (use_net) {
-        for (int e = threadIdx.x; e < 3 * 2 * 4 * 32; e += blockDim.x) {
-            const int lane = e & 31, frag = e >> 5;  // frag = (layer * 2 + kb) * 4 + nt
-            const int nt = frag & 3, kb = (frag >> 2) & 1, layer = frag >> 3;
-            const int off = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
-            const int kin = layer == 0 ? NF : H;
-            const int n = 8 * nt + (lane >> 2), k0 = 16 * kb + 2 * (lane & 3), k1 = k0 + 8;
-            auto wv = [&](int k) { return k < kin ? wts[off + n * kin + k] : 0.f; };
-            wfrag[2 * e] = pack_bf16(wv(k0), wv(k0 + 1));
-            wfrag[2 * e + 1] = pack_bf16(wv(k1), wv(k1 + 1));
-        }
-        for (int e = threadIdx.x; e < 4 * H + 1; e += blockDim.x) {
-            const int grp = e / H, n = e - grp * H;
-            wvec[e] = grp == 0 ? wts[OFF_B1 + n]
-                      : grp == 1 ? wts[OFF_B2 + n]
-                      : grp == 2 ? wts[OFF_B3 + n]
-                      : grp == 3 ? bfr(wts[OFF_W4 + n])
-                                 : wts[OFF_B4];
-        }
+        uint4 *dst = reinterpret_cast<uint4 *>(tsm);
+        for (int e = threadIdx.x; e < kFragWords / 4; e += blockDim.x) dst[e] = netfrag[e];
     }
     for (int l = threadIdx.x; l < NL; l += blockDim.x) {
         LLine ll{0, 1, 0, 0, 0};
@@ -575,13 +632,21 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
         sh.sigma = 1;
         if (l < nl) {
             const long long line = l0 + l;
-            const long long o = line / inner, c = line % inner;
-            const long long cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
-            const double speed = kick ? accel[cls] : vp_core::cell_centre(lo, dvel, (int)cls);
-            sh = vp_core::make_shift<float>(speed, dt, h, wp);
+            long long o, c, cls;
+            if (ldv.fast) {
+                const unsigned ou = fdiv((unsigned)line, ldv.inner);
+                o = ou;
+                c = (unsigned)line - ou * ldv.inner.d;
+                cls = from_inner ? fmod_u(fdiv((unsigned)c, ldv.cdiv), ldv.cmod) : fdiv(ou, ldv.cdiv);
+            } else {
+                o = line / inner;
+                c = line % inner;
+                cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
+            }
+            sh = tab[cls];
             ll.base = o * L * inner + c;
-            if (use_net && !kick) {
-                ll.sp = speed >= 0.0 ? 1 : -1;
+            if (use_net) {  // drift lines: +sp is the neighbour with larger |v|
+                ll.sp = vp_core::cell_centre(lo, dvel, (int)cls) >= 0.0 ? 1 : -1;
                 ll.has_p = cls + ll.sp >= 0 && cls + ll.sp < cmod;
                 ll.has_m = cls - ll.sp >= 0 && cls - ll.sp < cmod;
             }
@@ -600,28 +665,42 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
     __syncthreads();
     const int lt = threadIdx.x & (NL - 1), rt = threadIdx.x >> lgNL, rstep = blockDim.x >> lgNL;
     if (lt < nl) {
+        // four rows per thread in flight: all loads first, then the stores
         const LLine ll = lls[lt];
-        for (int r = rt; r < LP; r += rstep) {
-            int rr = r - kLG;  // line row
-            bool in = true;
-            if (PERIODIC) {
-                while (rr < 0) rr += L;
-                while (rr >= L) rr -= L;
-            } else {
-                in = rr >= 0 && rr < L;
-            }
-            float v = 0.f, d = 0.f;
-            if (in) {
+        const long long pofs = ll.sp * cdiv;
+        constexpr int B = 4;
+        for (int r0 = rt; r0 < LP; r0 += B * rstep) {
+            float v[B], up[B], um[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int r = r0 + j * rstep;
+                int rr = r - kLG;  // line row
+                if (PERIODIC) {
+                    if (L >= kLG) {  // staged rows reach at most kLG beyond either end
+                        rr += rr < 0 ? L : 0;
+                        rr -= rr >= L ? L : 0;
+                    } else {
+                        while (rr < 0) rr += L;
+                        while (rr >= L) rr -= L;
+                    }
+                }
+                const bool in = r < LP && (PERIODIC || (rr >= 0 && rr < L));
                 const long long a = ll.base + (long long)rr * inner;
-                v = f[a];
-                if (use_net && !kick) {
-                    const float up = ll.has_p ? fsnap[a + ll.sp * cdiv] : 0.f;
-                    const float um = ll.has_m ? fsnap[a - ll.sp * cdiv] : 0.f;
-                    d = 0.5f * (up - um);
+                v[j] = in ? f[a] : 0.f;
+                up[j] = in && use_net && ll.has_p ? fsnap[a + pofs] : 0.f;
+                um[j] = in && use_net && ll.has_m ? fsnap[a - pofs] : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int r = r0 + j * rstep;
+                if (r < LP) {
+                    lines[r * NL + lt] = v[j];
+                    if (use_net) {
+                        dvl[r * NL + lt] = 0.5f * (up[j] - um[j]);
+                        cvl[r * NL + lt] = 0.5f * (up[j] + um[j]) - v[j];
+                    }
                 }
             }
-            lines[r * NL + lt] = v;
-            dvl[r * NL + lt] = d;
         }
     }
     __syncthreads();
@@ -629,106 +708,151 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
     // or zero (outflow) beyond them (only for shifts of more than kLG - 5 cells)
     auto row = [&](const float *ln, int l, int q) -> float {
         if (q < -kLG || q >= L + kLG) {
-            if (!PERIODIC) return 0.f;
-            while (q < 0) q += L;
-            while (q >= L) q -= L;
+            if constexpr (PERIODIC) {
+                while (q < 0) q += L;
+                while (q >= L) q -= L;
+            } else {
+                return 0.f;
+            }
         }
         return ln[(q + kLG) * NL + l];
     };
-    // phase 1a: plain mass of every interface (CSL7, MP); without the
-    // network also the PP limiter
-    for (int e = threadIdx.x; e < NI; e += blockDim.x) {
-        const int l = e & (NL - 1), k = e >> lgNL;
-        if (l >= nl) continue;
-        const LineShift<float> &sh = shs[l];
-        const int sg = sh.sigma;
-        const int q = lls[l].q0 + k * sg;
-        float u[7];
+    if (!use_net) {
+        // phase 1 without the network: limited mass of every interface (CSL7, MP, PP)
+        for (int e = threadIdx.x; e < NI; e += blockDim.x) {
+            const int l = e & (NL - 1), k = e >> lgNL;
+            if (l >= nl) continue;
+            const LineShift<float> &sh = shs[l];
+            const int sg = sh.sigma;
+            const int q = lls[l].q0 + k * sg;
+            const int qa = q - 3 * sg, qb = q + 3 * sg;
+            float u[7];
+            if (min(qa, qb) >= -kLG && max(qa, qb) < L + kLG) {
+                const int st = sg * NL;
+                const float *pu = lines + (qa + kLG) * NL + l;
 #pragma unroll
-        for (int m = 0; m < 7; ++m) u[m] = row(lines, l, q + sg * (m - 3));
-        float phi = sh.w[0] * u[0];
+                for (int m = 0; m < 7; ++m) u[m] = pu[m * st];
+            } else {
 #pragma unroll
-        for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
-        phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
-        const float M = sh.nu * phi;
-        mass[e] = use_net ? M : pp_mass(M, u[3], u[4], sh.nu);
-    }
-    __syncthreads();
-    // phase 1b: the network on the tensor cores adds s g, then the PP limiter
-    if (use_net) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, t = lane & 3;
-        const uint2 *wf2 = reinterpret_cast<const uint2 *>(wfrag);
-        const int ntiles = (NI + 15) / 16;
-        for (int tile = warp; tile < ntiles; tile += blockDim.x / 32) {
-            uint32_t a[2][4];
-            float sr[2];
-#pragma unroll
-            for (int hr = 0; hr < 2; ++hr) {  // rows gq and gq + 8 of the tile
-                const int e = tile * 16 + gq + 8 * hr;
-                const int l = e & (NL - 1), k = e >> lgNL;
-                float x0 = 0.f, x1 = 0.f, d0 = 0.f, d1 = 0.f, nu = 0.f;
-                if (e < NI && l < nl) {
-                    const int sg = shs[l].sigma;
-                    const int q = lls[l].q0 + k * sg;
-                    x0 = row(lines, l, q + sg * (2 * t - 3));
-                    x1 = row(lines, l, q + sg * (2 * t - 2));
-                    d0 = row(dvl, l, q + sg * (2 * t - 3));
-                    d1 = row(dvl, l, q + sg * (2 * t - 2));
-                    nu = shs[l].nu;
-                }
-                float s = fmaxf(fabsf(x0), fabsf(x1));
-                s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, 1));
-                s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, 2));
-                s += 1e-30f;
-                // u_0 of the stencil is position 3: lane t = 1, second value
-                const float u0 = __shfl_sync(0xffffffffu, x1, (lane & ~3) | 1);
-                const float inv = 1.0f / s;
-                a[0][hr] = pack_bf16((x0 - u0) * inv, (x1 - u0) * inv);
-                a[0][2 + hr] = pack_bf16(d0 * inv, d1 * inv);
-                a[1][hr] = pack_bf16(t == 0 ? nu : 0.f, 0.f);
-                a[1][2 + hr] = 0u;
-                sr[hr] = s;
+                for (int m = 0; m < 7; ++m) u[m] = row(lines, l, qa + m * sg);
             }
-            float acc[4][4];
+            float phi = sh.w[0] * u[0];
+#pragma unroll
+            for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
+            phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
+            mass[e] = pp_mass(sh.nu * phi, u[3], u[4], sh.nu);
+        }
+    } else {
+        // phase 1 with the network: a warp takes 32 interfaces (two 16-row MMA
+        // tiles).  Lane i computes interface i's plain MP mass and its feature
+        // row (bf16, columns 0-7 stencil, 8-15 velocity difference, 16-23
+        // velocity curvature, 24 nu, 25-31 zero) into the warp's buffer;
+        // ldmatrix turns the rows into A fragments; the layers run with
+        // mma.sync (biases as the C operand, FP32 accumulation, ReLU and bf16
+        // rounding in one conversion); the output layer is an MMA with w4 in
+        // column 0 of B; lane i then adds s g and applies the PP limiter.
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = lane & 3;
+        unsigned char *fb = fbuf + warp * 32 * kFS;
+        const uint32_t fb_s = static_cast<uint32_t>(__cvta_generic_to_shared(fb));
+        // this lane's ldmatrix row: matrix lane >> 3 holds rows +8 (odd) and columns +8 (>= 2)
+        const uint32_t ldm = fb_s + (uint32_t)(((lane & 7) + 8 * ((lane >> 3) & 1)) * kFS + 16 * (lane >> 4));
+        const uint2 *wf2 = reinterpret_cast<const uint2 *>(wfrag);
+        const float2 b4c = make_float2(t == 0 ? wvec[4 * H] : 0.f, 0.f);
+        const int nit = (NI + 31) >> 5;
+        for (int it = warp; it < nit; it += blockDim.x >> 5) {
+            const int e = (it << 5) + lane;
+            const int l = e & (NL - 1), k = e >> lgNL;
+            const bool ok = e < NI && l < nl;
+            float Mp = 0.f, s = 1.f, u3 = 0.f, u4 = 0.f, nu = 0.f;
+            uint4 p0 = make_uint4(0u, 0u, 0u, 0u), p1 = p0, p2 = p0, p3 = p0;
+            if (ok) {
+                const LineShift<float> &sh = shs[l];
+                const int sg = sh.sigma;
+                const int q = lls[l].q0 + k * sg;
+                nu = sh.nu;
+                float u[8], dv[8], cv[8];
+                const int qa = q - 3 * sg, qb = q + 4 * sg;
+                if (min(qa, qb) >= -kLG && max(qa, qb) < L + kLG) {
+                    const int st = sg * NL;
+                    const float *pu = lines + (qa + kLG) * NL + l;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        u[m] = pu[m * st];
+                        dv[m] = pu[NL * LP + m * st];
+                        cv[m] = pu[2 * NL * LP + m * st];
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        u[m] = row(lines, l, qa + m * sg);
+                        dv[m] = row(dvl, l, qa + m * sg);
+                        cv[m] = row(cvl, l, qa + m * sg);
+                    }
+                }
+                float phi = sh.w[0] * u[0];
+#pragma unroll
+                for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
+                Mp = nu * vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
+                u3 = u[3];
+                u4 = u[4];
+                s = 0.f;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) s = fmaxf(s, fabsf(u[m]));
+                s += 1e-30f;
+                const float inv = 1.0f / s;
+                p0 = make_uint4(pack_bf16((u[0] - u3) * inv, (u[1] - u3) * inv),
+                                pack_bf16((u[2] - u3) * inv, 0.f), pack_bf16((u[4] - u3) * inv, (u[5] - u3) * inv),
+                                pack_bf16((u[6] - u3) * inv, (u[7] - u3) * inv));
+                p1 = make_uint4(pack_bf16(dv[0] * inv, dv[1] * inv), pack_bf16(dv[2] * inv, dv[3] * inv),
+                                pack_bf16(dv[4] * inv, dv[5] * inv), pack_bf16(dv[6] * inv, dv[7] * inv));
+                p2 = make_uint4(pack_bf16(cv[0] * inv, cv[1] * inv), pack_bf16(cv[2] * inv, cv[3] * inv),
+                                pack_bf16(cv[4] * inv, cv[5] * inv), pack_bf16(cv[6] * inv, cv[7] * inv));
+                p3.x = pack_bf16(nu, 0.f);
+            }
+            uint4 *fr = reinterpret_cast<uint4 *>(fb + lane * kFS);
+            fr[0] = p0;
+            fr[1] = p1;
+            fr[2] = p2;
+            fr[3] = p3;
+            __syncwarp();
+            uint32_t a[2][2][4];  // [tile][k block][fragment]
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int kb = 0; kb < 2; ++kb) ldsm_x4(a[j][kb], ldm + (uint32_t)(j * 16 * kFS + kb * 32));
+            __syncwarp();
+            float acc[2][4][4];
 #pragma unroll
             for (int layer = 0; layer < 3; ++layer) {
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt) {
-                    const float b0 = wvec[layer * H + 8 * nt + 2 * t], b1v = wvec[layer * H + 8 * nt + 2 * t + 1];
-                    acc[nt][0] = acc[nt][2] = b0;
-                    acc[nt][1] = acc[nt][3] = b1v;
+                    const float2 b = *reinterpret_cast<const float2 *>(wvec + layer * H + 8 * nt + 2 * t);
+                    const uint2 bb0 = wf2[((layer * 2 + 0) * 4 + nt) * 32 + lane];
+                    const uint2 bb1 = wf2[((layer * 2 + 1) * 4 + nt) * 32 + lane];
 #pragma unroll
-                    for (int kb = 0; kb < 2; ++kb) {
-                        const uint2 bb = wf2[((layer * 2 + kb) * 4 + nt) * 32 + lane];
-                        mma_bf16(acc[nt], a[kb], bb.x, bb.y);
+                    for (int j = 0; j < 2; ++j) {
+                        mma_bf16_c(acc[j][nt], a[j][0], bb0, b);
+                        mma_bf16(acc[j][nt], a[j][1], bb1.x, bb1.y);
                     }
                 }
-                if (layer < 2) relu_pack(acc, a);
-            }
-            // output g = b4 + w4 . bf16(relu(h3)) for rows gq and gq + 8
-            float p0 = 0.f, p1 = 0.f;
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const float w4v = wvec[3 * H + 8 * nt + 2 * t + j];
-                    p0 = fmaf(w4v, bfr(fmaxf(acc[nt][j], 0.f)), p0);
-                    p1 = fmaf(w4v, bfr(fmaxf(acc[nt][2 + j], 0.f)), p1);
-                }
-            p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
-            p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
-            p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-            p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
-            if (t < 2) {
-                const int e = tile * 16 + gq + 8 * t;
-                const int l = e & (NL - 1), k = e >> lgNL;
-                if (e < NI && l < nl) {
-                    const int sg = shs[l].sigma;
-                    const int q = lls[l].q0 + k * sg;
-                    mass[e] = pp_mass(fmaf(sr[t], wvec[4 * H] + (t == 0 ? p0 : p1), mass[e]), row(lines, l, q),
-                                      row(lines, l, q + sg), shs[l].nu);
-                }
+                for (int j = 0; j < 2; ++j) relu_pack(acc[j], a[j]);
             }
+            float g[2][4];
+            const uint2 w40 = w4f[lane], w41 = w4f[32 + lane];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                mma_bf16_c(g[j], a[j][0], w40, b4c);
+                mma_bf16(g[j], a[j][1], w41.x, w41.y);
+            }
+            // row r of tile j sits in lane 4 (r mod 8), element 0 (r < 8) or 2
+            const int src = (lane & 7) << 2;
+            const float g00 = __shfl_sync(0xffffffffu, g[0][0], src);
+            const float g02 = __shfl_sync(0xffffffffu, g[0][2], src);
+            const float g10 = __shfl_sync(0xffffffffu, g[1][0], src);
+            const float g12 = __shfl_sync(0xffffffffu, g[1][2], src);
+            const float gi = (lane & 16) ? ((lane & 8) ? g12 : g10) : ((lane & 8) ? g02 : g00);
+            if (ok) mass[e] = pp_mass(fmaf(s, gi, Mp), u3, u4, nu);
         }
     }
     __syncthreads();
@@ -835,15 +959,27 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
         f_snap = static_cast<const float *>(c->d_snap);
     }
     const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
-    // lines per CTA: a power of two, at most 16, within ~24 KB of shared memory
-    // (several CTAs per SM hide the latency of the layer chain)
+    int rc = vp_launch_shift_table(c, kick, dim, dt, accel_dev);
+    if (rc != VP_OK) return rc;
+    if (use_net) {
+        if (!c->d_netfrag) VP_CUDA_TRY(c, cudaMalloc(&c->d_netfrag, kFragWords * sizeof(uint32_t)));
+        k_net_frags<<<1, 256, 0, c->stream>>>(wts, static_cast<uint32_t *>(c->d_netfrag));
+        c->launches++;
+    }
+    // lines per CTA: a power of two, at most 16; the largest that leaves room
+    // for 7 CTAs per SM (28 warps, as many as the registers allow), else the
+    // largest within 48 KB of shared memory
     auto smem_for = [&](int nl) {
-        return (size_t)3 * 2 * 4 * 32 * 2 * sizeof(uint32_t) + 132 * sizeof(float) +
-               nl * (sizeof(LineShift<float>) + sizeof(LLine)) + 2 * (size_t)nl * (q.L + 2 * kLG) * sizeof(float) +
-               (size_t)nl * (q.L + 1) * sizeof(float);
+        return (size_t)kFragWords * sizeof(uint32_t) + nl * (sizeof(LineShift<float>) + sizeof(LLine)) +
+               3 * (size_t)nl * (q.L + 2 * kLG) * sizeof(float) + (size_t)nl * (q.L + 1) * sizeof(float) + 16 +
+               (size_t)(kTcThreads / 32) * 32 * kFS;
     };
     int lgNL = 4;
-    while (lgNL > 0 && smem_for(1 << lgNL) > 24 * 1024) --lgNL;
+    while (lgNL > 0 && smem_for(1 << lgNL) > 31 * 1024) --lgNL;
+    if (smem_for(1 << lgNL) > 31 * 1024) {
+        lgNL = 4;
+        while (lgNL > 0 && smem_for(1 << lgNL) > 48 * 1024) --lgNL;
+    }
     const int NL = 1 << lgNL;
     const size_t smem = smem_for(NL);
     if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line too long for the learned sweep");
@@ -851,14 +987,23 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     const unsigned blocks = (unsigned)((nl + NL - 1) / NL);
     cudaFuncSetAttribute(k_learned_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_learned_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const LineShift<float> *tab = static_cast<const LineShift<float> *>(c->d_shift);
+    const uint4 *frag = static_cast<const uint4 *>(c->d_netfrag);
+    LineDiv ldv{};
+    ldv.fast = nl <= 0xFFFFFFFFll && q.inner <= 0xFFFFFFFFll && q.cdiv <= 0xFFFFFFFFll && q.cmod <= 0xFFFFFFFFll;
+    if (ldv.fast) {
+        ldv.inner = make_fastdiv((unsigned)q.inner);
+        ldv.cdiv = make_fastdiv((unsigned)q.cdiv);
+        ldv.cmod = make_fastdiv((unsigned)q.cmod);
+    }
     if (q.periodic)
         k_learned_sweep<true><<<blocks, kTcThreads, smem, c->stream>>>(
-            static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
-            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap, lgNL);
+            static_cast<float *>(c->f), q.outer, q.L, q.inner, q.from_inner, q.cdiv, q.cmod, tab, frag, q.lo,
+            q.dvel, (float)c->g.alpha, use_net, f_snap, lgNL, ldv);
     else
         k_learned_sweep<false><<<blocks, kTcThreads, smem, c->stream>>>(
-            static_cast<float *>(c->f), q.outer, q.L, q.inner, kick, q.from_inner, q.cdiv, q.cmod, accel_dev,
-            q.lo, q.dvel, dt, q.h, c->wp, wts, (float)c->g.alpha, use_net, f_snap, lgNL);
+            static_cast<float *>(c->f), q.outer, q.L, q.inner, q.from_inner, q.cdiv, q.cmod, tab, frag, q.lo,
+            q.dvel, (float)c->g.alpha, use_net, f_snap, lgNL, ldv);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;

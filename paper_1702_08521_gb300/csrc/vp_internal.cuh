@@ -121,6 +121,7 @@ struct vp_ctx {
     long long launches;
     int *d_status;                      // device-side error word (bounded waits)
     void *d_snap;                       // copy of f before a learned sweep (allocated on first use)
+    void *d_netfrag;                    // network weights in MMA fragment order (allocated on first use)
     int opt_impl;                       // 0 auto, 1 staged, 2 TMA
     int opt_autotune;                   // 1: time candidate tiles on first use
     SweepTune tune[2][3];               // [kick][dim]
@@ -149,7 +150,7 @@ int vp_field_setup(vp_ctx *c);          // Green function tables (at create)
 // CSL weight polynomials of the given order (5 or 7), from the definition of the SL flux
 WPoly vp_csl_weight_polys(int order);
 // learned flux correction network: 9 features, 3 hidden layers of 32
-#define VP_NET_FEATURES 17
+#define VP_NET_FEATURES 25
 #define VP_NET_HIDDEN 32
 // analytic initial condition into any f array of grid g (precision from g)
 int vp_launch_init_ptr(void *f, const vp_grid &g, int kind, const double *p, int np, cudaStream_t st);

@@ -4,8 +4,8 @@ fine-grid runs of the method, training, and coarse runs with the network.
 The correction acts on the spatial sweeps (drifts): on a coarser velocity
 grid their error comes from the spread of speeds inside one velocity cell,
 which moves the sub-cell velocity gradient of f across x.  The network sees
-the spatial stencil of the line and the velocity difference of its
-neighbouring velocity cells at the same positions.  Velocity sweeps (kicks)
+the spatial stencil of the line and the velocity difference and curvature
+from its neighbouring velocity cells at the same positions.  Velocity sweeps (kicks)
 run the plain scheme: on these grids their coarse-grid error is orders of
 magnitude below the drifts'.
 
@@ -22,7 +22,7 @@ import numpy as np
 
 from . import vlasov as V
 
-NFEAT = 17  # network inputs: 8 stencil values, 8 velocity differences, nu
+NFEAT = 25  # network inputs: 8 stencil values, 8 velocity differences, 8 velocity curvatures, nu
 
 
 def landau_grid(dims: int, nx: int, nv: int, k: float = 0.5, vmax: float = 6.0) -> dict:
@@ -164,7 +164,7 @@ class Sampler:
 
 def he_init(seed: int = 0):
     """Initial parameters (W ~ N(0, 2 / fan_in), last layer x 0.1, zero biases),
-    laid out as W1[32][17] b1 W2[32][32] b2 W3[32][32] b3 w4[32] b4."""
+    laid out as W1[32][25] b1 W2[32][32] b2 W3[32][32] b3 w4[32] b4."""
     import torch
     g = torch.Generator().manual_seed(seed)
     parts = []

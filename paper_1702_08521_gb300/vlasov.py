@@ -360,7 +360,7 @@ def vp_ensemble_launch_count(ens) -> int:
 
 # ---- learned flux correction -----------------------------------------------------
 
-VP_NET_NPARAM = 2721
+VP_NET_NPARAM = 2977
 
 
 def _sh(stream):

@@ -66,17 +66,21 @@ def test_features_are_scale_invariant():
     assert np.allclose(X1, X2, rtol=1e-12, atol=1e-12)
     assert np.allclose(s2, 1e-6 * s1)
     assert np.all(X1[:, 3] == 0.0)
-    assert np.array_equal(X1[:, 16], nu)
+    assert np.array_equal(X1[:, 24], nu)
 
 
-def test_features_velocity_difference():
+def test_features_velocity_difference_and_curvature():
     # a line between neighbours that differ by a constant c has velocity
-    # features c / (2 s) everywhere; equal neighbours give zero
+    # difference features c / (2 s) everywhere; equal neighbours give zero
     u = np.full((1, 8), 2.0)
     X, s = N.features(u, u + 0.5, u - 0.5, np.array([0.25]))
     assert np.allclose(X[0, 8:16], 0.5 / 2.0)
+    assert np.allclose(X[0, 16:24], 0.0)
     X, _ = N.features(u, u, u, np.array([0.25]))
-    assert np.all(X[0, 8:16] == 0.0)
+    assert np.all(X[0, 8:24] == 0.0)
+    # a parabola in v: neighbours both 1 above gives curvature 2 / (2 s)
+    X, _ = N.features(u, u + 1.0, u + 1.0, np.array([0.25]))
+    assert np.allclose(X[0, 8:16], 0.0) and np.allclose(X[0, 16:24], 1.0 / 2.0)
 
 
 def test_pair_loss_gradients_match_finite_differences():
