@@ -301,10 +301,12 @@ def small_configs_bench(steps: int = 200):
 
 
 def learned_bench(draws: int = 64, eval_steps: int = 20):
-    """Learned velocity-sweep correction on the 2D2V Landau workload
+    """Learned spatial-sweep correction on the 2D2V Landau workload
     (k = (0.5, 0.5), alpha = 0.05): coarse 64^2 x 32^2 grid, trained on pairs
     from 64^2 x 128^2 MP7 FP32 runs of seeded (k, alpha) draws (PCG64 seed
-    1703: k in U[0.3, 0.6], alpha in U[0.01, 0.1]).  Errors: relative L1 at
+    1703: k in U[0.3, 0.6], alpha in U[0.01, 0.1]); three initialisations of
+    10000 Adam steps each, the one with the lowest loss on 5% held-out cell
+    pairs kept.  Errors: relative L1 at
     t = eval_steps dt against the fine 128^2 FP64 run (the GPU FP64 path,
     parity-tested against the oracle), restricted to the compared grid's
     cells.  Equal-error comparison: the plain resolution whose error equals
@@ -334,7 +336,7 @@ def learned_bench(draws: int = 64, eval_steps: int = 20):
     c = torch.cat(cs)
     gen_s = _time.time() - t0
     t0 = _time.time()
-    w, hist = LR.train_net(X, y, iters=3000, batch=32768, lr=2e-3, stream=stream, coef=c)
+    w, hist, heldout = LR.train_select(X, y, c, seeds=(0, 1, 2), iters=10000, batch=32768, lr=2e-3, stream=stream)
     torch.cuda.synchronize()
     train_s = _time.time() - t0
 
@@ -352,13 +354,27 @@ def learned_bench(draws: int = 64, eval_steps: int = 20):
         return float((a - b).abs().sum() / b.abs().sum())
 
     def timed(grid, f0, wts):
-        sim = LR.run(grid, f0, dt, 2, wts, stream)  # warm-up
-        sim.close()
+        # the run whose error is measured, then the step time: after warm-up
+        # steps (autotuning, graph capture) on the same context, eval_steps
+        # graph replays timed with events on the library stream
+        sim = LR.run(grid, f0, dt, eval_steps, wts, stream)
+        f_end = sim.f.clone()
+        stream.synchronize()
+        for _ in range(3):
+            if wts is None:
+                sim.step(dt, 1)
+            else:
+                sim.learned_step(dt, 1, wts)
         a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        sim = LR.run(grid, f0, dt, eval_steps, wts, stream)
+        if wts is None:
+            sim.step(dt, eval_steps)
+        else:
+            sim.learned_step(dt, eval_steps, wts)
         b0.record(stream)
         b0.synchronize()
+        sim.f.copy_(f_end)
+        torch.cuda.synchronize()
         return sim, a0.elapsed_time(b0) / eval_steps
 
     k, a = 0.5, 0.05
@@ -378,7 +394,7 @@ def learned_bench(draws: int = 64, eval_steps: int = 20):
     (e32, t32), (e64, t64) = res[32], res[64]
     out = {"workload": "2D2V Landau k=(0.5,0.5) alpha=0.05, coarse 64^2x32^2, fine 64^2x128^2, KDK dt=0.1",
            "t": eval_steps * dt, "train_pairs": int(y.numel()), "draws": draws,
-           "loss_first_last": [hist[0], hist[-1]],
+           "loss_first_last": [hist[0], hist[-1]], "heldout_loss_per_seed": heldout,
            "loss_without_net": float(((c * y).view(-1, 2).sum(dim=1) ** 2).mean()),
            "gen_s": round(gen_s, 1), "train_s": round(train_s, 1),
            "plain_32": {"l1": e32, "ms_per_step": t32}, "plain_64": {"l1": e64, "ms_per_step": t64},

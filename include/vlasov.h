@@ -297,6 +297,18 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
 int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
                      const float *wts_dev, int use_net, const float *f_snap_dev);
 
+/*
+ * vp_learned_step -- vp_step with every drift (spatial sweep) replaced by
+ * vp_learned_sweep(ctx, 0, d, h, NULL, wts_dev, 1, NULL): the same Strang
+ * sequence (Sec. 2.4, Eq. 55), kicks and field solves unchanged, captured
+ * into a CUDA graph per (dt, split, wts_dev) and replayed.  The network
+ * weights are read at every replay (training may update them in place).
+ * Arguments as vp_step; wts_dev: VP_NET_NPARAM device floats.  VP_ENOTSUP
+ * unless the grid is FP32 with CSL7.
+ */
+int vp_learned_step(vp_ctx *ctx, double dt, int split, int nsteps, double *accel_dev, const float *wts_dev,
+                    int mode, double *diag_dev);
+
 /* Mass that the sweep (kick, dim, dt) of ctx's current f moves through every
  * `every`-th interface of every line, in cell units: G[line][j] for the
  * interface before cell j * every (j = 0 .. L / every); f' = f + G_{i-1/2} -

@@ -179,28 +179,32 @@ int sweep_all(vp_ctx *c, int kick, int dim, double dt, const double *accel) {
 }
 
 // one Strang step (Eq. 55) on the context stream
-int enqueue_step(vp_ctx *c, double dt, int split, double *acc) {
+// one Strang step; with wts the drifts are learned sweeps of that network
+int enqueue_step(vp_ctx *c, double dt, int split, double *acc, const float *wts) {
     const vp_grid &g = c->g;
     const long long NX = c->NX;
     int rc;
+    auto drift = [&](int d, double h) {
+        return wts ? vp_learned_sweep(c, 0, d, h, nullptr, wts, 1, nullptr) : sweep_all(c, 0, d, h, nullptr);
+    };
     if (split == VP_SPLIT_KDK) {
         for (int d = 0; d < g.dv; ++d)
             if ((rc = sweep_all(c, 1, d, 0.5 * dt, acc + d * NX))) return rc;
         for (int d = g.dx - 1; d >= 0; --d)
-            if ((rc = sweep_all(c, 0, d, dt, nullptr))) return rc;
+            if ((rc = drift(d, dt))) return rc;
         if ((rc = vp_launch_moment(c, c->d_rho_s))) return rc;
         if ((rc = vp_launch_poisson(c, c->d_rho_s, c->d_phi_s, acc))) return rc;
         for (int d = 0; d < g.dv; ++d)
             if ((rc = sweep_all(c, 1, d, 0.5 * dt, acc + d * NX))) return rc;
     } else {
         for (int d = g.dx - 1; d >= 0; --d)
-            if ((rc = sweep_all(c, 0, d, 0.5 * dt, nullptr))) return rc;
+            if ((rc = drift(d, 0.5 * dt))) return rc;
         if ((rc = vp_launch_moment(c, c->d_rho_s))) return rc;
         if ((rc = vp_launch_poisson(c, c->d_rho_s, c->d_phi_s, acc))) return rc;
         for (int d = 0; d < g.dv; ++d)
             if ((rc = sweep_all(c, 1, d, dt, acc + d * NX))) return rc;
         for (int d = g.dx - 1; d >= 0; --d)
-            if ((rc = sweep_all(c, 0, d, 0.5 * dt, nullptr))) return rc;
+            if ((rc = drift(d, 0.5 * dt))) return rc;
     }
     return VP_OK;
 }
@@ -427,10 +431,10 @@ int vp_diagnostics(vp_ctx *c, int mode, vp_diag *out) {
     return VP_OK;
 }
 
-int vp_step(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, int mode,
-            double *diag_dev) {
-    int rc = check_ctx(c, true);
-    if (rc) return rc;
+// nsteps Strang steps, captured once per (dt, split, f, accel, network) in a CUDA graph
+static int run_steps(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, int mode, double *diag_dev,
+              const float *wts) {
+    int rc;
     if (!accel_dev) return vp_fail(c, VP_EINVAL, "accel_dev is NULL");
     if (split != VP_SPLIT_KDK && split != VP_SPLIT_DKD) return vp_fail(c, VP_EINVAL, "bad split");
     if (nsteps < 0 || !is_fin(dt)) return vp_fail(c, VP_EINVAL, "bad dt or nsteps");
@@ -443,14 +447,15 @@ int vp_step(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, int 
         for (int d = 0; d < c->g.dv; ++d)
             if ((rc = vp_tune_sweep(c, 1, d))) return rc;
     }
-    if (use_graph && !(gc.valid && gc.dt == dt && gc.split == split && gc.f == c->f && gc.acc == accel_dev)) {
+    if (use_graph && !(gc.valid && gc.dt == dt && gc.split == split && gc.f == c->f && gc.acc == accel_dev &&
+                      gc.wts == wts)) {
         if (gc.valid) {
             cudaGraphExecDestroy(gc.exec);
             gc.valid = 0;
         }
         const long long before = c->launches;
         VP_CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_step(c, dt, split, accel_dev);
+        rc = enqueue_step(c, dt, split, accel_dev, wts);
         cudaGraph_t graph;
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         const long long per_step_captured = c->launches - before;
@@ -465,19 +470,38 @@ int vp_step(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, int 
         gc.split = split;
         gc.f = c->f;
         gc.acc = accel_dev;
+        gc.wts = wts;
         gc.per_step = per_step_captured;
     }
     for (int s = 0; s < nsteps; ++s) {
         if (use_graph) {
             VP_CUDA_TRY(c, cudaGraphLaunch(gc.exec, c->stream));
             c->launches += gc.per_step;
-        } else if ((rc = enqueue_step(c, dt, split, accel_dev))) {
+        } else if ((rc = enqueue_step(c, dt, split, accel_dev, wts))) {
             return rc;
         }
         if (diag_dev && (rc = vp_launch_diag(c, mode, diag_dev + (long long)s * VP_NDIAG))) return rc;
     }
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
+}
+
+int vp_step(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, int mode,
+            double *diag_dev) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    return run_steps(c, dt, split, nsteps, accel_dev, mode, diag_dev, nullptr);
+}
+
+int vp_learned_step(vp_ctx *c, double dt, int split, int nsteps, double *accel_dev, const float *wts_dev,
+                    int mode, double *diag_dev) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    if (!wts_dev) return vp_fail(c, VP_EINVAL, "wts_dev is NULL");
+    if (c->g.precision != VP_F32 || c->g.order != 7)
+        return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
+    if ((rc = vp_learned_prepare(c))) return rc;
+    return run_steps(c, dt, split, nsteps, accel_dev, mode, diag_dev, wts_dev);
 }
 
 }  // extern "C"

@@ -941,6 +941,18 @@ LineGeo line_geo(const vp_grid &g, long long NX, long long NV, int kick, int dim
 }
 }  // namespace
 
+int vp_learned_prepare(vp_ctx *c) {
+    if (c->learned_ready) return VP_OK;
+    if (!c->d_snap) VP_CUDA_TRY(c, cudaMalloc(&c->d_snap, (size_t)c->ncell * sizeof(float)));
+    if (!c->d_netfrag) VP_CUDA_TRY(c, cudaMalloc(&c->d_netfrag, kFragWords * sizeof(uint32_t)));
+    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    c->learned_ready = 1;
+    return VP_OK;
+}
+
 extern "C" {
 
 int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
@@ -951,18 +963,18 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
     if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
         return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
+    int rc = vp_learned_prepare(c);
+    if (rc != VP_OK) return rc;
     if (use_net && !f_snap) {
-        // snapshot of f before the sweep in a library-owned buffer
-        const size_t bytes = (size_t)c->ncell * sizeof(float);
-        if (!c->d_snap) VP_CUDA_TRY(c, cudaMalloc(&c->d_snap, bytes));
-        VP_CUDA_TRY(c, cudaMemcpyAsync(c->d_snap, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        // snapshot of f before the sweep in the library-owned buffer
+        VP_CUDA_TRY(c, cudaMemcpyAsync(c->d_snap, c->f, (size_t)c->ncell * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, c->stream));
         f_snap = static_cast<const float *>(c->d_snap);
     }
     const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
-    int rc = vp_launch_shift_table(c, kick, dim, dt, accel_dev);
+    rc = vp_launch_shift_table(c, kick, dim, dt, accel_dev);
     if (rc != VP_OK) return rc;
     if (use_net) {
-        if (!c->d_netfrag) VP_CUDA_TRY(c, cudaMalloc(&c->d_netfrag, kFragWords * sizeof(uint32_t)));
         k_net_frags<<<1, 256, 0, c->stream>>>(wts, static_cast<uint32_t *>(c->d_netfrag));
         c->launches++;
     }
@@ -985,8 +997,6 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line too long for the learned sweep");
     const long long nl = q.outer * q.inner;
     const unsigned blocks = (unsigned)((nl + NL - 1) / NL);
-    cudaFuncSetAttribute(k_learned_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_learned_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     const LineShift<float> *tab = static_cast<const LineShift<float> *>(c->d_shift);
     const uint4 *frag = static_cast<const uint4 *>(c->d_netfrag);
     LineDiv ldv{};

@@ -94,6 +94,7 @@ struct vp_graph_cache {
     void *f;
     double *acc;
     long long per_step;  // kernels in one captured step
+    const float *wts;    // network of the learned drifts (NULL: plain step)
     int valid;
 };
 
@@ -122,6 +123,7 @@ struct vp_ctx {
     int *d_status;                      // device-side error word (bounded waits)
     void *d_snap;                       // copy of f before a learned sweep (allocated on first use)
     void *d_netfrag;                    // network weights in MMA fragment order (allocated on first use)
+    int learned_ready;                  // learned-sweep buffers allocated, kernel attributes set
     int opt_impl;                       // 0 auto, 1 staged, 2 TMA
     int opt_autotune;                   // 1: time candidate tiles on first use
     SweepTune tune[2][3];               // [kick][dim]
@@ -140,6 +142,8 @@ int vp_fail(vp_ctx *c, int code, const char *fmt, ...);
 
 // launchers implemented in the kernel files; all enqueue on ctx->stream
 int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double *accel);
+// buffers and kernel attributes of the learned sweep (outside any stream capture)
+int vp_learned_prepare(vp_ctx *c);
 int vp_launch_sweep(vp_ctx *c, int kick, int dim);
 int vp_tune_sweep(vp_ctx *c, int kick, int dim);  // outside stream capture only
 int vp_launch_moment(vp_ctx *c, double *rho);

@@ -215,6 +215,44 @@ def train_net(X, y, iters: int = 1500, batch: int = 32768, lr: float = 2e-3, see
     return w, hist
 
 
+def heldout_loss(w, X, y, coef) -> float:
+    """Mean squared cell-update residual of the network w over the pairs
+    (X, y, coef), computed by the training kernel on the current stream."""
+    import torch
+    grad = torch.zeros_like(w)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    V.vp_net_grad(X, y, y.numel(), w, grad, loss, torch.cuda.current_stream(), coef=coef, group=2)
+    return float(loss.item())
+
+
+def train_select(X, y, coef, seeds=(0, 1, 2), holdout: float = 0.05, split_seed: int = 12345, **kw):
+    """Train one network per seed on the cell pairs outside a random held-out
+    fraction and keep the one with the lowest held-out loss (the spread
+    between initialisations is as large as the gain of a better input set).
+    Returns (weights, loss history of the kept run, held-out loss per seed)."""
+    import torch
+    n = y.numel() // 2
+    g = torch.Generator(device="cuda")
+    g.manual_seed(split_seed)
+    perm = torch.randperm(n, device="cuda", generator=g)
+    nh = max(1, int(n * holdout))
+
+    def rows(p):
+        return torch.stack([2 * p, 2 * p + 1], dim=1).reshape(-1)
+
+    ti, hi = rows(perm[nh:]), rows(perm[:nh])
+    Xt, yt, ct = X[ti].contiguous(), y[ti].contiguous(), coef[ti].contiguous()
+    Xh, yh, ch = X[hi].contiguous(), y[hi].contiguous(), coef[hi].contiguous()
+    best, losses = None, []
+    for sd in seeds:
+        w, hist = train_net(Xt, yt, seed=sd, coef=ct, **kw)
+        lh = heldout_loss(w, Xh, yh, ch)
+        losses.append(lh)
+        if best is None or lh < best[0]:
+            best = (lh, w, hist)
+    return best[1], best[2], losses
+
+
 def restricted_initial_state(dims: int, nx: int, nv_fine: int, factor: int, k: float, alpha: float,
                              stream=None):
     """Coarse initial f as the mean of the fine point values (the state the
@@ -239,28 +277,19 @@ def restricted_initial_state(dims: int, nx: int, nv_fine: int, factor: int, k: f
 
 
 def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision: int = V.VP_F32):
-    """KDK run on `grid` from the state f0 with plain sweeps, or with learned
-    spatial sweeps when wts is given; returns the Simulation (caller closes)."""
+    """KDK run on `grid` from the state f0 with plain sweeps (vp_step), or
+    with learned spatial sweeps when wts is given (vp_learned_step); both
+    replay the step as a CUDA graph.  Returns the Simulation (caller closes)."""
     sim = V.Simulation(grid, precision=precision, stream=stream)
     # f0 may still be in flight on the caller's stream
     sim.stream.wait_stream(sim.torch.cuda.current_stream())
     with sim.torch.cuda.stream(sim.stream):
         sim.f.copy_(f0.to(sim.f.dtype))
     sim.field()
-    dims = grid["dims"]
-    for _ in range(steps):
-        for sw in _sweeps(dims):
-            if sw is None:
-                sim.field()
-                continue
-            kick, d, fac = sw
-            acc = sim.accel[d * sim.NX:] if kick else None
-            if kick:
-                V.vp_kick_sweep(sim.ctx, d, fac * dt, acc)
-            elif wts is not None:
-                # the library takes the snapshot of f the velocity neighbours need
-                V.vp_learned_sweep(sim.ctx, 0, d, fac * dt, None, wts, 1)
-            else:
-                V.vp_drift_sweep(sim.ctx, d, fac * dt)
+    if steps > 0:
+        if wts is None:
+            sim.step(dt, steps, split=V.VP_SPLIT_KDK)
+        else:
+            sim.learned_step(dt, steps, wts, split=V.VP_SPLIT_KDK)
     sim.sync()
     return sim

@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_ensemble_sync": (I, [P]),
             "vp_ensemble_launch_count": (LL, [P]),
             "vp_learned_sweep": (I, [P, I, I, D, P, P, I, P]),
+            "vp_learned_step": (I, [P, D, I, I, P, P, I, P]),
             "vp_fine_flux": (I, [P, I, I, D, P, I, P]),
             "vp_fluxnet_line_map": (I, [GP, GP, I, I, I, P, P, P]),
             "vp_group_mean": (I, [P, LL, I, P, I, D, P, P]),
@@ -376,6 +377,10 @@ def vp_learned_sweep(ctx, kick: int, dim: int, dt: float, accel, wts, use_net: i
     _check(ctx, load().vp_learned_sweep(ctx, kick, dim, dt, _ptr(accel), _ptr(wts), use_net, _ptr(f_snap)))
 
 
+def vp_learned_step(ctx, dt: float, split: int, nsteps: int, accel, wts, mode: int = 1, diag=None) -> None:
+    _check(ctx, load().vp_learned_step(ctx, dt, split, nsteps, _ptr(accel), _ptr(wts), mode, _ptr(diag)))
+
+
 def vp_fine_flux(ctx, kick: int, dim: int, dt: float, accel, every: int, G) -> None:
     _check(ctx, load().vp_fine_flux(ctx, kick, dim, dt, _ptr(accel), every, _ptr(G)))
 
@@ -461,6 +466,9 @@ class Simulation:
 
     def step(self, dt: float, nsteps: int, split: int = VP_SPLIT_KDK, mode: int = 1, diag=None):
         vp_step(self.ctx, dt, split, nsteps, self.accel, mode, diag)
+
+    def learned_step(self, dt: float, nsteps: int, wts, split: int = VP_SPLIT_KDK, mode: int = 1, diag=None):
+        vp_learned_step(self.ctx, dt, split, nsteps, self.accel, wts, mode, diag)
 
     def diagnostics(self, mode: int = 1) -> dict:
         return vp_diagnostics(self.ctx, mode)

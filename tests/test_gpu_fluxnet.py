@@ -243,3 +243,48 @@ def test_learned_correction_rejects_velocity_sweeps():
     with pytest.raises(V.VpError):
         V.vp_learned_sweep(sim.ctx, 1, 0, 0.4, acc, w, 1, snapshot(sim))
     sim.close()
+
+
+def test_learned_step_replays_the_sweep_sequence():
+    """vp_learned_step (captured in a CUDA graph) gives, bit for bit, the f
+    of the same KDK sequence issued sweep by sweep: plain kicks, learned
+    drifts (library snapshot), field solve between; and a plain vp_step
+    is unchanged by the learned path having run on the context."""
+    import torch
+    g = _grid2d(8, 16)
+    f0 = (inputs.random_f(8 * 8 * 16 * 16, seed=21, zeros=0.3) ** 2).astype(np.float32)
+    w = _t(N.pack(_params(5, scale=0.5)), torch.float32)
+    dt = 0.2
+    a, _ = both(g, V.VP_F32)
+    b, _ = both(g, V.VP_F32)
+    for sim in (a, b):
+        to_gpu(sim, f0)
+        sim.field()
+    a.learned_step(dt, 3, w)
+    a.sync()
+    for _ in range(3):
+        for d in range(2):
+            V.vp_kick_sweep(b.ctx, d, 0.5 * dt, b.accel[d * b.NX:])
+        for d in (1, 0):
+            V.vp_learned_sweep(b.ctx, 0, d, dt, None, w, 1)
+        b.field()
+        for d in range(2):
+            V.vp_kick_sweep(b.ctx, d, 0.5 * dt, b.accel[d * b.NX:])
+    b.sync()
+    fa, fb = from_gpu(a), from_gpu(b)
+    assert np.array_equal(fa, fb)
+    assert fa.min() >= 0.0
+    # the plain step on the same contexts still matches sweep by sweep
+    a.step(dt, 1)
+    a.sync()
+    for d in range(2):
+        V.vp_kick_sweep(b.ctx, d, 0.5 * dt, b.accel[d * b.NX:])
+    for d in (1, 0):
+        V.vp_drift_sweep(b.ctx, d, dt)
+    b.field()
+    for d in range(2):
+        V.vp_kick_sweep(b.ctx, d, 0.5 * dt, b.accel[d * b.NX:])
+    b.sync()
+    assert np.array_equal(from_gpu(a), from_gpu(b))
+    a.close()
+    b.close()
