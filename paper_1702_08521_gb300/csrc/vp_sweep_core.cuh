@@ -9,6 +9,15 @@ namespace vp_core {
 
 // ---- limiter arithmetic (Appendix A and Sec. 2.1.1) -------------------------
 
+// Every product that meets a sum is written either as fma() or as a
+// round-to-nearest multiply (mul_rn), never left to contraction: the walk
+// step is compiled in several instances (unrolled and remainder loops, the
+// first interface of a segment), and a contraction the compiler takes in one
+// instance but not another would make a cell's last bit depend on where the
+// tile and segment boundaries fall, i.e. on the autotuner's choice.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // minmod of four: min if all > 0, max if all < 0, else 0 (= max(min,0) + min(max,0))
 template <typename T>
 __device__ __forceinline__ T mm4(T a, T b, T c, T d) {
@@ -35,7 +44,7 @@ __device__ __forceinline__ double max3(double a, double b, double c) { return fm
 // curvature d_j = u_{j-1} - 2 u_j + u_{j+1} (App. A)
 template <typename T>
 __device__ __forceinline__ T curv(T um, T u, T up) {
-    return (um + up) - T(2) * u;
+    return fma(T(-2), u, um + up);
 }
 
 // d^{M4} between cells with curvatures x and y (App. A):
@@ -46,8 +55,8 @@ __device__ __forceinline__ T curv(T um, T u, T up) {
 template <typename T>
 __device__ __forceinline__ T dm4(T x, T y) {
     const T m = fmin(x, y), M = fmax(x, y);
-    const T mn = fmin(m, T(4) * m - M);
-    const T mx = fmax(M, T(4) * M - m);
+    const T mn = fmin(m, fma(T(4), m, -M));
+    const T mx = fmax(M, fma(T(4), M, -m));
     return fmin(fmax(T(0), mn), mx);
 }
 
@@ -61,9 +70,9 @@ __device__ __forceinline__ T dm4(T x, T y) {
 template <typename T>
 __device__ __forceinline__ T mp_clamp(T phi, T um1, T u0, T u1, T alpha, T m4m, T m4p) {
     const T back = u0 - um1;
-    const T ful = u0 + alpha * back;
-    const T fmd = T(0.5) * (u0 + u1) - T(0.5) * m4p;
-    const T flc = u0 + T(0.5) * back + (T(4) / T(3)) * m4m;
+    const T ful = fma(alpha, back, u0);
+    const T fmd = fma(T(0.5), u0 + u1, T(-0.5) * m4p);
+    const T flc = fma(T(4) / T(3), m4m, fma(T(0.5), back, u0));
     const T lo = fmax(min3(u0, u1, fmd), min3(u0, ful, flc));
     const T hi = fmin(max3(u0, u1, fmd), max3(u0, ful, flc));
     return fmin(fmax(phi, lo), hi);
@@ -80,9 +89,9 @@ __device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T 
     const T dp = u0 + u2 - T(2) * u1;    // at the downwind cell
     const T m4p = mm4(T(4) * dc - dp, T(4) * dp - dc, dc, dp);
     const T m4m = mm4(T(4) * dm - dc, T(4) * dc - dm, dm, dc);
-    const T ful = u0 + alpha * back;
-    const T fmd = T(0.5) * (u0 + u1) - T(0.5) * m4p;
-    const T flc = u0 + T(0.5) * back + (T(4) / T(3)) * m4m;
+    const T ful = fma(alpha, back, u0);
+    const T fmd = fma(T(0.5), u0 + u1, T(-0.5) * m4p);
+    const T flc = fma(T(4) / T(3), m4m, fma(T(0.5), back, u0));
     const T lo = fmax(fmin(fmin(u0, u1), fmd), fmin(fmin(u0, ful), flc));
     const T hi = fmin(fmax(fmax(u0, u1), fmd), fmax(fmax(u0, ful), flc));
     return fmin(fmax(phi, lo), hi);
@@ -101,7 +110,7 @@ template <typename T>
 __device__ __forceinline__ T mp_limit(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
     const T a = phi - u0;
     const T p = u1 - u0;
-    const T q = alpha * (u0 - um1);
+    const T q = mul_rn(alpha, u0 - um1);
     if ((p - a) * a > T(0) && (q - a) * a > T(0)) return phi;
     return mp_bounds(phi, um2, um1, u0, u1, u2, alpha);
 }
@@ -124,26 +133,26 @@ template <typename T>
 __device__ __forceinline__ T pp_blend(T phi, T u0, T u1, T two_nu, T up, T um) {
     T th = T(1);
     if (up < T(0)) {
-        const T base = u0 - two_nu * u0;  // U^{UP,+}
+        const T base = fma(-two_nu, u0, u0);  // U^{UP,+}
         const T den = base - up;
         th = den > T(0) ? Prec<T>::div(base, den) : T(0);
     }
     if (um < T(0)) {
-        const T base = u1 + two_nu * u0;  // U^{UP,-}
+        const T base = fma(two_nu, u0, u1);  // U^{UP,-}
         const T den = base - um;
         const T t2 = den > T(0) ? Prec<T>::div(base, den) : T(0);
         th = fmin(th, t2);
     }
     th *= Prec<T>::safety;
     th = fmin(fmax(th, T(0)), T(1));
-    return th * phi + (T(1) - th) * u0;
+    return fma(th, phi, mul_rn(T(1) - th, u0));
 }
 
 // PP limiter: keep f_i - 2 nu phi >= 0 and f_{i+1} + 2 nu phi >= 0
 template <typename T>
 __device__ __forceinline__ T pp_limit(T phi, T u0, T u1, T two_nu) {
-    const T up = u0 - two_nu * phi;
-    const T um = u1 + two_nu * phi;
+    const T up = fma(-two_nu, phi, u0);
+    const T um = fma(two_nu, phi, u1);
     if (fmin(up, um) >= T(0)) return phi;
     return pp_blend(phi, u0, u1, two_nu, up, um);
 }
@@ -290,7 +299,7 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
                                              w[(K + 4) & 7], w[(K + 5) & 7], w[(K + 6) & 7],      \
                                              w[(K + 7) & 7], alpha, two_nu, mp, pp, T(0), T(0));  \
         }                                                                                         \
-        store(i, w[(K + 4) & 7] - nu * (fout - fin));                                             \
+        store(i, fma(-nu, fout - fin, w[(K + 4) & 7]));                                           \
         fin = fout;                                                                               \
         i += sg;                                                                                  \
         w[K & 7] = *src;                                                                          \

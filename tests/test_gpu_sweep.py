@@ -185,3 +185,36 @@ def test_sweep_rejects_bad_arguments():
     with pytest.raises(V.VpError):
         V.vp_kick_sweep(sim.ctx, 0, 0.1, None)
     sim.close()
+
+
+@pytest.mark.parametrize("dims,nx,nv", [(2, [8, 8], [16, 16]), (1, [64], [96])])
+def test_sweep_bits_do_not_depend_on_tuning(dims, nx, nv):
+    """Every sweep gives the same bits whatever kernel, tile width and
+    segment count runs it: each implementation with the default tiles, and
+    three independently autotuned contexts (timing-based choices)."""
+    L = 4 * math.pi
+    g = dict(dims=dims, nx=nx, nv=nv, xlo=[0.0] * dims, xhi=[L] * dims, vlo=[-6.0] * dims, vhi=[6.0] * dims,
+             order=7)
+    n = int(np.prod(nx)) * int(np.prod(nv))
+    f0 = (inputs.random_f(n, seed=21, zeros=0.3) ** 2).astype(np.float32)
+    setups = [(0, 0), (1, 0), (2, 0), (0, 1), (0, 1), (1, 1)]  # (sweep impl, autotune)
+    sweeps = [(1, d) for d in range(dims)] + [(0, d) for d in range(dims)]
+    results = []
+    for impl, tune in setups:
+        out = []
+        for kick, d in sweeps:
+            sim, _ = both(g, V.VP_F32)
+            V.vp_set_option(sim.ctx, V.VP_OPT_SWEEP_IMPL, impl)
+            V.vp_set_option(sim.ctx, V.VP_OPT_AUTOTUNE, tune)
+            to_gpu(sim, f0)
+            sim.field()
+            if kick:
+                V.vp_kick_sweep(sim.ctx, d, 0.13, sim.accel[d * sim.NX:])
+            else:
+                V.vp_drift_sweep(sim.ctx, d, 0.37)
+            out.append(from_gpu(sim))
+            sim.close()
+        results.append(out)
+    for out in results[1:]:
+        for a, b in zip(out, results[0]):
+            assert np.array_equal(a, b)
