@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--learned-draws", type=int, default=64)
     p.add_argument("--ensemble-steps", type=int, default=20)
+    p.add_argument("--convergence", action="store_true",
+                   help="add the Sec. 3.2 convergence study of the self-gravitating slab")
     return p.parse_args()
 
 
@@ -297,6 +299,85 @@ def small_configs_bench(steps: int = 200):
                      "dtype": cfg["precision"], "ms_per_step": round(ms, 4),
                      "cell_updates_per_s": ncell * nsw / (ms / 1e3), "bound": "latency (L2-resident)"}
         sim.close()
+    return out
+
+
+def run_slab(ratio: float, n: int, precision: str = "f32"):
+    """The self-gravitating slab of Sec. 3.2 at N_x = N_v = n to t = 4T with
+    SL-MPP7 + PP and the time step of Sec. 2.4 taken every step: dt =
+    nu min(dx / V_max, dv / max|a|), nu = 0.2 (Eqs. 56-58).  The step is the
+    KDK sequence (kick dt/2, drift dt, field, kick dt/2) issued sweep by sweep,
+    since dt changes from step to step.  Returns (f at 4T on the device, steps)."""
+    import torch
+    from paper_1702_08521_gb300 import inputs
+    from paper_1702_08521_gb300 import vlasov as V
+    cfg = inputs.jeans_slab(ratio, n, precision=precision)
+    g = cfg["grid"]
+    sim = V.Simulation(g, precision=V.VP_F32 if precision == "f32" else V.VP_F64)
+    V.vp_init_f(sim.ctx, *cfg["ic"])
+    sim.field()
+    dx = (g["xhi"][0] - g["xlo"][0]) / n
+    vmax = g["vhi"][0]
+    dv = 2.0 * vmax / n
+    t, steps, t_end = 0.0, 0, cfg["t_end"]
+    while t < t_end * (1.0 - 1e-12):
+        with torch.cuda.stream(sim.stream):
+            amax = float(sim.accel.abs().max())
+        dt = cfg["nu"] * min(dx / vmax, dv / amax if amax > 0 else math.inf)
+        dt = min(dt, t_end - t)
+        V.vp_kick_sweep(sim.ctx, 0, 0.5 * dt, sim.accel)
+        V.vp_drift_sweep(sim.ctx, 0, dt)
+        sim.field()
+        V.vp_kick_sweep(sim.ctx, 0, 0.5 * dt, sim.accel)
+        t += dt
+        steps += 1
+    sim.sync()
+    f = sim.f.clone()
+    sim.close()
+    return f, steps
+
+
+def convergence_bench(ratios=(0.5, 1.1), ns=(64, 128, 256, 512), nref: int = 1024):
+    """Sec. 3.2 convergence study: eps_VP (Eq. 72) at t = 4T of FP64 SL-MPP7
+    runs of the slab at N_x = N_v = N against an FP64 N_ref run, restricted to
+    N by averaging N_ref / N x N_ref / N blocks; least-squares orders over all
+    N and over N <= N_ref / 4 (where the reference's own error is small).
+    FP64, because the FP32 round-off of a run grows with N (FP32 / FP64 at
+    t = 4T: 2.3e-5 at N = 512, 7.7e-5 at 1024 for k / k_J = 1.1), which would
+    floor the comparison; the FP32 / FP64 difference at N = 512 is reported."""
+    import time as _time
+    import numpy as np
+    import torch
+    out = {}
+    for ratio in ratios:
+        t0 = _time.time()
+        ref, ref_steps = run_slab(ratio, nref, precision="f64")
+        ref = ref.view(nref, nref)
+        eps, steps, f512 = {}, {}, None
+        for n in ns:
+            f, st = run_slab(ratio, n, precision="f64")
+            r = nref // n
+            fr = ref.view(n, r, n, r).mean(dim=(1, 3))
+            eps[n] = float((f.view(n, n) - fr).abs().sum() / fr.abs().sum())
+            steps[n] = st
+            if n == 512:
+                f512 = f
+        fp_floor = None
+        if f512 is not None:
+            f32, _ = run_slab(ratio, 512)
+            fp_floor = float((f32.double() - f512).abs().sum() / f512.abs().sum())
+
+        def order(sel):
+            lx = np.log(np.array(sel, dtype=float))
+            ly = np.log(np.array([eps[n] for n in sel]))
+            return round(-float(np.polyfit(lx, ly, 1)[0]), 3)
+
+        out[f"k/kJ={ratio}"] = {"eps_vp": {str(n): eps[n] for n in ns}, "steps": {str(n): steps[n] for n in ns},
+                                "n_ref": nref, "ref_steps": ref_steps, "precision": "f64",
+                                "order_fit_all": order(ns),
+                                "order_fit_n_le_ref_over_4": order([n for n in ns if 4 * n <= nref]),
+                                "fp32_vs_fp64_at_512": fp_floor, "seconds": round(_time.time() - t0, 1)}
+        torch.cuda.synchronize()
     return out
 
 
@@ -595,6 +676,10 @@ def main():
         except Exception as ex:  # reported, not hidden
             lrn = {"error": str(ex)[:300]}
 
+    conv = None
+    if args.convergence and rank == 0:
+        conv = convergence_bench()
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         small, desc = small_cfg(cfg)
@@ -613,6 +698,7 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
                "sweeps": per_kind, "tuning": tuning, "ensemble": ens, "l2_resident": l2res, "learned": lrn,
+               "convergence": conv,
                "e2e": e2e,
                "cpu_baseline": cpu}
         print(json.dumps(out))

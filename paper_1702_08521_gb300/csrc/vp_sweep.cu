@@ -559,6 +559,8 @@ SweepTune default_tune(const vp_ctx *c, const SweepGeo &geo) {
         int W = (int)(32768 / sizeof(T) / L);  // ~32 KB staged tile
         W = W > 128 ? 128 : (W < 32 ? 32 : W);
         W &= ~3;
+        // long lines: narrower tiles (down to 4 columns) so the staged lines fit
+        while (W > 4 && (size_t)(L + 2 * ghost_rows(geo)) * W * sizeof(T) > 200 * 1024) W /= 2;
         int nseg = L / 8;
         const int maxseg = 256 / W > 0 ? 256 / W : 1;
         nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
@@ -605,12 +607,14 @@ int tune_t(vp_ctx *c, int kick, int dim) {
     int nc = 0;
     if (geo.inner > 1) {
         const int impls[2] = {2, 1};
+        // lines too long for a 32-column tile take 4-16 columns and more segments
+        const bool longl = (size_t)(geo.L + 2 * ghost_rows(geo)) * 32 * sizeof(T) > 200 * 1024;
         for (int ii = 0; ii < 2; ++ii) {
             if (c->opt_impl && impls[ii] != c->opt_impl) continue;
-            for (int W = 32; W <= 128; W *= 2)
-                for (int nseg = 1; nseg <= 8; nseg *= 2) {
+            for (int W = longl ? 4 : 32; W <= (longl ? 16 : 128); W *= 2)
+                for (int nseg = 1; nseg <= (longl ? 64 : 8); nseg *= 2) {
                     const int th = W * nseg;
-                    if (th < 64 || th > 512 || nseg > geo.L) continue;
+                    if (th < 64 || th > 512 || nseg > geo.L || (longl && nseg * 8 > geo.L)) continue;
                     const int Weff = geo.inner < W ? (int)geo.inner : W;
                     if (impls[ii] == 2 && !tma_eligible<T>(c, geo, Weff)) continue;
                     if (impls[ii] == 1 && (size_t)(geo.L + 2 * ghost_rows(geo)) * W * sizeof(T) > 200 * 1024)

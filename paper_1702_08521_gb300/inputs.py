@@ -18,6 +18,8 @@ standard plasma/stellar-dynamics tests, no external data):
                         dt=0.05, 50 steps.
 * ``ensemble``          512 uneven 1D1V runs + 8 2D2V Landau runs, parameters drawn
                         from numpy PCG64(seed=1702).
+* ``jeans_slab``        1D1V self-gravitating slab of Sec. 3.2 (Test-2), k/k_J = 0.5
+                        (unstable) or 1.1 (damped), G = mean density = L = 1.
 """
 from __future__ import annotations
 
@@ -73,6 +75,25 @@ def plummer(nx: int = 32, nv: int = 64, box: float = 4.0, vbox: float = 1.5) -> 
                            coupling=4.0 * math.pi, rho_bg=0.0),
                 ic=(IC_PLUMMER, [1.0, 1.0, 1.0]),
                 dt=0.05, steps=50, split=SPLIT_DKD, precision="f32", mode=1)
+
+
+def jeans_slab(ratio: float = 0.5, n: int = 64, amp: float | None = None, precision: str = "f32") -> dict:
+    """Sec. 3.2 (Test-2): the slab of Eq. 69 in units G = mean density = L = 1,
+    so that the dynamical time T = (G rho)^(-1/2) = 1 and V = L / T = 1.
+    k = 4 pi / L; sigma from k / k_J = ratio with k_J = (4 pi G rho)^(1/2) / sigma
+    (Eq. 71); A = 0.01 and v in [-V, V] for ratio < 1, A = 0.1 and v in
+    [-2V, 2V] otherwise; periodic x, zero-inflow v, gravity (S = 4 pi G) with
+    the mean density as background.  The runs end at t = 4T with the time step
+    of Sec. 2.4 (nu = 0.2, Eqs. 56-58) taken each step."""
+    k = 4.0 * math.pi
+    sigma = ratio * math.sqrt(4.0 * math.pi) / k
+    vmax = 1.0 if ratio < 1.0 else 2.0
+    a = amp if amp is not None else (0.01 if ratio < 1.0 else 0.1)
+    return dict(name=f"jeans_slab_1d1v_{n}x{n}_k/kJ={ratio}",
+                grid=_grid(1, [n], [n], [0.0], [1.0], [-vmax], [vmax], order=7,
+                           coupling=4.0 * math.pi, rho_bg=1.0),
+                ic=(IC_LANDAU, [a, k, 0.0, 0.0, sigma, 1.0]),
+                k=k, sigma=sigma, t_end=4.0, nu=0.2, split=SPLIT_KDK, precision=precision, mode=2)
 
 
 def advect_1d(n: int, shape: int, order: int = 7, mp: int = 1, pp: int = 1,

@@ -29,6 +29,7 @@ CASES = [
     (1, [64], [130]),
     (1, [300], [33]),
     (1, [6], [1024]),  # long contiguous lines: few lines per CTA, many segments
+    (1, [4096], [20]),  # long strided lines (the 4096-cell limit): tiles narrower than a warp
     (2, [9, 7], [10, 12]),
     (2, [16, 5], [33, 8]),
     (3, [5, 6, 4], [6, 5, 8]),
@@ -120,7 +121,7 @@ def test_fp64_limiter_switches(mp, pp):
     sim.close()
 
 
-@pytest.mark.parametrize("dims,nx,nv", CASES[:4])
+@pytest.mark.parametrize("dims,nx,nv", CASES[:5])
 def test_fp32_sweeps_match_oracle(dims, nx, nv):
     g = grid(dims, nx, nv, order=7)
     sim, og = both(g, V.VP_F32)
@@ -187,7 +188,7 @@ def test_sweep_rejects_bad_arguments():
     sim.close()
 
 
-@pytest.mark.parametrize("dims,nx,nv", [(2, [8, 8], [16, 16]), (1, [64], [96])])
+@pytest.mark.parametrize("dims,nx,nv", [(2, [8, 8], [16, 16]), (1, [64], [96]), (1, [2048], [64])])
 def test_sweep_bits_do_not_depend_on_tuning(dims, nx, nv):
     """Every sweep gives the same bits whatever kernel, tile width and
     segment count runs it: each implementation with the default tiles, and

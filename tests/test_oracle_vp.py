@@ -3,14 +3,16 @@
 Pins: the Landau damping rate and frequency from the kinetic dispersion
 relation (solved here with scipy's Faddeeva function, independent of the
 oracle) against the printed gamma = 0.153; moments of the analytic initial
-conditions; conservation of mass and total energy; the Plummer density.
+conditions; conservation of mass and total energy; the Plummer density; the
+growth and decay rates of the self-gravitating slab of Sec. 3.2 from the
+gravitational form of the same dispersion relation.
 """
 import math
 
 import numpy as np
 import pytest
-from scipy.optimize import fsolve
-from scipy.special import erfc, wofz
+from scipy.optimize import brentq, fsolve
+from scipy.special import erfc, erfcx, wofz
 
 import oracle as O
 from paper_1702_08521_gb300 import inputs
@@ -160,3 +162,93 @@ def test_plummer_density_at_t0():
     core = r2 < 2.0
     assert np.max(np.abs(rho[core] / want[core] - 1)) < 0.05
     assert f.min() >= 0.0
+
+
+# ---- self-gravitating slab (Sec. 3.2, Eqs. 69-71) ----------------------------
+#
+# Linearising the Vlasov equation about f0 = rho N(v; 0, sigma^2) with
+# d^2 phi / dx^2 = 4 pi G (rho - rho_bar) gives, for a mode exp(i(kx - wt)),
+# 1 - (k_J / k)^2 [1 + xi Z(xi)] = 0 with xi = w / (sqrt(2) k sigma): the
+# electron relation with the sign of the coupling reversed.  For k < k_J a
+# purely growing root w = i gamma has xi = i y and 1 + xi Z(xi) =
+# 1 - sqrt(pi) y erfcx(y); for k / k_J = 1.1 the least damped root is purely
+# imaginary as well (w = -0.578 i, found by the scan in the test).
+
+
+def jeans_growth_root(ratio: float) -> float:
+    """gamma of the growing mode for k / k_J = ratio < 1."""
+    y = brentq(lambda y: math.sqrt(math.pi) * y * erfcx(y) - (1.0 - ratio ** 2), 1e-9, 50.0)
+    cfg = inputs.jeans_slab(ratio)
+    return math.sqrt(2.0) * cfg["k"] * cfg["sigma"] * y
+
+
+def jeans_least_damped_root(ratio: float) -> complex:
+    """Root of the full relation with the largest imaginary part (Newton from a
+    grid of starting points)."""
+    cfg = inputs.jeans_slab(ratio)
+    k, sigma = cfg["k"], cfg["sigma"]
+
+    def D(w):
+        xi = w / (math.sqrt(2.0) * k * sigma)
+        return 1.0 - (1.0 / ratio ** 2) * (1.0 + xi * 1j * math.sqrt(math.pi) * wofz(xi))
+
+    roots = []
+    with np.errstate(all="ignore"):  # Newton steps may leave the Faddeeva range
+        roots = _scan(D)
+    return max(roots, key=lambda w: w.imag)
+
+
+def _scan(D):
+    roots = []
+    for wr in np.linspace(0.0, 12.0, 25):
+        for wi in (-0.1, -0.5, -1.0, -3.0):
+            w = complex(wr, wi)
+            for _ in range(80):
+                h = 1e-7
+                dw = -D(w) / ((D(w + h) - D(w - h)) / (2 * h))
+                w += dw
+                if not np.isfinite(w) or abs(dw) < 1e-14:
+                    break
+            if np.isfinite(w) and abs(D(w)) < 1e-10 and w.real >= -1e-9:
+                roots.append(w)
+    return roots
+
+
+def _slab_rate(ratio, n, amp, dt, t0, t1):
+    """Oracle run of the slab; slope of ln|a_k| over [t0, t1] (k = 4 pi / L,
+    mode 2 of the box)."""
+    cfg = inputs.jeans_slab(ratio, n, amp=amp, precision="f64")
+    g, f = _setup(cfg)
+    _, _, acc = O.field(g, f)
+    acc = np.ascontiguousarray(acc)
+    steps = int(round(t1 / dt))
+    diag = O.step(g, f, dt, steps, acc, split=cfg["split"], mode=cfg["mode"], diag=True)
+    t = dt * np.arange(1, steps + 1)
+    sel = (t >= t0 - 1e-9) & (t <= t1 + 1e-9)
+    return np.polyfit(t[sel], np.log(diag[sel, 6]), 1)[0], diag
+
+
+def test_jeans_roots():
+    # the cold limit bounds the kinetic growth rate from above
+    g = jeans_growth_root(0.5)
+    cfg = inputs.jeans_slab(0.5)
+    cold = math.sqrt(4 * math.pi - (cfg["k"] * cfg["sigma"]) ** 2)
+    assert 0.7 * cold < g < cold
+    w = jeans_least_damped_root(1.1)
+    assert abs(w.real) < 1e-6 and -1.0 < w.imag < 0.0
+
+
+def test_oracle_jeans_growth_rate_matches_kinetic_dispersion():
+    """k / k_J = 0.5, 64 x 64, A = 1e-3: the slope of ln|a_k| over t in
+    [0.8, 1.6] T (after the decaying branch, before nonlinearity) equals the
+    growing root within 0.5%."""
+    rate, diag = _slab_rate(0.5, 64, 1e-3, 0.005, 0.8, 1.6)
+    assert rate == pytest.approx(jeans_growth_root(0.5), rel=5e-3), rate
+    assert np.all(diag[:, 4] >= 0.0)
+
+
+def test_oracle_jeans_stable_mode_decays_at_the_kinetic_rate():
+    """k / k_J = 1.1, 64 x 64, A = 1e-3, v in [-2V, 2V]: ln|a_k| falls at the
+    least damped root over t in [1, 3] T within 0.5%."""
+    rate, _ = _slab_rate(1.1, 64, 1e-3, 0.005, 1.0, 3.0)
+    assert rate == pytest.approx(jeans_least_damped_root(1.1).imag, rel=5e-3), rate
