@@ -43,6 +43,7 @@ extern "C" {
 #define VP_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
 #define VP_ENONFINITE (-5)  /* diagnostics found NaN or Inf in f */
 #define VP_ENOTSUP (-6)     /* configuration not supported */
+#define VP_ECFL (-7)        /* a sweep's CFL number is outside the scheme's range (RK-MPP5: |nu| < 1/2) */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define VP_F32 0
@@ -53,6 +54,8 @@ extern "C" {
 #define VP_POIS_ISOLATED 1
 #define VP_SPLIT_KDK 0
 #define VP_SPLIT_DKD 1
+#define VP_SCHEME_SL 0
+#define VP_SCHEME_RK 1
 #define VP_IC_LANDAU 0
 #define VP_IC_TWOSTREAM 1
 #define VP_IC_PLUMMER 2
@@ -77,6 +80,8 @@ typedef struct {
     double coupling;       /* S in lap(phi) = S (rho - rho_bg): 4 pi G for
                               gravity (Eq. 3), -1 for electrons (Eq. 74) */
     double rho_bg;         /* neutralising background density */
+    int scheme;            /* VP_SCHEME_SL: semi-Lagrangian SL-MPP (Eq. 49, any CFL);
+                              VP_SCHEME_RK: RK-MPP5 (Eqs. 8-10, order 5, |nu| < 1/2) */
 } vp_grid;
 
 /* diagnostics of one state, all double precision */

@@ -122,6 +122,9 @@ def _load():
             "vpo_advect_line": (None, [I, I, I, D, I, L, P, L, D]),
             "vpo_nx_total": (L, [GP]),
             "vpo_nv_total": (L, [GP]),
+            "vpo_rk_mpp5_line": (I, [I, I, D, I, L, P, L, D]),
+            "vpo_drift_sweep_rk": (I, [GP, P, I, D]),
+            "vpo_kick_sweep_rk": (I, [GP, P, I, D, P]),
             "vpo_drift_sweep": (I, [GP, P, I, D]),
             "vpo_kick_sweep": (I, [GP, P, I, D, P]),
             "vpo_density_moment": (None, [GP, P, P]),
@@ -205,6 +208,16 @@ def advect_line(line, s: float, *, order: int = 7, mp: int = 1, pp: int = 1,
     return out
 
 
+def rk_line(line, cnu: float, *, mp: int = 1, pp: int = 1, alpha: float = 4.0,
+            bc: int = BC_PERIODIC) -> np.ndarray:
+    """One RK-MPP5 step (Sec. 2.1.1, Eqs. 8-10) of a 1D line with CFL number
+    cnu = c dt / dx (|cnu| < 1/2); returns a new array."""
+    out = _f64(line).copy()
+    if _load().vpo_rk_mpp5_line(mp, pp, alpha, bc, out.size, _p(out), 1, cnu) != 0:
+        raise ValueError("RK-MPP5 needs |c dt / dx| < 1/2")
+    return out
+
+
 # ---- sweeps, moments, Poisson, diagnostics --------------------------------
 
 def _check_f(g: Grid, f: np.ndarray) -> np.ndarray:
@@ -226,6 +239,21 @@ def kick_sweep(g: Grid, f: np.ndarray, dim: int, dt: float, accel_dim) -> None:
         raise ValueError("accel_dim must hold NX values")
     if _load().vpo_kick_sweep(ctypes.byref(g), _p(_check_f(g, f)), dim, dt, _p(a)) != 0:
         raise ValueError("bad kick sweep arguments")
+
+
+def drift_sweep_rk(g: Grid, f: np.ndarray, dim: int, dt: float) -> None:
+    """drift_sweep with RK-MPP5 lines (every |v dt / dx| < 1/2)."""
+    if _load().vpo_drift_sweep_rk(ctypes.byref(g), _p(_check_f(g, f)), dim, dt) != 0:
+        raise ValueError("bad RK drift sweep (|v dt / dx| must stay below 1/2)")
+
+
+def kick_sweep_rk(g: Grid, f: np.ndarray, dim: int, dt: float, accel_dim) -> None:
+    """kick_sweep with RK-MPP5 lines (every |a dt / dv| < 1/2)."""
+    a = _f64(accel_dim)
+    if a.size != g.NX:
+        raise ValueError("accel_dim must hold NX values")
+    if _load().vpo_kick_sweep_rk(ctypes.byref(g), _p(_check_f(g, f)), dim, dt, _p(a)) != 0:
+        raise ValueError("bad RK kick sweep (|a dt / dv| must stay below 1/2)")
 
 
 def density_moment(g: Grid, f: np.ndarray) -> np.ndarray:

@@ -266,6 +266,52 @@ void vpo_advect_line(int order, int mp, int pp, double alpha, int bc, long L,
 }
 
 /* ------------------------------------------------------------------------ */
+/* RK--MPP5, Sec. 2.1.1: Eq. (8) interface value, Eq. (9) MP, the PP limiter  */
+/* of Eqs. (15)-(23), three-stage TVD Runge-Kutta, Eq. (10)                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * Interface value between u[0] = f_i (upwind) and u[1] = f_{i+1}: Eq. (8)
+ * written for the interface i+1/2, i.e. on f_{i-2} .. f_{i+2}.
+ */
+static double rk_interface(int mp, int pp, double alpha, double nu, const double *u) {
+    double phi = (2.0 * u[-2] - 13.0 * u[-1] + 47.0 * u[0] + 27.0 * u[1] - 3.0 * u[2]) / 60.0;
+    if (mp) phi = vpo_mp_constraint(phi, u, alpha);
+    if (pp) phi = vpo_pp_limiter(phi, u[0], u[1], nu);
+    return phi;
+}
+
+/* one Euler stage out_i = g_i - nu L_i(g), L_i = f^_{i+1/2} - f^_{i-1/2};
+ * for c < 0 the stencil is mirrored (sigma = -1) */
+static void rk_stage(int mp, int pp, double alpha, int bc, long L, const double *g, long sigma, double nu,
+                     double *out) {
+    for (long i = 0; i < L; ++i) {
+        double w[7];
+        for (int k = -3; k <= 3; ++k) w[k + 3] = fetch(g, L, bc, i + sigma * k);
+        double flux_out = rk_interface(mp, pp, alpha, nu, &w[3]); /* upwind cell i          */
+        double flux_in = rk_interface(mp, pp, alpha, nu, &w[2]);  /* upwind cell i - sigma  */
+        out[i] = w[3] - nu * (flux_out - flux_in);
+    }
+}
+
+/* One RK--MPP5 step of a line with CFL number cnu = c dt / dx (signed);
+ * returns -1 (line untouched) unless |cnu| < 1/2, the PP limiter's condition. */
+int vpo_rk_mpp5_line(int mp, int pp, double alpha, int bc, long L, double *line, long stride, double cnu) {
+    const long sigma = cnu < 0.0 ? -1 : 1;
+    const double nu = fabs(cnu);
+    if (!(nu < 0.5)) return -1;
+    double *f0 = (double *)malloc(sizeof(double) * 4 * L);
+    double *f1 = f0 + L, *f2 = f1 + L, *e = f2 + L;
+    for (long i = 0; i < L; ++i) f0[i] = line[i * stride];
+    rk_stage(mp, pp, alpha, bc, L, f0, sigma, nu, f1);                 /* f^(1) */
+    rk_stage(mp, pp, alpha, bc, L, f1, sigma, nu, e);
+    for (long i = 0; i < L; ++i) f2[i] = 0.75 * f0[i] + 0.25 * e[i];   /* f^(2) */
+    rk_stage(mp, pp, alpha, bc, L, f2, sigma, nu, e);
+    for (long i = 0; i < L; ++i) line[i * stride] = f0[i] / 3.0 + 2.0 / 3.0 * e[i];
+    free(f0);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* grid helpers                                                             */
 /* ------------------------------------------------------------------------ */
 long vpo_nx_total(const vpo_grid *g) {
@@ -353,6 +399,50 @@ int vpo_kick_sweep(const vpo_grid *g, double *f, int dim, double dt, const doubl
                         inner, s);
     }
     return 0;
+}
+
+/* The sweeps above with RK--MPP5 in place of the SL update (Sec. 2.1.1);
+ * -1 if any line's |c dt / Delta| >= 1/2 (those lines are left unchanged). */
+int vpo_drift_sweep_rk(const vpo_grid *g, double *f, int dim, double dt) {
+    if (!grid_ok(g) || dim < 0 || dim >= g->dx) return -1;
+    const long NV = vpo_nv_total(g);
+    long outer = 1, inner = NV, vstride = 1;
+    for (int k = 0; k < dim; ++k) outer *= g->nx[k];
+    for (int k = dim + 1; k < g->dx; ++k) inner *= g->nx[k];
+    for (int k = dim + 1; k < g->dv; ++k) vstride *= g->nv[k];
+    const long L = g->nx[dim];
+    const double h = dxd(g, dim);
+    const long nlines = outer * inner;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (long line = 0; line < nlines; ++line) {
+        long o = line / inner, c = line % inner;
+        long vid = ((c % NV) / vstride) % g->nv[dim];
+        double cnu = vc(g, dim, vid) * dt / h;
+        bad |= vpo_rk_mpp5_line(g->mp, g->pp, g->alpha, g->xbc, L, f + o * L * inner + c, inner, cnu) != 0;
+    }
+    return bad ? -1 : 0;
+}
+
+int vpo_kick_sweep_rk(const vpo_grid *g, double *f, int dim, double dt, const double *accel_dim) {
+    if (!grid_ok(g) || dim < 0 || dim >= g->dv) return -1;
+    const long NX = vpo_nx_total(g);
+    long vouter = 1, inner = 1;
+    for (int k = 0; k < dim; ++k) vouter *= g->nv[k];
+    for (int k = dim + 1; k < g->dv; ++k) inner *= g->nv[k];
+    const long L = g->nv[dim];
+    const double h = dvd(g, dim);
+    const long nlines = NX * vouter * inner;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (long line = 0; line < nlines; ++line) {
+        long o = line / inner, c = line % inner;
+        long xpt = o / vouter;
+        double cnu = accel_dim[xpt] * dt / h;
+        bad |= vpo_rk_mpp5_line(g->mp, g->pp, g->alpha, VPO_BC_OUTFLOW, L, f + o * L * inner + c, inner,
+                                cnu) != 0;
+    }
+    return bad ? -1 : 0;
 }
 
 /* rho(x) = integral of f over velocity space (Eq. 3) on the mesh. */

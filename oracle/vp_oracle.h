@@ -76,6 +76,9 @@ void vpo_advect_line(int order, int mp, int pp, double alpha, int bc, long L,
 /* ---- sweeps, moments, Poisson, diagnostics, step ------------------------ */
 long vpo_nx_total(const vpo_grid *g);
 long vpo_nv_total(const vpo_grid *g);
+int vpo_rk_mpp5_line(int mp, int pp, double alpha, int bc, long L, double *line, long stride, double cnu);
+int vpo_drift_sweep_rk(const vpo_grid *g, double *f, int dim, double dt);
+int vpo_kick_sweep_rk(const vpo_grid *g, double *f, int dim, double dt, const double *accel_dim);
 int vpo_drift_sweep(const vpo_grid *g, double *f, int dim, double dt);
 int vpo_kick_sweep(const vpo_grid *g, double *f, int dim, double dt, const double *accel_dim);
 void vpo_density_moment(const vpo_grid *g, const double *f, double *rho);

@@ -104,6 +104,14 @@ int validate(const vp_grid *g, char *msg, size_t n) {
         snprintf(msg, n, "xbc must be VP_BC_PERIODIC or VP_BC_OUTFLOW");
         return VP_EINVAL;
     }
+    if (g->scheme != VP_SCHEME_SL && g->scheme != VP_SCHEME_RK) {
+        snprintf(msg, n, "scheme must be VP_SCHEME_SL or VP_SCHEME_RK");
+        return VP_EINVAL;
+    }
+    if (g->scheme == VP_SCHEME_RK && g->order != 5) {
+        snprintf(msg, n, "RK-MPP5 is fifth order: order must be 5");
+        return VP_ENOTSUP;
+    }
     if (g->pois_order != 2 && g->pois_order != 4 && g->pois_order != 6) {
         snprintf(msg, n, "pois_order must be 2, 4 or 6");
         return VP_EINVAL;
@@ -171,6 +179,9 @@ bool capturing(const vp_ctx *c) {
 
 int sweep_all(vp_ctx *c, int kick, int dim, double dt, const double *accel) {
     int rc;
+    // RK-MPP5 (Eq. 10): three stages fused in one launch, default tiles (its
+    // stages do not leave f bit-for-bit unchanged at dt = 0, which the tuner needs)
+    if (c->g.scheme == VP_SCHEME_RK) return vp_launch_rk_sweep(c, kick, dim, dt, accel);
     if (c->opt_autotune && !c->tune[kick][dim].valid && !capturing(c))
         if ((rc = vp_tune_sweep(c, kick, dim))) return rc;
     rc = vp_launch_shift_table(c, kick, dim, dt, accel);
@@ -273,7 +284,7 @@ int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out) {
         delete c;
         return VP_ECUDA;
     }
-    if ((rc = vp_sweep_setup(c)) || (rc = vp_field_setup(c))) {
+    if ((rc = vp_sweep_setup(c)) || (rc = vp_field_setup(c)) || (rc = vp_rk_setup())) {
         fprintf(stderr, "vp_create: %s\n", c->err);
         free_buffers(c);
         delete c;
@@ -410,6 +421,7 @@ int vp_sync(vp_ctx *c) {
     if (st) {
         cudaMemset(c->d_status, 0, sizeof(int));
         if (st == VP_ETIMEOUT) return vp_fail(c, VP_ETIMEOUT, "a device-side wait gave up");
+        if (st == VP_ECFL) return vp_fail(c, VP_ECFL, "an RK-MPP5 sweep had |nu| >= 1/2 (Sec. 2.1.1)");
         return vp_fail(c, VP_ECUDA, "a kernel's self-check failed (status %d)", st);
     }
     return VP_OK;

@@ -144,6 +144,9 @@ int vp_fail(vp_ctx *c, int code, const char *fmt, ...);
 int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double *accel);
 // buffers and kernel attributes of the learned sweep (outside any stream capture)
 int vp_learned_prepare(vp_ctx *c);
+// RK-MPP5 sweeps: kernel attributes once per process, one sweep (table + fused stages)
+int vp_rk_setup();
+int vp_launch_rk_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel);
 int vp_launch_sweep(vp_ctx *c, int kick, int dim);
 int vp_tune_sweep(vp_ctx *c, int kick, int dim);  // outside stream capture only
 int vp_launch_moment(vp_ctx *c, double *rho);

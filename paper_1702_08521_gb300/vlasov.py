@@ -17,11 +17,12 @@ import threading
 
 from . import _build
 
-VP_OK, VP_EINVAL, VP_ECUDA, VP_ENOMEM, VP_ETIMEOUT, VP_ENONFINITE, VP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+VP_OK, VP_EINVAL, VP_ECUDA, VP_ENOMEM, VP_ETIMEOUT, VP_ENONFINITE, VP_ENOTSUP, VP_ECFL = 0, -1, -2, -3, -4, -5, -6, -7
 VP_F32, VP_F64 = 0, 1
 VP_BC_PERIODIC, VP_BC_OUTFLOW = 0, 1
 VP_POIS_PERIODIC, VP_POIS_ISOLATED = 0, 1
 VP_SPLIT_KDK, VP_SPLIT_DKD = 0, 1
+VP_SCHEME_SL, VP_SCHEME_RK = 0, 1
 VP_IC_LANDAU, VP_IC_TWOSTREAM, VP_IC_PLUMMER, VP_IC_ADVECT = 0, 1, 2, 3
 VP_NDIAG = 9
 VP_OPT_SWEEP_IMPL, VP_OPT_AUTOTUNE = 1, 2
@@ -47,6 +48,7 @@ class vp_grid(ctypes.Structure):
         ("pp", ctypes.c_int), ("alpha", ctypes.c_double), ("precision", ctypes.c_int),
         ("poisson", ctypes.c_int), ("pois_order", ctypes.c_int),
         ("coupling", ctypes.c_double), ("rho_bg", ctypes.c_double),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -157,7 +159,7 @@ def _check(ctx, rc: int) -> None:
 def make_grid(dims: int, nx, nv, xlo, xhi, vlo, vhi, *, xbc: int = VP_BC_PERIODIC,
               order: int = 7, mp: int = 1, pp: int = 1, alpha: float = 4.0,
               precision: int = VP_F32, poisson: int = VP_POIS_PERIODIC, pois_order: int = 6,
-              coupling: float = -1.0, rho_bg: float = 1.0, **_ignored) -> vp_grid:
+              coupling: float = -1.0, rho_bg: float = 1.0, scheme: int = 0, **_ignored) -> vp_grid:
     g = vp_grid()
     g.dx = g.dv = dims
     for d in range(dims):
@@ -167,6 +169,7 @@ def make_grid(dims: int, nx, nv, xlo, xhi, vlo, vhi, *, xbc: int = VP_BC_PERIODI
     g.xbc, g.order, g.mp, g.pp, g.alpha = xbc, order, mp, pp, float(alpha)
     g.precision, g.poisson, g.pois_order = precision, poisson, pois_order
     g.coupling, g.rho_bg = float(coupling), float(rho_bg)
+    g.scheme = int(scheme)
     return g
 
 
