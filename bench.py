@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--learned-draws", type=int, default=64)
     p.add_argument("--ensemble-steps", type=int, default=20)
+    p.add_argument("--no-schemes", action="store_true", help="skip the SL-MPP5 / RK-MPP5 sweep comparison")
     p.add_argument("--convergence", action="store_true",
                    help="add the Sec. 3.2 convergence study of the self-gravitating slab")
     return p.parse_args()
@@ -299,6 +300,57 @@ def small_configs_bench(steps: int = 200):
                      "dtype": cfg["precision"], "ms_per_step": round(ms, 4),
                      "cell_updates_per_s": ncell * nsw / (ms / 1e3), "bound": "latency (L2-resident)"}
         sim.close()
+    return out
+
+
+def scheme_compare_bench(sim, cfg, reps: int = 2):
+    """The cost comparison of Sec. 4 on the benchmark's own state: one sweep of
+    every kind with SL-MPP5 (Eq. 49, autotuned tiles) and with RK-MPP5 (Eq.
+    10, three stages fused in one launch), both FP32, both contexts bound to
+    the benchmark's f (the sweeps advance it), dt half the benchmark's so that
+    every line keeps |nu| < 1/2 as RK-MPP5 requires.  Best of `reps` launches
+    after a warm-up (CUDA events on the library stream)."""
+    import torch
+    from paper_1702_08521_gb300 import vlasov as V
+    g = cfg["grid"]
+    dt = 0.5 * cfg["dt"]
+    ctxs = {}
+    for name, scheme in (("sl_mpp5", V.VP_SCHEME_SL), ("rk_mpp5", V.VP_SCHEME_RK)):
+        grid = V.make_grid(**{**g, "order": 5, "scheme": scheme, "precision": V.VP_F32})
+        ctx = V.vp_create(grid, sim.stream)
+        V.vp_bind_f(ctx, sim.f)
+        ctxs[name] = ctx
+    out = {}
+    try:
+        for kick in (0, 1):
+            for d in range(g["dims"]):
+                row = {}
+                for name, ctx in ctxs.items():
+                    def launch():
+                        if kick:
+                            V.vp_kick_sweep(ctx, d, dt, sim.accel[d * sim.NX:])
+                        else:
+                            V.vp_drift_sweep(ctx, d, dt)
+                    launch()
+                    V.vp_sync(ctx)
+                    ts = []
+                    for _ in range(reps):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(sim.stream)
+                        launch()
+                        b.record(sim.stream)
+                        b.synchronize()
+                        ts.append(a.elapsed_time(b))
+                    V.vp_sync(ctx)
+                    row[name + "_ms"] = round(min(ts), 4)
+                row["ratio"] = round(row["rk_mpp5_ms"] / row["sl_mpp5_ms"], 3)
+                out[("kick_v" if kick else "drift_x") + str(d + 1)] = row
+    finally:
+        for ctx in ctxs.values():
+            V.vp_destroy(ctx)
+    tot = {k: sum(r[k + "_ms"] for r in out.values()) for k in ("sl_mpp5", "rk_mpp5")}
+    out["all_kinds"] = {"sl_mpp5_ms": round(tot["sl_mpp5"], 4), "rk_mpp5_ms": round(tot["rk_mpp5"], 4),
+                        "ratio": round(tot["rk_mpp5"] / tot["sl_mpp5"], 3)}
     return out
 
 
@@ -630,6 +682,13 @@ def main():
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "frac_of_spec_8tbs": round(achieved / 8000.0, 4)}
 
+    schemes = None
+    if not args.no_schemes and rank == 0:
+        try:
+            schemes = scheme_compare_bench(sim, cfg)
+        except Exception as ex:  # reported, not hidden
+            schemes = {"error": str(ex)[:300]}
+
     # end to end through the C ABI with host buffers: H2D f, one step, D2H f
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -698,7 +757,7 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
                "sweeps": per_kind, "tuning": tuning, "ensemble": ens, "l2_resident": l2res, "learned": lrn,
-               "convergence": conv,
+               "convergence": conv, "rk_vs_sl": schemes,
                "e2e": e2e,
                "cpu_baseline": cpu}
         print(json.dumps(out))

@@ -69,7 +69,7 @@ struct StageStore {
 };
 
 // Strided lines: a tile of W consecutive lines (columns), rows at pitch W.
-template <typename T, bool PERIODIC>
+template <typename T, bool PERIODIC, bool FULL>
 __global__ void __launch_bounds__(512) k_rk_cols(T *__restrict__ f, const LineShift<T> *__restrict__ tab,
                                                  SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -125,24 +125,24 @@ __global__ void __launch_bounds__(512) k_rk_cols(T *__restrict__ f, const LineSh
     constexpr int G = PERIODIC ? 1 : VP_GHOST;
     if (act) {  // f^(1) = f^n - nu L(f^n)
         StageStore<T, false> s1{b0 + cc + i0 * W, nullptr, st, 0, T(0), T(0)};
-        vp_core::walk<T, 5, PERIODIC, false, G>(a0 + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s1);
+        vp_core::walk<T, 5, PERIODIC, FULL, G>(a0 + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s1);
     }
     __syncthreads();
     if (act) {  // f^(2) = 3/4 f^n + 1/4 (f^(1) - nu L(f^(1)))
         StageStore<T, true> s2{c0p + cc + i0 * W, a0 + cc + i0 * W, st, st, T(0.75), T(0.25)};
-        vp_core::walk<T, 5, PERIODIC, false, G>(b0 + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s2);
+        vp_core::walk<T, 5, PERIODIC, FULL, G>(b0 + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s2);
     }
     __syncthreads();
     if (act) {  // f^{n+1} = 1/3 f^n + 2/3 (f^(2) - nu L(f^(2)))
         StageStore<T, true> s3{base + cc + (long long)i0 * geo.inner, a0 + cc + i0 * W,
                                (long long)sh.sigma * geo.inner, st, T(1) / T(3), T(2) / T(3)};
-        vp_core::walk<T, 5, PERIODIC, false, G>(c0p + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s3);
+        vp_core::walk<T, 5, PERIODIC, FULL, G>(c0p + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s3);
     }
 }
 
 // Contiguous lines: R lines per CTA, each a row at odd pitch P (ghosts on
 // both sides); the result goes to a fourth tile at pitch Q and out in rows.
-template <typename T>
+template <typename T, bool FULL>
 __global__ void __launch_bounds__(512) k_rk_rows(T *__restrict__ f, const LineShift<T> *__restrict__ tab,
                                                  SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -163,9 +163,21 @@ __global__ void __launch_bounds__(512) k_rk_rows(T *__restrict__ f, const LineSh
         A[r * P + k] = B[r * P + k] = C[r * P + k] = T(0);
         A[r * P + GP + L + k] = B[r * P + GP + L + k] = C[r * P + GP + L + k] = T(0);
     }
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int r = (int)fdiv(e, geo.fd_l), pos = e - r * L;
-        A[r * P + GP + pos] = base[e];
+    constexpr int VEC = 16 / sizeof(T);
+    const bool vec = (L % VEC) == 0;  // rows start on 16-byte boundaries of f
+    if (vec) {
+        for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
+            const float4 x = *reinterpret_cast<const float4 *>(base + e);
+            const T *xv = reinterpret_cast<const T *>(&x);
+            const int r = (int)fdiv(e, geo.fd_l), pos = e - r * L;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) A[r * P + GP + pos + k] = xv[k];
+        }
+    } else {
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int r = (int)fdiv(e, geo.fd_l), pos = e - r * L;
+            A[r * P + GP + pos] = base[e];
+        }
     }
     __syncthreads();
     const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
@@ -184,22 +196,33 @@ __global__ void __launch_bounds__(512) k_rk_rows(T *__restrict__ f, const LineSh
     T *a0 = A + line * P + GP, *b0 = B + line * P + GP, *c0p = C + line * P + GP;
     if (act) {
         StageStore<T, false> s1{b0 + i0, nullptr, sg, 0, T(0), T(0)};
-        vp_core::walk<T, 5, false, false, VP_GHOST>(a0, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s1);
+        vp_core::walk<T, 5, false, FULL, VP_GHOST>(a0, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s1);
     }
     __syncthreads();
     if (act) {
         StageStore<T, true> s2{c0p + i0, a0 + i0, sg, sg, T(0.75), T(0.25)};
-        vp_core::walk<T, 5, false, false, VP_GHOST>(b0, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s2);
+        vp_core::walk<T, 5, false, FULL, VP_GHOST>(b0, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s2);
     }
     __syncthreads();
     if (act) {
         StageStore<T, true> s3{out + line * Q + i0, a0 + i0, sg, sg, T(1) / T(3), T(2) / T(3)};
-        vp_core::walk<T, 5, false, false, VP_GHOST>(c0p, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s3);
+        vp_core::walk<T, 5, false, FULL, VP_GHOST>(c0p, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s3);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int r = (int)fdiv(e, geo.fd_l), pos = e - r * L;
-        base[e] = out[r * Q + pos];
+    if (vec) {
+        for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
+            float4 x;
+            T *xv = reinterpret_cast<T *>(&x);
+            const int r = (int)fdiv(e, geo.fd_l), pos = e - r * L;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) xv[k] = out[r * Q + pos + k];
+            *reinterpret_cast<float4 *>(base + e) = x;
+        }
+    } else {
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int r = (int)fdiv(e, geo.fd_l), pos = e - r * L;
+            base[e] = out[r * Q + pos];
+        }
     }
 }
 
@@ -246,13 +269,18 @@ int launch_rk(vp_ctx *c, int kick, int dim) {
     const int L = geo.L;
     if (geo.inner > 1) {
         const int gp = geo.periodic ? 0 : VP_GHOST;
-        int W = 32;
+        // up to 128 lines per tile within 100 KB, narrower for long lines;
+        // segments of at least 16 cells (each stage restarts the walk at every
+        // segment), up to 512 threads (measured best of four tile rules on the
+        // Plummer 32^3 x 64^3 state)
+        int W = 128;
+        while (W > 32 && (size_t)3 * (L + 2 * gp) * W * sizeof(T) > 100 * 1024) W /= 2;
         while (W > 4 && (size_t)3 * (L + 2 * gp) * W * sizeof(T) > 200 * 1024) W /= 2;
         if (geo.inner < W) W = (int)geo.inner;
         const size_t smem = (size_t)3 * (L + 2 * gp) * W * sizeof(T);
         if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
-        int nseg = L / 8;
-        const int maxseg = 256 / W > 0 ? 256 / W : 1;
+        int nseg = L / 16;
+        const int maxseg = 512 / W > 0 ? 512 / W : 1;
         nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
         geo.W = W;
         geo.nseg = nseg;
@@ -264,10 +292,15 @@ int launch_rk(vp_ctx *c, int kick, int dim) {
         geo.fd_nseg = make_fastdiv((unsigned)nseg);
         geo.fd_wv = make_fastdiv((unsigned)(W / (16 / sizeof(T)) > 0 ? W / (16 / sizeof(T)) : 1));
         const int threads = ((W * nseg + 31) / 32) * 32;
-        if (geo.periodic)
-            k_rk_cols<T, true><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+        const bool full = c->g.mp && c->g.pp;
+        if (geo.periodic && full)
+            k_rk_cols<T, true, true><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+        else if (geo.periodic)
+            k_rk_cols<T, true, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+        else if (full)
+            k_rk_cols<T, false, true><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
         else
-            k_rk_cols<T, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+            k_rk_cols<T, false, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
     } else {
         const int P = (L + 2 * VP_GHOST) | 1, Q = L | 1;
         int R = 4096 / L;
@@ -287,18 +320,27 @@ int launch_rk(vp_ctx *c, int kick, int dim) {
         const long long blocks = (geo.outer + R - 1) / R;
         if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
         const int threads = ((R * nseg + 31) / 32) * 32;
-        k_rk_rows<T><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
+        if (c->g.mp && c->g.pp)
+            k_rk_rows<T, true><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
+        else
+            k_rk_rows<T, false><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp);
     }
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
 }
 
+template <typename T, bool FULL>
+void rk_attrs_one() {
+    cudaFuncSetAttribute(k_rk_cols<T, true, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rk_cols<T, false, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rk_rows<T, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 template <typename T>
 void rk_attrs() {
-    cudaFuncSetAttribute(k_rk_cols<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_rk_cols<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_rk_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    rk_attrs_one<T, true>();
+    rk_attrs_one<T, false>();
 }
 
 }  // namespace
