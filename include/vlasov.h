@@ -60,6 +60,7 @@ extern "C" {
 #define VP_IC_TWOSTREAM 1
 #define VP_IC_PLUMMER 2
 #define VP_IC_ADVECT 3
+#define VP_IC_SPHERE 4
 #define VP_NDIAG 9
 
 /* ---- grid and scheme --------------------------------------------------- */
@@ -135,6 +136,8 @@ int vp_bind_f(vp_ctx *ctx, void *f_dev);
  *   VP_IC_TWOSTREAM params {alpha, k}: v_1^2 exp(-|v|^2/2)/(2 pi)^{D/2} (1 + alpha cos k x_1)
  *   VP_IC_PLUMMER   params {G, M, a}: isotropic Plummer distribution function
  *   VP_IC_ADVECT    params {shape}: Test-1 profiles in x (Eqs. 60, 62, 63, 65-67)
+ *   VP_IC_SPHERE    params {G, M, R}: uniform sphere of mass M and radius 2R about
+ *                   the box centre, Maxwellian with sigma^2 = G M / (20 R) (Eq. 77)
  */
 int vp_init_f(vp_ctx *ctx, int kind, const double *params, int nparams);
 

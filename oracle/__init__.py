@@ -31,7 +31,7 @@ _lib = None
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 POIS_PERIODIC, POIS_ISOLATED = 0, 1
 SPLIT_KDK, SPLIT_DKD = 0, 1
-IC_LANDAU, IC_TWOSTREAM, IC_PLUMMER, IC_ADVECT = 0, 1, 2, 3
+IC_LANDAU, IC_TWOSTREAM, IC_PLUMMER, IC_ADVECT, IC_SPHERE = 0, 1, 2, 3, 4
 NDIAG = 9
 DIAG_NAMES = ("mass", "ke", "fe", "pe", "min_f", "max_f", "mode_amp", "l1", "l2")
 

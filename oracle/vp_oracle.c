@@ -781,6 +781,10 @@ int vpo_step(const vpo_grid *g, double *f, double dt, int split, int nsteps, dou
  * VPO_IC_PLUMMER  params {G, M, a}: isotropic Plummer distribution
  *     F(E) = 24 sqrt(2) / (7 pi^3) a^2 / (G^5 M^4) (-E)^{7/2}, E < 0,
  *     E = |v|^2 / 2 - G M / sqrt(r^2 + a^2), r from the box centre
+ * VPO_IC_SPHERE   params {G, M, R}: Sec. 3.4 (Eq. 77): a sphere of mass M and
+ *     radius 2R about the box centre of uniform density rho0 = M / (4 pi (2R)^3 / 3),
+ *     rho0 (2 pi sigma^2)^{-3/2} exp(-|v|^2 / 2 sigma^2), sigma^2 = G M / (20 R),
+ *     inside (r < 2R), zero outside
  * VPO_IC_ADVECT   params {shape}: Test-1 profiles in x on [0, 1)^D,
  *     0: rectangle (Eqs. 60, 65), 1: 1 + (1/D) sum sin(2 pi x_d) (Eqs. 62, 66),
  *     2: sum sin^4(4 pi x_d) (Eqs. 63, 67); constant in v.
@@ -831,6 +835,17 @@ int vpo_init_f(const vpo_grid *g, int kind, const double *p, int np, double *f) 
                 val = E < 0.0 ? 24.0 * sqrt(2.0) / (7.0 * M_PI * M_PI * M_PI) * a * a /
                                     (pow(G, 5.0) * pow(M, 4.0)) * pow(-E, 3.5)
                               : 0.0;
+            } else if (kind == VPO_IC_SPHERE) {
+                if (np < 3 || D != 3) return -1;
+                double G = p[0], M = p[1], R = p[2], r2 = 0.0, v2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double c = 0.5 * (g->xlo[d] + g->xhi[d]);
+                    r2 += (xs[d] - c) * (xs[d] - c);
+                    v2 += vs[d] * vs[d];
+                }
+                double rho0 = M / (4.0 * M_PI * pow(2.0 * R, 3.0) / 3.0);
+                double s2 = G * M / (20.0 * R);
+                val = r2 < (2.0 * R) * (2.0 * R) ? rho0 * exp(-v2 / (2.0 * s2)) / pow(2.0 * M_PI * s2, 1.5) : 0.0;
             } else if (kind == VPO_IC_ADVECT) {
                 if (np < 1) return -1;
                 int shape = (int)p[0];

@@ -39,6 +39,7 @@ extern "C" {
 #define VPO_IC_TWOSTREAM 1
 #define VPO_IC_PLUMMER 2
 #define VPO_IC_ADVECT 3
+#define VPO_IC_SPHERE 4
 
 #define VPO_NDIAG 9 /* mass, ke, fe, pe, min_f, max_f, mode_amp, l1, l2 */
 

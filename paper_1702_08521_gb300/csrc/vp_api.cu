@@ -321,12 +321,12 @@ int vp_bind_f(vp_ctx *c, void *f_dev) {
 int vp_init_f(vp_ctx *c, int kind, const double *params, int nparams) {
     int rc = check_ctx(c, true);
     if (rc) return rc;
-    static const int need[4] = {6, 2, 3, 1};
-    if (kind < 0 || kind > 3) return vp_fail(c, VP_EINVAL, "unknown initial condition %d", kind);
+    static const int need[5] = {6, 2, 3, 1, 3};
+    if (kind < 0 || kind > 4) return vp_fail(c, VP_EINVAL, "unknown initial condition %d", kind);
     if (!params || nparams < need[kind])
         return vp_fail(c, VP_EINVAL, "initial condition %d needs %d parameters", kind, need[kind]);
-    if (kind == VP_IC_PLUMMER && c->g.dx != 3)
-        return vp_fail(c, VP_EINVAL, "the Plummer sphere needs 3D3V");
+    if ((kind == VP_IC_PLUMMER || kind == VP_IC_SPHERE) && c->g.dx != 3)
+        return vp_fail(c, VP_EINVAL, "the Plummer and uniform spheres need 3D3V");
     for (int i = 0; i < nparams; ++i)
         if (!is_fin(params[i])) return vp_fail(c, VP_EINVAL, "non-finite parameter");
     return vp_launch_init(c, kind, params, nparams);

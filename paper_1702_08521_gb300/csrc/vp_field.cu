@@ -389,6 +389,18 @@ __global__ void k_init(T *__restrict__ f, long long ncell, IcArgs a) {
         val = E < 0.0 ? 24.0 * sqrt(2.0) * b * b / (7.0 * kPi * kPi * kPi * pow(G, 5.0) * pow(M, 4.0)) *
                             pow(-E, 3.5)
                       : 0.0;
+    } else if (a.kind == VP_IC_SPHERE) {
+        // uniform sphere of mass M and radius 2R about the box centre with a
+        // Maxwellian of sigma^2 = G M / (20 R) (Eq. 77, Sec. 3.4)
+        const double G = a.p[0], M = a.p[1], R = a.p[2];
+        const double rho0 = M / (4.0 * kPi * (8.0 * R * R * R) / 3.0);
+        const double s2 = G * M / (20.0 * R);
+        double r2 = 0.0, v2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            r2 += (xs[d] - a.xc[d]) * (xs[d] - a.xc[d]);
+            v2 += vs[d] * vs[d];
+        }
+        val = r2 < 4.0 * R * R ? rho0 * exp(-v2 / (2.0 * s2)) / pow(2.0 * kPi * s2, 1.5) : 0.0;
     } else {
         const int shape = (int)a.p[0];
         if (shape == 0) {

@@ -20,6 +20,8 @@ standard plasma/stellar-dynamics tests, no external data):
                         from numpy PCG64(seed=1702).
 * ``jeans_slab``        1D1V self-gravitating slab of Sec. 3.2 (Test-2), k/k_J = 0.5
                         (unstable) or 1.1 (damped), G = mean density = L = 1.
+* ``uniform_sphere``    3D3V collapse of a uniform sphere (Sec. 3.4, Test-4),
+                        64^3 x 32^3, G = M = R = 1.
 """
 from __future__ import annotations
 
@@ -33,7 +35,7 @@ TWO_PI = 2.0 * math.pi
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 POIS_PERIODIC, POIS_ISOLATED = 0, 1
 SPLIT_KDK, SPLIT_DKD = 0, 1
-IC_LANDAU, IC_TWOSTREAM, IC_PLUMMER, IC_ADVECT = 0, 1, 2, 3
+IC_LANDAU, IC_TWOSTREAM, IC_PLUMMER, IC_ADVECT, IC_SPHERE = 0, 1, 2, 3, 4
 
 
 def _grid(dims, nx, nv, xlo, xhi, vlo, vhi, **kw) -> dict:
@@ -75,6 +77,20 @@ def plummer(nx: int = 32, nv: int = 64, box: float = 4.0, vbox: float = 1.5) -> 
                            coupling=4.0 * math.pi, rho_bg=0.0),
                 ic=(IC_PLUMMER, [1.0, 1.0, 1.0]),
                 dt=0.05, steps=50, split=SPLIT_DKD, precision="f32", mode=1)
+
+
+def uniform_sphere(nx: int = 64, nv: int = 32, precision: str = "f32") -> dict:
+    """Sec. 3.4 (Test-4): a uniform sphere of mass M and radius 2R (Eq. 77,
+    sigma^2 = G M / (20 R), virial ratio 0.5) in units G = M = R = 1, so that
+    T = (R^3 / G M)^(1/2) = 1 and V = R / T = 1; box [-3R, 3R]^3 x [-3V, 3V]^3
+    with outgoing boundaries in x and v and the isolated Poisson solver;
+    SL-MPP7, DKD, the time step of Sec. 2.4 (nu = 0.2) each step, to t = 8T."""
+    return dict(name=f"uniform_sphere_3d3v_{nx}^3x{nv}^3",
+                grid=_grid(3, [nx] * 3, [nv] * 3, [-3.0] * 3, [3.0] * 3, [-3.0] * 3, [3.0] * 3,
+                           order=7, xbc=BC_OUTFLOW, poisson=POIS_ISOLATED, pois_order=6,
+                           coupling=4.0 * math.pi, rho_bg=0.0),
+                ic=(IC_SPHERE, [1.0, 1.0, 1.0]),
+                t_end=8.0, nu=0.2, split=SPLIT_DKD, precision=precision, mode=1)
 
 
 def jeans_slab(ratio: float = 0.5, n: int = 64, amp: float | None = None, precision: str = "f32") -> dict:

@@ -23,7 +23,7 @@ VP_BC_PERIODIC, VP_BC_OUTFLOW = 0, 1
 VP_POIS_PERIODIC, VP_POIS_ISOLATED = 0, 1
 VP_SPLIT_KDK, VP_SPLIT_DKD = 0, 1
 VP_SCHEME_SL, VP_SCHEME_RK = 0, 1
-VP_IC_LANDAU, VP_IC_TWOSTREAM, VP_IC_PLUMMER, VP_IC_ADVECT = 0, 1, 2, 3
+VP_IC_LANDAU, VP_IC_TWOSTREAM, VP_IC_PLUMMER, VP_IC_ADVECT, VP_IC_SPHERE = 0, 1, 2, 3, 4
 VP_NDIAG = 9
 VP_OPT_SWEEP_IMPL, VP_OPT_AUTOTUNE = 1, 2
 DIAG_NAMES = ("mass", "ke", "fe", "pe", "min_f", "max_f", "mode_amp", "l1", "l2")

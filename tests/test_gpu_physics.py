@@ -88,3 +88,20 @@ def test_self_gravitating_slab(ratio, t0, t1):
     want = jeans_growth_root(ratio) if ratio < 1 else jeans_least_damped_root(ratio).imag
     assert rate == pytest.approx(want, rel=5e-3), (rate, want)
     assert f32.min() >= 0.0
+
+
+def test_uniform_sphere_ic_and_steps_match_oracle():
+    """Sec. 3.4 sphere at 16^3 x 8^3 (FP64): the initial state equals the
+    oracle's, and so does the state after 3 DKD steps of dt = 0.05."""
+    cfg = inputs.uniform_sphere(16, 8, precision="f64")
+    sim, og = both(cfg["grid"], V.VP_F64)
+    V.vp_init_f(sim.ctx, *cfg["ic"])
+    f_o = O.init_f(og, *cfg["ic"])
+    assert rel_max(from_gpu(sim), f_o) <= 1e-14
+    sim.field()
+    _, _, acc = O.field(og, f_o)
+    acc = np.ascontiguousarray(acc)
+    sim.step(0.05, 3, split=cfg["split"])
+    O.step(og, f_o, 0.05, 3, acc, split=cfg["split"], mode=1)
+    assert rel_max(from_gpu(sim), f_o) <= 1e-12
+    sim.close()

@@ -252,3 +252,27 @@ def test_oracle_jeans_stable_mode_decays_at_the_kinetic_rate():
     least damped root over t in [1, 3] T within 0.5%."""
     rate, _ = _slab_rate(1.1, 64, 1e-3, 0.005, 1.0, 3.0)
     assert rate == pytest.approx(jeans_least_damped_root(1.1).imag, rel=5e-3), rate
+
+
+# ---- uniform-sphere collapse (Sec. 3.4, Eq. 77) ------------------------------
+
+
+def test_uniform_sphere_initial_state():
+    """The sampled sphere carries the closed-form moments of a uniform sphere
+    of mass M = 1, radius 2R = 2 with sigma^2 = GM/(20R): mass M, kinetic
+    energy 3/2 M sigma^2 = 0.075, potential energy -3 G M^2 / (5 * 2R) = -0.3,
+    virial ratio 2K/|W| = 0.5 as the paper sets it, within the error of a
+    sphere sampled on 32^3 cell centres (and approaching them from 16^3)."""
+    res = {}
+    for n in (16, 32):
+        cfg = inputs.uniform_sphere(n, 16, precision="f64")
+        g, f = _setup(cfg)
+        res[n] = O.diagnostics(g, f)
+    d16, d32 = res[16], res[32]
+    assert d32["mass"] == pytest.approx(1.0, rel=0.02)
+    assert d32["ke"] == pytest.approx(0.075, rel=0.02)
+    assert d32["pe"] == pytest.approx(-0.3, rel=0.03)
+    assert 2 * d32["ke"] / abs(d32["pe"]) == pytest.approx(0.5, rel=0.05)
+    assert abs(d32["mass"] - 1) < abs(d16["mass"] - 1)
+    assert abs(d32["pe"] + 0.3) < abs(d16["pe"] + 0.3)
+    assert d32["min_f"] == 0.0
