@@ -133,6 +133,43 @@ struct vp_ctx {
 
 // error helpers
 int vp_fail(vp_ctx *c, int code, const char *fmt, ...);
+
+// line geometry of the sweep (kick, dim): lines of L cells at stride
+// `inner`, `outer` blocks of them, and the class of a line (its velocity index
+// for drifts, its spatial point for kicks) that selects its shift
+inline SweepGeo vp_make_geo(const vp_ctx *c, int kick, int dim) {
+
+    const vp_grid &g = c->g;
+    SweepGeo geo{};
+    if (!kick) {
+        long long outer = 1, inner = c->NV, vstride = 1;
+        for (int k = 0; k < dim; ++k) outer *= g.nx[k];
+        for (int k = dim + 1; k < g.dx; ++k) inner *= g.nx[k];
+        for (int k = dim + 1; k < g.dv; ++k) vstride *= g.nv[k];
+        geo.outer = outer;
+        geo.inner = inner;
+        geo.L = g.nx[dim];
+        geo.periodic = g.xbc == VP_BC_PERIODIC;
+        geo.cls_from_inner = 1;
+        geo.cdiv = vstride;
+        geo.cmod = g.nv[dim];
+    } else {
+        long long vouter = 1, inner = 1;
+        for (int k = 0; k < dim; ++k) vouter *= g.nv[k];
+        for (int k = dim + 1; k < g.dv; ++k) inner *= g.nv[k];
+        geo.outer = c->NX * vouter;
+        geo.inner = inner;
+        geo.L = g.nv[dim];
+        geo.periodic = 0;
+        geo.cls_from_inner = 0;
+        geo.cdiv = vouter;
+        geo.cmod = 1;
+    }
+    geo.fd_cdiv = make_fastdiv((unsigned)geo.cdiv);
+    geo.fd_cmod = make_fastdiv((unsigned)geo.cmod);
+    return geo;
+}
+
 #define VP_CUDA_TRY(ctx, call)                                                         \
     do {                                                                               \
         cudaError_t e_ = (call);                                                       \

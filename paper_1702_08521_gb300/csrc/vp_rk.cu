@@ -226,41 +226,10 @@ __global__ void __launch_bounds__(512) k_rk_rows(T *__restrict__ f, const LineSh
     }
 }
 
-SweepGeo rk_geo(const vp_ctx *c, int kick, int dim) {
-    const vp_grid &g = c->g;
-    SweepGeo geo{};
-    if (!kick) {
-        long long outer = 1, inner = c->NV, vstride = 1;
-        for (int k = 0; k < dim; ++k) outer *= g.nx[k];
-        for (int k = dim + 1; k < g.dx; ++k) inner *= g.nx[k];
-        for (int k = dim + 1; k < g.dv; ++k) vstride *= g.nv[k];
-        geo.outer = outer;
-        geo.inner = inner;
-        geo.L = g.nx[dim];
-        geo.periodic = g.xbc == VP_BC_PERIODIC;
-        geo.cls_from_inner = 1;
-        geo.cdiv = vstride;
-        geo.cmod = g.nv[dim];
-    } else {
-        long long vouter = 1, inner = 1;
-        for (int k = 0; k < dim; ++k) vouter *= g.nv[k];
-        for (int k = dim + 1; k < g.dv; ++k) inner *= g.nv[k];
-        geo.outer = c->NX * vouter;
-        geo.inner = inner;
-        geo.L = g.nv[dim];
-        geo.periodic = 0;
-        geo.cls_from_inner = 0;
-        geo.cdiv = vouter;
-        geo.cmod = 1;
-    }
-    geo.fd_cdiv = make_fastdiv((unsigned)geo.cdiv);
-    geo.fd_cmod = make_fastdiv((unsigned)geo.cmod);
-    return geo;
-}
 
 template <typename T>
 int launch_rk(vp_ctx *c, int kick, int dim) {
-    SweepGeo geo = rk_geo(c, kick, dim);
+    SweepGeo geo = vp_make_geo(c, kick, dim);
     if (geo.outer >= (1LL << 32) || geo.inner >= (1LL << 32))
         return vp_fail(c, VP_ENOTSUP, "sweep geometry exceeds 32-bit line indexing");
     const LineShift<T> *tab = static_cast<const LineShift<T> *>(c->d_shift);

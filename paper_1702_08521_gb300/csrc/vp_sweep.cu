@@ -385,37 +385,6 @@ void set_attrs() {
     } while (0)
 
 // geometry of the sweep along axis `dim` (kick: velocity axis, else spatial)
-SweepGeo make_geo(const vp_ctx *c, int kick, int dim) {
-    const vp_grid &g = c->g;
-    SweepGeo geo{};
-    if (!kick) {
-        long long outer = 1, inner = c->NV, vstride = 1;
-        for (int k = 0; k < dim; ++k) outer *= g.nx[k];
-        for (int k = dim + 1; k < g.dx; ++k) inner *= g.nx[k];
-        for (int k = dim + 1; k < g.dv; ++k) vstride *= g.nv[k];
-        geo.outer = outer;
-        geo.inner = inner;
-        geo.L = g.nx[dim];
-        geo.periodic = g.xbc == VP_BC_PERIODIC;
-        geo.cls_from_inner = 1;
-        geo.cdiv = vstride;
-        geo.cmod = g.nv[dim];
-    } else {
-        long long vouter = 1, inner = 1;
-        for (int k = 0; k < dim; ++k) vouter *= g.nv[k];
-        for (int k = dim + 1; k < g.dv; ++k) inner *= g.nv[k];
-        geo.outer = c->NX * vouter;
-        geo.inner = inner;
-        geo.L = g.nv[dim];
-        geo.periodic = 0;
-        geo.cls_from_inner = 0;
-        geo.cdiv = vouter;
-        geo.cmod = 1;
-    }
-    geo.fd_cdiv = make_fastdiv((unsigned)geo.cdiv);
-    geo.fd_cmod = make_fastdiv((unsigned)geo.cmod);
-    return geo;
-}
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -584,7 +553,7 @@ SweepTune default_tune(const vp_ctx *c, const SweepGeo &geo) {
 
 template <typename T>
 int launch_sweep_t(vp_ctx *c, int kick, int dim) {
-    const SweepGeo geo = make_geo(c, kick, dim);
+    const SweepGeo geo = vp_make_geo(c, kick, dim);
     SweepTune tu = c->tune[kick][dim];
     if (!tu.valid || (c->opt_impl && geo.inner > 1 && tu.impl != c->opt_impl)) tu = default_tune<T>(c, geo);
     if (c->opt_impl == 1) tu.impl = 1;
@@ -597,7 +566,7 @@ int launch_sweep_t(vp_ctx *c, int kick, int dim) {
 // the fastest.  Runs once per (kind, axis), never inside a stream capture.
 template <typename T>
 int tune_t(vp_ctx *c, int kick, int dim) {
-    const SweepGeo geo = make_geo(c, kick, dim);
+    const SweepGeo geo = vp_make_geo(c, kick, dim);
     SweepTune best = default_tune<T>(c, geo);
     if (kick) VP_CUDA_TRY(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * c->NX, c->stream));
     int rc = vp_launch_shift_table(c, kick, dim, 0.0, kick ? c->d_acc : nullptr);
