@@ -49,21 +49,17 @@ __global__ void k_rk_table(LineShift<T> *__restrict__ tab, int nclass, int kick,
     tab[c] = sh;
 }
 
-// store of one stage: value v of row i goes to *p; with a combination, the
-// stored value is ca * a_i + cv * v (a_i: the line's f^n at the same row)
-template <typename T, bool COMBINE>
+// store of one stage: row i of the stage gets ca * a_i + cv * v (a_i: the
+// line's f^n at the same row); ca = 0, cv = 1 stores v itself
+template <typename T>
 struct StageStore {
     T *p;
     const T *a;
     long long step, astep;
     T ca, cv;
     __device__ __forceinline__ void operator()(int, T v) {
-        if (COMBINE) {
-            *p = fma(cv, v, mul_rn(ca, *a));
-            a += astep;
-        } else {
-            *p = v;
-        }
+        *p = fma(cv, v, mul_rn(ca, *a));
+        a += astep;
         p += step;
     }
 };
@@ -123,20 +119,21 @@ __global__ void __launch_bounds__(512) k_rk_cols(T *__restrict__ f, const LineSh
     const long long st = (long long)sh.sigma * W;
     const T alpha = (T)lp.alpha;
     constexpr int G = PERIODIC ? 1 : VP_GHOST;
-    if (act) {  // f^(1) = f^n - nu L(f^n)
-        StageStore<T, false> s1{b0 + cc + i0 * W, nullptr, st, 0, T(0), T(0)};
-        vp_core::walk<T, 5, PERIODIC, FULL, G>(a0 + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s1);
-    }
-    __syncthreads();
-    if (act) {  // f^(2) = 3/4 f^n + 1/4 (f^(1) - nu L(f^(1)))
-        StageStore<T, true> s2{c0p + cc + i0 * W, a0 + cc + i0 * W, st, st, T(0.75), T(0.25)};
-        vp_core::walk<T, 5, PERIODIC, FULL, G>(b0 + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s2);
-    }
-    __syncthreads();
-    if (act) {  // f^{n+1} = 1/3 f^n + 2/3 (f^(2) - nu L(f^(2)))
-        StageStore<T, true> s3{base + cc + (long long)i0 * geo.inner, a0 + cc + i0 * W,
-                               (long long)sh.sigma * geo.inner, st, T(1) / T(3), T(2) / T(3)};
-        vp_core::walk<T, 5, PERIODIC, FULL, G>(c0p + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, s3);
+    // stage k stores cv E(g) + ca f^n with E(g) = g - nu L(g) (Eq. 10):
+    // f^(1) = E(f^n) (ca = 0), f^(2) = 3/4 f^n + 1/4 E(f^(1)),
+    // f^{n+1} = 1/3 f^n + 2/3 E(f^(2)); one walker instance runs all three
+#pragma unroll 1
+    for (int stage = 0; stage < 3; ++stage) {
+        if (act) {
+            const T *src = stage == 0 ? a0 : (stage == 1 ? b0 : c0p);
+            T *dst = stage == 0 ? b0 + cc + i0 * W : (stage == 1 ? c0p + cc + i0 * W : base + cc + (long long)i0 * geo.inner);
+            const long long dstep = stage == 2 ? (long long)sh.sigma * geo.inner : st;
+            const T ca = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1) / T(3));
+            const T cv = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2) / T(3));
+            StageStore<T> sto{dst, a0 + cc + i0 * W, dstep, st, ca, cv};
+            vp_core::walk<T, 5, PERIODIC, FULL, G>(src + cc, W, L, sh, r0, r1, alpha, lp.mp, lp.pp, sto);
+        }
+        __syncthreads();
     }
 }
 
@@ -194,21 +191,19 @@ __global__ void __launch_bounds__(512) k_rk_rows(T *__restrict__ f, const LineSh
     const T alpha = (T)lp.alpha;
     const long long sg = sh.sigma;
     T *a0 = A + line * P + GP, *b0 = B + line * P + GP, *c0p = C + line * P + GP;
-    if (act) {
-        StageStore<T, false> s1{b0 + i0, nullptr, sg, 0, T(0), T(0)};
-        vp_core::walk<T, 5, false, FULL, VP_GHOST>(a0, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s1);
+    // the three stages of Eq. 10 through one walker instance (see k_rk_cols)
+#pragma unroll 1
+    for (int stage = 0; stage < 3; ++stage) {
+        if (act) {
+            const T *src = stage == 0 ? a0 : (stage == 1 ? b0 : c0p);
+            T *dst = stage == 0 ? b0 + i0 : (stage == 1 ? c0p + i0 : out + line * Q + i0);
+            const T ca = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1) / T(3));
+            const T cv = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2) / T(3));
+            StageStore<T> sto{dst, a0 + i0, sg, sg, ca, cv};
+            vp_core::walk<T, 5, false, FULL, VP_GHOST>(src, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, sto);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (act) {
-        StageStore<T, true> s2{c0p + i0, a0 + i0, sg, sg, T(0.75), T(0.25)};
-        vp_core::walk<T, 5, false, FULL, VP_GHOST>(b0, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s2);
-    }
-    __syncthreads();
-    if (act) {
-        StageStore<T, true> s3{out + line * Q + i0, a0 + i0, sg, sg, T(1) / T(3), T(2) / T(3)};
-        vp_core::walk<T, 5, false, FULL, VP_GHOST>(c0p, 1, L, sh, r0, r1, alpha, lp.mp, lp.pp, s3);
-    }
-    __syncthreads();
     if (vec) {
         for (int e = threadIdx.x * VEC; e < tot; e += blockDim.x * VEC) {
             float4 x;
