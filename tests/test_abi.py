@@ -57,3 +57,39 @@ def test_null_context_is_rejected(lib):
     assert L.vp_drift_sweep(None, 0, 0.1) == vlasov.VP_EINVAL
     assert L.vp_last_error(None) == b"null context"
     assert L.vp_num_cells(None) == 0
+
+
+def header_defines():
+    """#define VP_<NAME> <integer> of include/vlasov.h."""
+    src = open(os.path.join(ROOT, "include", "vlasov.h")).read()
+    out = {}
+    for m in re.finditer(r"^#define\s+(VP_\w+)\s+\(?(-?\d+)\)?", src, flags=re.M):
+        out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant the binding defines under a header name has the
+    header's value (error codes, schemes, boundary and initial-condition kinds)."""
+    hdr = header_defines()
+    shared = [n for n in hdr if hasattr(vlasov, n)]
+    assert len(shared) >= 20, shared
+    for n in shared:
+        assert getattr(vlasov, n) == hdr[n], n
+    for n in ("VP_ECFL", "VP_SCHEME_SL", "VP_SCHEME_RK", "VP_IC_SPHERE", "VP_NET_NPARAM"):
+        assert n in hdr and hasattr(vlasov, n), n
+
+
+def test_grid_struct_matches_the_header():
+    """The ctypes vp_grid lists the header struct's fields in order."""
+    src = open(os.path.join(ROOT, "include", "vlasov.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} vp_grid;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(None, 1)[1].split(","):
+            names.append(re.sub(r"\[.*\]", "", part).strip())
+    assert [f[0] for f in vlasov.vp_grid._fields_] == names

@@ -189,3 +189,23 @@ def test_two_dimensional_split_advection_order():
         errs = [run(n, order) for n in (16, 32, 64)]
         slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
         assert np.all(slopes >= slope), (order, errs, slopes)
+
+
+def test_oracle_grid_struct_matches_its_header():
+    """oracle.Grid lists vpo_grid's fields (oracle/vp_oracle.h) in order, and
+    the IC / boundary codes agree with the header's."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "oracle", "vp_oracle.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} vpo_grid;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [re.sub(r"\[.*\]", "", p).strip() for p in decl.split(None, 1)[1].split(",")]
+    assert [f[0] for f in O.Grid._fields_] == names
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define\s+VPO_(\w+)\s+(-?\d+)", src, flags=re.M)}
+    for n in ("IC_LANDAU", "IC_TWOSTREAM", "IC_PLUMMER", "IC_ADVECT", "IC_SPHERE", "BC_PERIODIC", "BC_OUTFLOW"):
+        assert getattr(O, n) == defs[n], n
