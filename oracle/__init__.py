@@ -116,6 +116,7 @@ def _load():
         sig = {
             "vpo_csl_flux": (D, [I, D, P]),
             "vpo_mp_constraint": (D, [D, P, D]),
+            "vpo_mp_bounds": (None, [P, D, P, P]),
             "vpo_pp_limiter": (D, [D, D, D, D]),
             "vpo_interface_flux": (D, [I, I, I, D, D, P]),
             "vpo_shift_split": (None, [D, P, P]),
@@ -180,6 +181,14 @@ def mp_constraint(phi: float, u, alpha: float = 4.0) -> float:
     """MP constraint of Appendix A; u[-3..3] with u[0] the paper's f_i."""
     u = _stencil(u)
     return _load().vpo_mp_constraint(phi, ctypes.c_void_p(u.ctypes.data + 3 * 8), alpha)
+
+
+def mp_bounds(u, alpha: float = 4.0) -> tuple:
+    """(f_min, f_max) of Appendix A steps 4-6 for the stencil u[-3..3], u[0] = f_i."""
+    u = _stencil(u)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _load().vpo_mp_bounds(ctypes.c_void_p(u.ctypes.data + 3 * 8), alpha, ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
 
 
 def pp_limiter(phibar: float, u0: float, u1: float, nu: float) -> float:

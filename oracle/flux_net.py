@@ -15,8 +15,11 @@ neighbouring velocity cells of the sweep's axis, + on the side of larger |v|):
     h2   = relu(W2 h1 + b2)      W2: 32 x 32
     h3   = relu(W3 h2 + b3)      W3: 32 x 32
     g    = w4 . h3 + b4          w4: 32
-    M    = nu * MP(Phi_CSL) + s * g   (mass through the interface; then the
-                                       PP limiter on M, update f - (M_out - M_in))
+    M    = nu * MP(Phi_CSL) + s * g   (mass through the interface)
+    M    = clamp(M, nu f_min, nu f_max)  (the MP bounds of Appendix A again,
+                                       in mass form: the corrected flux obeys them)
+    M    = PP(M)                     (Eqs. 15-23 with 2 nu Phi written as 2 M)
+    f'_i = f_{i-N} - (M_out - M_in)  (flux form, Eq. 49 with nu Phi -> M)
 Weights and every matrix input (x, h1, h2, h3) are rounded to bfloat16 as on
 the tensor cores; sums are exact here (FP64) and FP32 on the GPU.  Target of
 g at an interface: y = (M_target - nu MP(Phi_CSL)) / s.  Training loss: the
@@ -24,10 +27,17 @@ mean over cells of r^2, r = (s_r (g_r - y_r) - s_l (g_l - y_l)) / max(s_l, s_r)
 over the cell's right / left interface, i.e. the error of the cell update
 (loss_and_grad with group = 2); group = 1 gives the per-interface error.
 The backward pass treats the bfloat16 rounding as the identity.
+
+learned_line() is the whole learned SL update of one line in this form.  It
+is written in masses so that it needs no division by nu: at nu = 0 (an
+integer shift) the MP bounds in mass form have zero width, every mass is 0
+and the update is the exact shift of the line.
 """
 from __future__ import annotations
 
 import numpy as np
+
+from . import BC_PERIODIC, csl_flux, mp_bounds, mp_constraint, shift_split
 
 HIDDEN = 32
 NFEAT = 25
@@ -131,3 +141,71 @@ def loss_and_grad(p: dict, X, y, *, round_bf16: bool = True, coef=None, group: i
     grads["W1"] = dh1.T @ x0
     grads["b1"] = dh1.sum(axis=0)
     return loss, grads
+
+
+def pp_mass(M: float, u0: float, u1: float, nu: float) -> float:
+    """PP flux limiter of Sec. 2.1.1 (Eqs. 15-23) in mass form: the interface
+    carries M = nu Phi out of the upwind cell u0 into u1.  Both halves of the
+    update, u0 - 2 M and u1 + 2 M, must stay >= 0; where one would not, M is
+    blended towards the upwind mass nu u0 by theta (same reading of theta
+    under rounding as the oracle's flux-form limiter: (1 - 8 eps) when it
+    binds, clamped to [0, 1], 0 for a non-positive denominator)."""
+    u_plus, u_up_plus = u0 - 2.0 * M, u0 - 2.0 * nu * u0
+    u_minus, u_up_minus = u1 + 2.0 * M, u1 + 2.0 * nu * u0
+    th_plus = th_minus = 1.0
+    binds = False
+    if u_plus < 0.0:
+        den = u_up_plus - u_plus
+        th_plus = u_up_plus / den if den > 0.0 else 0.0
+        binds = True
+    if u_minus < 0.0:
+        den = u_up_minus - u_minus
+        th_minus = u_up_minus / den if den > 0.0 else 0.0
+        binds = True
+    th = min(th_plus, th_minus)
+    if binds:
+        th *= 1.0 - 8.0 * 2.0 ** -53
+    th = min(max(th, 0.0), 1.0)
+    return th * M + (1.0 - th) * (nu * u0)
+
+
+def learned_line(line, up_line, um_line, s: float, p: dict, bc: int = BC_PERIODIC,
+                 alpha: float = 4.0) -> np.ndarray:
+    """One learned SL update of a spatial line by a shift of s cells.
+
+    line: the line's cells; up_line / um_line: the same cells on the lines of
+    the neighbouring velocity cells (+: the side of larger |v|), zeros where
+    the velocity grid ends.  Steps, per interface of the shifted line (upwind
+    cell q, stencil u_{-3..4} in upwind order): the CSL7 flux (Sec. 2.1.2),
+    the MP constraint (Appendix A), the network correction s g, the MP bounds
+    on the total in mass form, the PP limiter in mass form; then the flux-form
+    update of every cell (Eq. 49).  Shift decomposition s = N + zeta as in the
+    plain sweep (nearest integer N, nu = |zeta|, direction sign zeta)."""
+    line = np.asarray(line, dtype=np.float64)
+    L = line.size
+    n_int, zeta = shift_split(s)
+    sg = -1 if zeta < 0 else 1
+    nu = abs(zeta)
+
+    def val(a, k):
+        if bc == BC_PERIODIC:
+            return float(a[k % L])
+        return float(a[k]) if 0 <= k < L else 0.0
+
+    def mass(q):
+        idx = [q + sg * (k - 3) for k in range(8)]
+        u = np.array([val(line, i) for i in idx])
+        up = np.array([val(up_line, i) for i in idx])
+        um = np.array([val(um_line, i) for i in idx])
+        phi = mp_constraint(csl_flux(7, nu, u[:7]), u[:7], alpha)
+        X, sc = features(u[None, :], up[None, :], um[None, :], np.array([nu]))
+        M = nu * phi + sc[0] * forward(p, X)[0][0]
+        fmin, fmax = mp_bounds(u[:7], alpha)
+        M = min(max(M, nu * fmin), nu * fmax)
+        return pp_mass(M, u[3], u[4], nu)
+
+    out = np.empty(L)
+    for i in range(L):
+        q = i - n_int
+        out[i] = val(line, q) - (mass(q) - mass(q - sg))
+    return out

@@ -132,13 +132,10 @@ double vpo_csl_flux(int order, double nu, const double *u) {
 /*
  * Interface between u[0] (the paper's f_i) and u[1] (f_{i+1}); uses
  * u[-2..2] = f_{i-2} .. f_{i+2}; phi is step 1's interpolated value.
+ * vpo_mp_bounds returns f^min and f^max of steps 4-6.
  */
-double vpo_mp_constraint(double phi, const double *u, double alpha) {
+void vpo_mp_bounds(const double *u, double alpha, double *fmin_out, double *fmax_out) {
     const double fim2 = u[-2], fim1 = u[-1], fi = u[0], fip1 = u[1], fip2 = u[2];
-    /* step 2 */
-    double fstar = fi + minmod2(fip1 - fi, alpha * (fi - fim1));
-    /* step 3 (R3: the strict "< 0" as printed) */
-    if ((phi - fi) * (phi - fstar) < 0.0) return phi;
     /* step 4: d_k = f_{k-1} + f_{k+1} - 2 f_k */
     double d_im1 = fim2 + fi - 2.0 * fim1;
     double d_i = fim1 + fip1 - 2.0 * fi;
@@ -152,10 +149,21 @@ double vpo_mp_constraint(double phi, const double *u, double alpha) {
     double f_lc = fi + (fi - fim1) / 2.0 + 4.0 * dm4_m / 3.0;
     /* step 6 */
     double a = min3(fi, fip1, f_md), b = min3(fi, f_ul, f_lc);
-    double f_min = a > b ? a : b;
+    *fmin_out = a > b ? a : b;
     a = max3(fi, fip1, f_md);
     b = max3(fi, f_ul, f_lc);
-    double f_max = a < b ? a : b;
+    *fmax_out = a < b ? a : b;
+}
+
+double vpo_mp_constraint(double phi, const double *u, double alpha) {
+    const double fim1 = u[-1], fi = u[0], fip1 = u[1];
+    /* step 2 */
+    double fstar = fi + minmod2(fip1 - fi, alpha * (fi - fim1));
+    /* step 3 (R3: the strict "< 0" as printed) */
+    if ((phi - fi) * (phi - fstar) < 0.0) return phi;
+    /* steps 4-6 */
+    double f_min, f_max;
+    vpo_mp_bounds(u, alpha, &f_min, &f_max);
     /* step 7 */
     return median3(phi, f_min, f_max);
 }

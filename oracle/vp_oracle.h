@@ -65,6 +65,8 @@ typedef struct {
  * u[0] towards u[1]; nu in [0, 1] is the fractional CFL number. */
 double vpo_csl_flux(int order, double nu, const double *u);
 double vpo_mp_constraint(double phi, const double *u, double alpha);
+/* f^min, f^max of Appendix A steps 4-6 (the bounds step 7 applies) */
+void vpo_mp_bounds(const double *u, double alpha, double *fmin_out, double *fmax_out);
 double vpo_pp_limiter(double phibar, double u0, double u1, double nu);
 double vpo_interface_flux(int order, int mp, int pp, double alpha, double nu, const double *u);
 
