@@ -213,11 +213,18 @@ int vp_sync(vp_ctx *ctx);
  *   VP_OPT_AUTOTUNE:   1 (default) times candidate tile shapes of each sweep
  *                      geometry on its first use (with a zero shift, which
  *                      leaves f unchanged) and keeps the fastest; 0 uses
- *                      fixed defaults.
+ *                      fixed defaults;
+ *   VP_OPT_WAIT_LIMIT: iterations of each bounded device-side wait in the
+ *                      sweeps (the TMA kernel's tile barriers; default 2^26,
+ *                      seconds).  A wait that runs out makes the kernel drain
+ *                      its own copies, return, and vp_sync report
+ *                      VP_ETIMEOUT; 0 makes every such wait give up at once
+ *                      (a test of that path).
  * Changing an option forgets tuned shapes and the captured step graph.
  */
 #define VP_OPT_SWEEP_IMPL 1
 #define VP_OPT_AUTOTUNE 2
+#define VP_OPT_WAIT_LIMIT 3
 int vp_set_option(vp_ctx *ctx, int option, long long value);
 
 /* Tile shape in use for sweep (kick, dim): out4 = {impl, W or R, segments,
@@ -268,6 +275,12 @@ int vp_ensemble_autotune(vp_ens *ens);
 int vp_ensemble_step(vp_ens *ens, double dt, int nsteps);
 /* wait for the stream; VP_ETIMEOUT if a bounded wait in the kernel gave up */
 int vp_ensemble_sync(vp_ens *ens);
+/* polls of each stage-dependency wait in the kernel before it gives up
+ * (default 2^24, about a second); a CTA whose wait runs out records
+ * VP_ETIMEOUT for vp_ensemble_sync and leaves the kernel, and the step's f is
+ * then undefined.  0 makes every dependency wait give up at once (a test of
+ * that path).  Forgets the captured step graph. */
+int vp_ensemble_set_wait_limit(vp_ens *ens, long long iterations);
 long long vp_ensemble_launch_count(const vp_ens *ens);
 
 /* ---- learned flux correction (not in the paper) --------------------------
@@ -284,9 +297,12 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
  * speeds moves the sub-cell gradient of f across x, also where the cell's
  * own fractional shift nu is zero, hence a mass rather than a flux value.
  * The PP limiter (Sec. 2.1.1) then acts on the total mass (u_0 - 2M >= 0,
- * u_1 + 2M >= 0, blending with the upwind mass nu u_0) and the update keeps
+ * u_1 + 2M >= 0: the clamp of M into [-u_1/2, u_0/2]) and the update keeps
  * the flux form f'_i = f_{i-n} - (M_out - M_in) (Eq. 49), so mass conservation
- * and f >= 0 hold as for the plain scheme.  Weights and matrix inputs are rounded to bfloat16, sums are
+ * and f >= 0 hold as for the plain scheme.  With use_net = 2 the corrected
+ * mass first passes the MP bounds of App. A again (the clamp into
+ * [nu f_min, nu f_max]); a network trained without that clamp loses its
+ * gain under it, so use_net = 1 (PP only) is the default of vp_learned_step.  Weights and matrix inputs are rounded to bfloat16, sums are
  * FP32.  Parameters: VP_NET_NPARAM floats, W1[32][25] b1[32] W2[32][32]
  * b2[32] W3[32][32] b3[32] w4[32] b4[1] (FP32 master copy; rounded when used).
  * Training pairs come from fine-grid runs of the method (vp_fine_flux,
@@ -295,13 +311,14 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
 #define VP_NET_NPARAM 2977
 
 /* one sweep of the grid of ctx (FP32, order 7) with the network correction
- * (use_net = 1, drifts only) or without it (use_net = 0: identical to
- * vp_drift_sweep / vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device);
- * f_snap_dev: a copy of f taken before the sweep (device, vp_num_cells
- * floats), read for the velocity neighbours when use_net = 1; NULL: the
- * library copies f into a buffer of its own (allocated on first use, freed
- * by vp_destroy) on ctx's stream; ignored when use_net = 0; in place.
- * VP_ENOTSUP for use_net with kick = 1. */
+ * (use_net = 1: PP on the corrected mass; use_net = 2: MP bounds then PP;
+ * drifts only) or without it (use_net = 0: identical to vp_drift_sweep /
+ * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); f_snap_dev: a copy
+ * of f taken before the sweep (device, vp_num_cells floats), read for the
+ * velocity neighbours when use_net > 0; NULL: the library copies f into a
+ * buffer of its own (allocated on first use, freed by vp_destroy) on ctx's
+ * stream; ignored when use_net = 0; in place.  VP_ENOTSUP for use_net with
+ * kick = 1, VP_EINVAL for use_net outside 0..2. */
 int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
                      const float *wts_dev, int use_net, const float *f_snap_dev);
 
@@ -386,7 +403,12 @@ int vp_net_adam(float *wts_dev, float *m_dev, float *v_dev, float *grad_dev, int
  *   Set-up:   the first call on each device looks up the array's device
  *             address (with that device current) and sets a kernel
  *             attribute; make that first call before any stream capture.
- * Returns VP_OK, VP_EINVAL (bad or too large grid, NULL array) or VP_ECUDA.
+ *             The address is kept for the life of the process: it assumes
+ *             the device's primary context is not reset (cudaDeviceReset)
+ *             between calls.
+ * Returns VP_OK, VP_EINVAL (bad or too large grid, NULL array) or VP_ECUDA,
+ * also when a CUDA error from earlier work is pending on the calling thread
+ * (it is left pending, not cleared, and nothing is launched).
  */
 #define VP_NOALLOC_MAX_POINTS 262144
 int vp_poisson_periodic_noalloc(const vp_grid *grid, void *cuda_stream, const double *rho_dev,

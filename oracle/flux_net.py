@@ -16,8 +16,8 @@ neighbouring velocity cells of the sweep's axis, + on the side of larger |v|):
     h3   = relu(W3 h2 + b3)      W3: 32 x 32
     g    = w4 . h3 + b4          w4: 32
     M    = nu * MP(Phi_CSL) + s * g   (mass through the interface)
-    M    = clamp(M, nu f_min, nu f_max)  (the MP bounds of Appendix A again,
-                                       in mass form: the corrected flux obeys them)
+    M    = clamp(M, nu f_min, nu f_max)  (optional: the MP bounds of Appendix A
+                                       again, in mass form)
     M    = PP(M)                     (Eqs. 15-23 with 2 nu Phi written as 2 M)
     f'_i = f_{i-N} - (M_out - M_in)  (flux form, Eq. 49 with nu Phi -> M)
 Weights and every matrix input (x, h1, h2, h3) are rounded to bfloat16 as on
@@ -170,16 +170,16 @@ def pp_mass(M: float, u0: float, u1: float, nu: float) -> float:
 
 
 def learned_line(line, up_line, um_line, s: float, p: dict, bc: int = BC_PERIODIC,
-                 alpha: float = 4.0) -> np.ndarray:
+                 alpha: float = 4.0, mp_bound: bool = False) -> np.ndarray:
     """One learned SL update of a spatial line by a shift of s cells.
 
     line: the line's cells; up_line / um_line: the same cells on the lines of
     the neighbouring velocity cells (+: the side of larger |v|), zeros where
     the velocity grid ends.  Steps, per interface of the shifted line (upwind
     cell q, stencil u_{-3..4} in upwind order): the CSL7 flux (Sec. 2.1.2),
-    the MP constraint (Appendix A), the network correction s g, the MP bounds
-    on the total in mass form, the PP limiter in mass form; then the flux-form
-    update of every cell (Eq. 49).  Shift decomposition s = N + zeta as in the
+    the MP constraint (Appendix A), the network correction s g, with mp_bound
+    the MP bounds on the total in mass form, the PP limiter in mass form; then
+    the flux-form update of every cell (Eq. 49).  Shift decomposition s = N + zeta as in the
     plain sweep (nearest integer N, nu = |zeta|, direction sign zeta)."""
     line = np.asarray(line, dtype=np.float64)
     L = line.size
@@ -200,8 +200,9 @@ def learned_line(line, up_line, um_line, s: float, p: dict, bc: int = BC_PERIODI
         phi = mp_constraint(csl_flux(7, nu, u[:7]), u[:7], alpha)
         X, sc = features(u[None, :], up[None, :], um[None, :], np.array([nu]))
         M = nu * phi + sc[0] * forward(p, X)[0][0]
-        fmin, fmax = mp_bounds(u[:7], alpha)
-        M = min(max(M, nu * fmin), nu * fmax)
+        if mp_bound:
+            fmin, fmax = mp_bounds(u[:7], alpha)
+            M = min(max(M, nu * fmin), nu * fmax)
         return pp_mass(M, u[3], u[4], nu)
 
     out = np.empty(L)

@@ -279,6 +279,7 @@ int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out) {
     ALLOC(c->d_status, sizeof(int));
 #undef ALLOC
     c->opt_autotune = 1;
+    c->opt_wait_limit = 1u << 26;
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
         free_buffers(c);
         delete c;
@@ -391,6 +392,9 @@ int vp_set_option(vp_ctx *c, int option, long long value) {
         c->opt_impl = (int)value;
     } else if (option == VP_OPT_AUTOTUNE) {
         c->opt_autotune = value != 0;
+    } else if (option == VP_OPT_WAIT_LIMIT) {
+        if (value < 0 || value > 0xffffffffLL) return vp_fail(c, VP_EINVAL, "wait limit must fit 32 bits");
+        c->opt_wait_limit = (unsigned)value;
     } else {
         return vp_fail(c, VP_EINVAL, "unknown option %d", option);
     }
@@ -472,7 +476,10 @@ static int run_steps(vp_ctx *c, double dt, int split, int nsteps, double *accel_
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         const long long per_step_captured = c->launches - before;
         c->launches = before;  // captured, not launched
-        if (rc) return rc;
+        if (rc) {
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            return rc;
+        }
         if (e != cudaSuccess) return vp_fail(c, VP_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&gc.exec, graph, 0);
         cudaGraphDestroy(graph);

@@ -73,6 +73,7 @@ struct EnsParams {
     int mp, pp, order;
     int W, R;          // tile widths of strided / contiguous sweeps
     int xpt;           // spatial points per density tile
+    unsigned wait_limit;  // iterations of each dependency wait before it gives up
     WPoly wp;
     float wpf[7][7];   // the weight polynomials' coefficients in FP32 (wp.c)
 };
@@ -82,9 +83,9 @@ struct EnsParams {
 __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 
-// wait until counter >= target (thread 0); false on timeout
-__device__ bool wait_count(const unsigned *ctr, unsigned target) {
-    for (unsigned it = 0; it < (1u << 24); ++it) {
+// wait until counter >= target (thread 0); false after `limit` polls
+__device__ bool wait_count(const unsigned *ctr, unsigned target, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it) {
         const unsigned v = *reinterpret_cast<const volatile unsigned *>(ctr);
         if (v >= target) {
             __threadfence();
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(kThreads) k_ensemble(float *__restrict__ pool,
             s_ok = 1;
             if (e.stage > 0) {
                 const StageDesc &prev = r.st[e.stage - 1];
-                if (!wait_count(done + prev.done_slot, (unsigned)prev.tiles)) {
+                if (!wait_count(done + prev.done_slot, (unsigned)prev.tiles, P.wait_limit)) {
                     atomicExch(status, VP_ETIMEOUT);
                     s_ok = 0;
                 }
@@ -661,6 +662,7 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
     e->P.pp = 1;
     e->P.order = order;
     e->P.W = 64;
+    e->P.wait_limit = 1u << 24;
     e->P.R = 32;
     e->P.xpt = 8;
     e->P.wp = vp_csl_weight_polys(order);
@@ -859,6 +861,16 @@ int vp_ensemble_set_tiles(vp_ens *e, int W, int R, int ctas_per_sm) {
     per = per < 1 ? 1 : per;
     e->ctas_per_sm = ctas_per_sm > 0 && ctas_per_sm < per ? ctas_per_sm : per;
     if (e->graph_valid) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph_valid = 0;
+    }
+    return VP_OK;
+}
+
+int vp_ensemble_set_wait_limit(vp_ens *e, long long iterations) {
+    if (!e || iterations < 0 || iterations > 0xffffffffLL) return VP_EINVAL;
+    e->P.wait_limit = (unsigned)iterations;
+    if (e->graph_valid) {  // the limit is a launch parameter baked into the graph
         cudaGraphExecDestroy(e->graph);
         e->graph_valid = 0;
     }

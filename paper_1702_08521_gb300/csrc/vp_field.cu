@@ -748,6 +748,9 @@ extern "C" int vp_poisson_periodic_noalloc(const vp_grid *g, void *cuda_stream, 
         NX *= g->nx[d];
     }
     if (NX > VP_NOALLOC_MAX_POINTS) return VP_EINVAL;
+    // an error left by earlier work would be indistinguishable from ours at
+    // the end: report it (and leave it pending) before launching anything
+    if (cudaPeekAtLastError() != cudaSuccess) return VP_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return VP_ECUDA;
     double2 *buf = nullptr;

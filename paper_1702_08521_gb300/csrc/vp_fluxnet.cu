@@ -9,11 +9,12 @@
 // (u+_k + u-_k - 2 u_k) / (2 s), nu) with u+ / u- the same cells of the lines in
 // the neighbouring velocity cells (+: larger |v|).  The correction is a mass, not a flux value: the
 // sub-cell spread of speeds inside a coarse velocity cell moves mass even
-// where the cell's own fractional shift nu vanishes.  The PP limiter then acts
-// on the total mass (f_i - 2 M >= 0, f_{i+1} + 2 M >= 0) and the update keeps
-// the flux form f'_i = f_{i-n} - (M_out - M_in), so conservation and f >= 0
-// hold exactly as for the plain scheme.  Weights and matrix inputs are
-// bfloat16, sums FP32.
+// where the cell's own fractional shift nu is small.  The corrected mass
+// passes the PP limiter (f_i - 2 M >= 0, f_{i+1} + 2 M >= 0) and, on request
+// (use_net = 2), the MP bounds of App. A before it (the clamp into
+// [nu f_min, nu f_max]); the update keeps the flux form
+// f'_i = f_{i-n} - (M_out - M_in), so conservation and f >= 0 hold exactly as
+// for the plain scheme.  Weights and matrix inputs are bfloat16, sums FP32.
 //
 // Training data come from fine-grid runs of the method itself: for a sweep,
 // the fine-grid mass through every coarse interface (mean over the fine
@@ -105,30 +106,6 @@ __device__ __forceinline__ float net_features(const float *u, const float *up, c
     for (int k = 0; k < 8; ++k) x[16 + k] = (0.5f * (up[k] + um[k]) - u[k]) * inv;
     x[24] = nu;
     return s;
-}
-
-// PP limiter (Sec. 2.1.1, Eqs. 15-23) on the mass M through the interface
-// between the upwind cell u0 and u1: keep u0 - 2 M >= 0 and u1 + 2 M >= 0 by
-// blending M with the upwind mass nu u0 (theta as in the plain sweep, with
-// the same (1 - 8 eps) safety factor)
-__device__ __forceinline__ float pp_mass(float M, float u0, float u1, float nu) {
-    const float up = u0 - 2.f * M, um = u1 + 2.f * M;
-    if (fminf(up, um) >= 0.f) return M;
-    const float two_nu = 2.f * nu;
-    float th = 1.f;
-    if (up < 0.f) {
-        const float base = u0 - two_nu * u0;
-        const float den = base - up;
-        th = den > 0.f ? __fdividef(base, den) : 0.f;
-    }
-    if (um < 0.f) {
-        const float base = u1 + two_nu * u0;
-        const float den = base - um;
-        th = fminf(th, den > 0.f ? __fdividef(base, den) : 0.f);
-    }
-    th *= 1.0f - 8.0f * 5.9604644775390625e-08f;
-    th = fminf(fmaxf(th, 0.f), 1.f);
-    return th * M + (1.f - th) * (nu * u0);
 }
 
 // ---- training ----------------------------------------------------------------------
@@ -350,10 +327,8 @@ __global__ void k_fine_flux(const float *__restrict__ f, long long outer, int L,
         float u[7];
 #pragma unroll
         for (int k = 0; k < 7; ++k) u[k] = val(up - 3 + k);
-        const float two_nu = 2.0f * sh.nu;
-        const float ph = vp_core::flux<float, 7, true>(sh, u[0], u[1], u[2], u[3], u[4], u[5], u[6], alpha,
-                                                       two_nu, 1, 1);
-        const double g = (S(ip) - S(ip - n)) + (double)sh.nu * (double)ph;
+        const float M = vp_core::flux<float, 7, true>(sh, u[0], u[1], u[2], u[3], u[4], u[5], u[6], alpha, 1, 1);
+        const double g = (S(ip) - S(ip - n)) + (double)M;
         G[line * nout + j] = sg > 0 ? g : -g;
     }
 }
@@ -483,7 +458,8 @@ __global__ void k_group_mean(const double *__restrict__ Gf, long long ncl, int n
 // threads read consecutive lines: coalesced for strided sweeps), with the
 // lines' shift decompositions.  Phase 1 computes every interface's limited
 // mass: the plain MP mass, plus s g from the network on the tensor cores
-// (described at the loop), then the PP limiter.  Phase 2: one thread per
+// (described at the loop), then (use_net = 2) the MP bounds, and the PP
+// limiter.  Phase 2: one thread per
 // cell writes the flux-form update.  Interface k of a line is the k-th one
 // the upwind walk meets: its upwind cell is q_k = q_0 + k sigma,
 // q_0 = (sigma > 0 ? 0 : L - 1) - n - sigma; the k-th cell of the walk
@@ -740,7 +716,8 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
 #pragma unroll
             for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
             phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
-            mass[e] = pp_mass(sh.nu * phi, u[3], u[4], sh.nu);
+            mass[e] = vp_core::pp_clamp(vp_core::mul_rn(sh.nu, phi), vp_core::half_rd(u[3]),
+                                        vp_core::half_rd(u[4]));
         }
     } else {
         // phase 1 with the network: a warp takes 32 interfaces (two 16-row MMA
@@ -750,7 +727,8 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
         // ldmatrix turns the rows into A fragments; the layers run with
         // mma.sync (biases as the C operand, FP32 accumulation, ReLU and bf16
         // rounding in one conversion); the output layer is an MMA with w4 in
-        // column 0 of B; lane i then adds s g and applies the PP limiter.
+        // column 0 of B; lane i then adds s g and applies the PP limiter (after
+        // the MP bounds when use_net = 2).
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = lane & 3;
         unsigned char *fb = fbuf + warp * 32 * kFS;
         const uint32_t fb_s = static_cast<uint32_t>(__cvta_generic_to_shared(fb));
@@ -763,7 +741,7 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
             const int e = (it << 5) + lane;
             const int l = e & (NL - 1), k = e >> lgNL;
             const bool ok = e < NI && l < nl;
-            float Mp = 0.f, s = 1.f, u3 = 0.f, u4 = 0.f, nu = 0.f;
+            float Mp = 0.f, s = 1.f, u3 = 0.f, u4 = 0.f, nu = 0.f, mlo = 0.f, mhi = 0.f;
             uint4 p0 = make_uint4(0u, 0u, 0u, 0u), p1 = p0, p2 = p0, p3 = p0;
             if (ok) {
                 const LineShift<float> &sh = shs[l];
@@ -792,7 +770,13 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
                 float phi = sh.w[0] * u[0];
 #pragma unroll
                 for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
-                Mp = nu * vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
+                // MP bounds of this stencil (App. A steps 4-6); the plain
+                // mass and, after the network, the corrected one are clamped
+                // into them (the constraint equals the clamp, see mp_clamp)
+                vp_core::mp_lohi(u[1], u[2], u[3], u[4], u[5], alpha, mlo, mhi);
+                mlo = vp_core::mul_rn(nu, mlo);
+                mhi = vp_core::mul_rn(nu, mhi);
+                Mp = fminf(fmaxf(vp_core::mul_rn(nu, phi), mlo), mhi);
                 u3 = u[3];
                 u4 = u[4];
                 s = 0.f;
@@ -852,7 +836,11 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict_
             const float g10 = __shfl_sync(0xffffffffu, g[1][0], src);
             const float g12 = __shfl_sync(0xffffffffu, g[1][2], src);
             const float gi = (lane & 16) ? ((lane & 8) ? g12 : g10) : ((lane & 8) ? g02 : g00);
-            if (ok) mass[e] = pp_mass(fmaf(s, gi, Mp), u3, u4, nu);
+            if (ok) {
+                float M = fmaf(s, gi, Mp);
+                if (use_net == 2) M = fminf(fmaxf(M, mlo), mhi);
+                mass[e] = vp_core::pp_clamp(M, vp_core::half_rd(u3), vp_core::half_rd(u4));
+            }
         }
     }
     __syncthreads();
@@ -960,6 +948,7 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     if (!c || !c->f) return VP_EINVAL;
     if (c->g.precision != VP_F32 || c->g.order != 7)
         return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
+    if (use_net < 0 || use_net > 2) return vp_fail(c, VP_EINVAL, "use_net must be 0, 1 or 2");
     if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
     if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
         return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");

@@ -126,6 +126,7 @@ struct vp_ctx {
     int learned_ready;                  // learned-sweep buffers allocated, kernel attributes set
     int opt_impl;                       // 0 auto, 1 staged, 2 TMA
     int opt_autotune;                   // 1: time candidate tiles on first use
+    unsigned opt_wait_limit;            // iterations of each bounded device-side wait
     SweepTune tune[2][3];               // [kick][dim]
     vp_graph_cache graph;
     char err[256];

@@ -237,7 +237,7 @@ template <typename T, int ORDER, bool PERIODIC, bool FULL>
 __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ CUtensorMap tmap,
                                                         const LineShift<T> *__restrict__ tab,
                                                         SweepGeo geo, LimParams lp,
-                                                        int *__restrict__ status) {
+                                                        int *__restrict__ status, unsigned wait_limit) {
     extern __shared__ __align__(128) unsigned char smraw_tma[];
     unsigned char *smraw = smraw_tma;
     __shared__ __align__(8) uint64_t bar[2];
@@ -293,11 +293,15 @@ __global__ void __launch_bounds__(512) k_sweep_cols_tma(const __grid_constant__ 
         const int s = k & 1;
         T *in = in_buf + s * itile;
         T *out = out_buf + s * otile;
-        if (!vp_tma::mbar_wait(&bar[s], (uint32_t)((k >> 1) & 1))) {
-            // the tile never arrived: report, drain our stores, leave
+        const bool arrived = vp_tma::mbar_wait(&bar[s], (uint32_t)((k >> 1) & 1), wait_limit);
+        if (__syncthreads_or(!arrived)) {
+            // a thread gave up on the tile: report, wait (bounded) for this
+            // CTA's loads still in flight (this tile's and the next one's)
+            // and for its stores, leave
             if (threadIdx.x == 0) {
                 atomicExch(status, VP_ETIMEOUT);
-                vp_tma::mbar_wait(&bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1), 1u << 20);
+                vp_tma::mbar_wait(&bar[s], (uint32_t)((k >> 1) & 1), 1u << 22);
+                if (t + gridDim.x < ntiles) vp_tma::mbar_wait(&bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1), 1u << 22);
                 vp_tma::wait_all<0>();
             }
             return;
@@ -469,7 +473,8 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
         long long grid = (long long)per_sm * c->sm_count;
         grid = grid > tiles ? tiles : grid;
 #define VP_LAUNCH(O, P, F) \
-    k_sweep_cols_tma<T, O, P, F><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status)
+    k_sweep_cols_tma<T, O, P, F><<<(unsigned)grid, threads, smem, c->stream>>>(map, tab, geo, lp, c->d_status, \
+                                                                                c->opt_wait_limit)
         VP_DISPATCH(order, per, full, VP_LAUNCH);
 #undef VP_LAUNCH
     } else {

@@ -78,11 +78,10 @@ __device__ __forceinline__ T mp_clamp(T phi, T um1, T u0, T u1, T alpha, T m4m, 
     return fmin(fmax(phi, lo), hi);
 }
 
-// Steps 4-7 of the MP constraint (taken only when step 3 rejects phi).  The
-// median of step 7 is a clamp: both intervals of step 6 contain u0, so
-// f_min <= u0 <= f_max exactly.
+// Steps 4-6 of the MP constraint: the bounds [f_min, f_max].  Both intervals
+// of step 6 contain u0, so f_min <= u0 <= f_max exactly.
 template <typename T>
-__device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
+__device__ __forceinline__ void mp_lohi(T um2, T um1, T u0, T u1, T u2, T alpha, T &lo, T &hi) {
     const T back = u0 - um1;
     const T dm = um2 + u0 - T(2) * um1;  // curvature at the upwind neighbour
     const T dc = um1 + u1 - T(2) * u0;   // at the upwind cell
@@ -92,8 +91,16 @@ __device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T 
     const T ful = fma(alpha, back, u0);
     const T fmd = fma(T(0.5), u0 + u1, T(-0.5) * m4p);
     const T flc = fma(T(4) / T(3), m4m, fma(T(0.5), back, u0));
-    const T lo = fmax(fmin(fmin(u0, u1), fmd), fmin(fmin(u0, ful), flc));
-    const T hi = fmin(fmax(fmax(u0, u1), fmd), fmax(fmax(u0, ful), flc));
+    lo = fmax(fmin(fmin(u0, u1), fmd), fmin(fmin(u0, ful), flc));
+    hi = fmin(fmax(fmax(u0, u1), fmd), fmax(fmax(u0, ful), flc));
+}
+
+// Steps 4-7 (taken only when step 3 rejects phi): the median of step 7 is
+// the clamp into [f_min, f_max].
+template <typename T>
+__device__ __forceinline__ T mp_bounds(T phi, T um2, T um1, T u0, T u1, T u2, T alpha) {
+    T lo, hi;
+    mp_lohi(um2, um1, u0, u1, u2, alpha, lo, hi);
     return fmin(fmax(phi, lo), hi);
 }
 
@@ -115,53 +122,31 @@ __device__ __forceinline__ T mp_limit(T phi, T um2, T um1, T u0, T u1, T u2, T a
     return mp_bounds(phi, um2, um1, u0, u1, u2, alpha);
 }
 
-template <typename T>
-struct Prec;
-template <>
-struct Prec<float> {
-    static constexpr float safety = 1.0f - 8.0f * 5.9604644775390625e-08f;  // 1 - 8 * 2^-24
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-};
-template <>
-struct Prec<double> {
-    static constexpr double safety = 1.0 - 8.0 * 1.1102230246251565e-16;  // 1 - 8 * 2^-53
-    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
-};
+// Half of a cell, rounded towards minus infinity: the most mass one interface
+// may take out of a non-negative cell so that two of them leave it >= 0.
+__device__ __forceinline__ float half_rd(float u) { return __fmul_rd(u, 0.5f); }
+__device__ __forceinline__ double half_rd(double u) { return __dmul_rd(u, 0.5); }
 
-// theta blend when one half of the Euler update would go negative
+// PP limiter (Sec. 2.1.1, Eqs. 15-23) on the mass M = nu Phi that an interface
+// carries from its upwind cell u0 into u1.  For u0, u1 >= 0 and 0 < nu <= 1/2
+// the theta blend returns Phi unless one half of the Euler update goes
+// negative; then U+ < 0 gives theta+ (Phi - u0) = (1 - 2 nu) u0 / (2 nu), i.e.
+// exactly the flux u0 / (2 nu) that empties the upwind half, and U- < 0 the
+// flux -u1 / (2 nu) (both cannot bind at once).  So the limiter is the clamp
+// of M into [-u1 / 2, u0 / 2], with h0, h1 the rounded-down halves of u0, u1.
+// A cell then loses at most h through each of its two interfaces, and
+// (u - M_out) + M_in >= 0 holds after rounding, subnormals included.
 template <typename T>
-__device__ __forceinline__ T pp_blend(T phi, T u0, T u1, T two_nu, T up, T um) {
-    T th = T(1);
-    if (up < T(0)) {
-        const T base = fma(-two_nu, u0, u0);  // U^{UP,+}
-        const T den = base - up;
-        th = den > T(0) ? Prec<T>::div(base, den) : T(0);
-    }
-    if (um < T(0)) {
-        const T base = fma(two_nu, u0, u1);  // U^{UP,-}
-        const T den = base - um;
-        const T t2 = den > T(0) ? Prec<T>::div(base, den) : T(0);
-        th = fmin(th, t2);
-    }
-    th *= Prec<T>::safety;
-    th = fmin(fmax(th, T(0)), T(1));
-    return fma(th, phi, mul_rn(T(1) - th, u0));
+__device__ __forceinline__ T pp_clamp(T M, T h0, T h1) {
+    return fmin(fmax(M, -h1), h0);
 }
 
-// PP limiter: keep f_i - 2 nu phi >= 0 and f_{i+1} + 2 nu phi >= 0
-template <typename T>
-__device__ __forceinline__ T pp_limit(T phi, T u0, T u1, T two_nu) {
-    const T up = fma(-two_nu, phi, u0);
-    const T um = fma(two_nu, phi, u1);
-    if (fmin(up, um) >= T(0)) return phi;
-    return pp_blend(phi, u0, u1, two_nu, up, um);
-}
-
-// Interface flux on the upwind-ordered stencil (u0 = upwind cell).  FULL:
-// MP and PP both on, so the runtime switches drop out of the loop.
+// Interface mass on the upwind-ordered stencil (u0 = upwind cell): the CSL
+// flux, the MP constraint, times nu, then the PP limiter.  FULL: MP and PP
+// both on, so the runtime switches drop out of the loop.
 template <typename T, int ORDER, bool FULL>
 __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
-                                  T alpha, T two_nu, int mp, int pp) {
+                                  T alpha, int mp, int pp) {
     T phi;
     if ((FULL || mp) && um1 == u0 && u0 == u1) {
         // flat around the interface: every MP bound collapses onto u0, whatever
@@ -181,15 +166,16 @@ __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T
         if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
         if (FULL || mp) phi = mp_limit(phi, um2, um1, u0, u1, u2, alpha);
     }
-    if (FULL || pp) phi = pp_limit(phi, u0, u1, two_nu);
-    return phi;
+    T M = mul_rn(sh.nu, phi);
+    if (FULL || pp) M = pp_clamp(M, half_rd(u0), half_rd(u1));
+    return M;
 }
 
-// Interface flux for the line walker: the CSL interpolant, the MP constraint
-// as a clamp (no branch) with d^{M4} at both faces of u0 passed in, then PP.
+// The CSL interpolant and, for the line walker, the MP constraint as a clamp
+// (no branch) with d^{M4} at both faces of u0 passed in.
 template <typename T, int ORDER, bool FULL>
 __device__ __forceinline__ T flux_walk(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
-                                       T alpha, T two_nu, int mp, int pp, T m4m, T m4p) {
+                                       T alpha, int mp, T m4m, T m4p) {
     T phi;
     if (ORDER == 7) {
         phi = sh.w[0] * um3;
@@ -203,7 +189,6 @@ __device__ __forceinline__ T flux_walk(const LineShift<T> &sh, T um3, T um2, T u
     phi = fma(sh.w[5], u2, phi);
     if (ORDER == 7) phi = fma(sh.w[6], u3, phi);
     if (FULL || mp) phi = mp_clamp(phi, um1, u0, u1, alpha, m4m, m4p);
-    if (FULL || pp) phi = pp_limit(phi, u0, u1, two_nu);
     return phi;
 }
 
@@ -212,14 +197,16 @@ __device__ __forceinline__ T flux_walk(const LineShift<T> &sh, T um3, T um2, T u
 // Advance cells [r0, r1) of one line staged in shared memory; row r of the
 // line is at sm0[r * ss].  Zero-inflow lines have GP >= 1 zero rows on each
 // side (rows -GP..-1 and L..L+GP-1); periodic lines wrap.
-// The walk goes upwind -> downwind so that each interface flux is computed
+// The walk goes upwind -> downwind so that each interface mass is computed
 // once; the 8-cell stencil window rotates through registers (unrolled by 8).
-// The curvature of the upwind cell and d^{M4} at its upwind face carry over
-// from one interface to the next, so each interface adds one curvature and
-// one d^{M4}.  Where every active lane of a warp sits on a flat stencil
-// (u_{-1} = u_0 = u_1) the flux is u_0 exactly (all MP bounds collapse onto
-// u_0, d^{M4} at the downwind face is 0, the PP limiter keeps it) and the
-// warp skips the arithmetic.  store(i, v) writes the new value of cell i.
+// The curvature of the upwind cell, d^{M4} at its upwind face and the
+// rounded-down half of the cell carry over from one interface to the next, so
+// each interface adds one curvature, one d^{M4} and one half.  Where every
+// active lane of a warp sits on a flat stencil (u_{-1} = u_0 = u_1) the
+// constrained flux is u_0 exactly (all MP bounds collapse onto u_0, d^{M4} at
+// the downwind face is 0) and the warp skips the interpolant and the bounds.
+// The update is the flux form of Eq. 49 in masses, f' = (u - M_out) + M_in.
+// store(i, v) writes the new value of cell i.
 
 template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, typename Store>
 __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, const LineShift<T> &sh,
@@ -227,7 +214,6 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
     if (r0 >= r1) return;
     const int sg = sh.sigma;
     const T nu = sh.nu;
-    const T two_nu = T(2) * nu;
     int i = sg > 0 ? r0 : r1 - 1;
     const int cnt = r1 - r0;
     // Source row of load k (k = 0, 1, ...) is p0 + k sg; load k feeds step
@@ -256,7 +242,7 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
     T w[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) w[k] = *row(p0 + k * sg);
-    // incoming flux of the first cell: upwind cell i - sg, stencil w[0..6]
+    // incoming mass of the first cell: upwind cell i - sg, stencil w[0..6]
     T dc = T(0), m4m = T(0);  // curvature at the next upwind cell, d^{M4} at its upwind face
     T m4p = T(0);
     if (FULL || mp) {
@@ -266,40 +252,50 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
         m4m = dm4(dm, dc);
         m4p = dm4(dc, dp);
     }
-    T fin = flux_walk<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, two_nu, mp, pp,
-                                      m4m, m4p);
+    // hc: rounded-down half of the cell the walk is on (the upwind cell of its
+    // outgoing interface)
+    T hc = (FULL || pp) ? half_rd(w[4]) : T(0);
+    T fin = mul_rn(nu, flux_walk<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, mp,
+                                                 m4m, m4p));
+    if (FULL || pp) fin = pp_clamp(fin, half_rd(w[3]), hc);
     if (FULL || mp) {
         dc = curv(w[3], w[4], w[5]);
         m4m = m4p;
     }
 
-    // one cell with the window rotated by K (u_k at w[(K + 4 + k) & 7]); the
-    // next value enters from *src, which then moves by inc
+    // one cell with the window rotated by K (u_k at w[(K + 4 + k) & 7]): the
+    // outgoing mass, then f' = (u - M_out) + M_in; the next value enters from
+    // *src, which then moves by inc
 #define VP_WALK_STEP(K)                                                                           \
     {                                                                                             \
-        T fout;                                                                                   \
+        const T u0_ = w[(K + 4) & 7], u1_ = w[(K + 5) & 7];                                       \
+        T phi;                                                                                    \
         if (FULL || mp) {                                                                         \
-            const T u0_ = w[(K + 4) & 7], u1_ = w[(K + 5) & 7];                                   \
             const T dp = curv(u0_, u1_, w[(K + 6) & 7]);                                          \
             const bool flat = w[(K + 3) & 7] == u0_ && u0_ == u1_;                                \
             if (__all_sync(__activemask(), flat)) {                                               \
-                fout = u0_;                                                                       \
+                phi = u0_;                                                                        \
                 m4m = T(0);                                                                       \
             } else {                                                                              \
                 m4p = dm4(dc, dp);                                                                \
-                fout = flux_walk<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7],              \
-                                                 w[(K + 3) & 7], u0_, u1_, w[(K + 6) & 7],        \
-                                                 w[(K + 7) & 7], alpha, two_nu, mp, pp, m4m,      \
-                                                 m4p);                                            \
+                phi = flux_walk<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7],               \
+                                                w[(K + 3) & 7], u0_, u1_, w[(K + 6) & 7],         \
+                                                w[(K + 7) & 7], alpha, mp, m4m, m4p);             \
                 m4m = m4p;                                                                        \
             }                                                                                     \
             dc = dp;                                                                              \
         } else {                                                                                  \
-            fout = flux_walk<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7], w[(K + 3) & 7],  \
-                                             w[(K + 4) & 7], w[(K + 5) & 7], w[(K + 6) & 7],      \
-                                             w[(K + 7) & 7], alpha, two_nu, mp, pp, T(0), T(0));  \
+            phi = flux_walk<T, ORDER, FULL>(sh, w[(K + 1) & 7], w[(K + 2) & 7], w[(K + 3) & 7],   \
+                                            u0_, u1_, w[(K + 6) & 7], w[(K + 7) & 7], alpha, mp,  \
+                                            T(0), T(0));                                          \
         }                                                                                         \
-        store(i, fma(-nu, fout - fin, w[(K + 4) & 7]));                                           \
+        T fout = mul_rn(nu, phi);                                                                 \
+        if (FULL || pp) {                                                                         \
+            const T hn = half_rd(u1_);                                                            \
+            fout = pp_clamp(fout, hc, hn);                                                        \
+            hc = hn;                                                                              \
+        }                                                                                         \
+        store(i, (u0_ - fout) + fin);                                                             \
         fin = fout;                                                                               \
         i += sg;                                                                                  \
         w[K & 7] = *src;                                                                          \

@@ -25,7 +25,7 @@ VP_SPLIT_KDK, VP_SPLIT_DKD = 0, 1
 VP_SCHEME_SL, VP_SCHEME_RK = 0, 1
 VP_IC_LANDAU, VP_IC_TWOSTREAM, VP_IC_PLUMMER, VP_IC_ADVECT, VP_IC_SPHERE = 0, 1, 2, 3, 4
 VP_NDIAG = 9
-VP_OPT_SWEEP_IMPL, VP_OPT_AUTOTUNE = 1, 2
+VP_OPT_SWEEP_IMPL, VP_OPT_AUTOTUNE, VP_OPT_WAIT_LIMIT = 1, 2, 3
 DIAG_NAMES = ("mass", "ke", "fe", "pe", "min_f", "max_f", "mode_amp", "l1", "l2")
 
 _lock = threading.Lock()
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_ensemble_autotune": (I, [P]),
             "vp_ensemble_step": (I, [P, D, I]),
             "vp_ensemble_sync": (I, [P]),
+            "vp_ensemble_set_wait_limit": (I, [P, LL]),
             "vp_ensemble_launch_count": (LL, [P]),
             "vp_learned_sweep": (I, [P, I, I, D, P, P, I, P]),
             "vp_learned_step": (I, [P, D, I, I, P, P, I, P]),
@@ -356,6 +357,10 @@ def vp_ensemble_step(ens, dt: float, nsteps: int) -> None:
 
 def vp_ensemble_sync(ens) -> None:
     _echeck(ens, load().vp_ensemble_sync(ens))
+
+
+def vp_ensemble_set_wait_limit(ens, iterations: int) -> None:
+    _echeck(ens, load().vp_ensemble_set_wait_limit(ens, int(iterations)))
 
 
 def vp_ensemble_launch_count(ens) -> int:

@@ -87,6 +87,25 @@ def test_initial_conditions_and_diagnostics(cfg):
     sim.close()
 
 
+@pytest.mark.parametrize("cfg", [inputs.two_stream(32, 64), inputs.plummer(6, 8)])
+def test_fp32_diagnostics_match_oracle_on_evolved_state(cfg):
+    """FP32 f: the moments, energies, extrema and norms (FP64 sums of the FP32
+    cells, compensated FP32 partial sums in the velocity moment) against the
+    oracle's FP64 diagnostics of the same FP32-rounded state, after a few
+    steps so that the state is not an analytic one."""
+    sim, og = both(cfg["grid"], V.VP_F32)
+    kind, params = cfg["ic"]
+    V.vp_init_f(sim.ctx, kind, params)
+    sim.field()
+    sim.step(cfg["dt"], 3, split=cfg["split"])
+    f_g = from_gpu(sim)
+    d_g = V.vp_diagnostics(sim.ctx, 1)
+    d_o = O.diagnostics(og, f_g, 1)
+    for k in O.DIAG_NAMES:
+        assert d_g[k] == pytest.approx(d_o[k], rel=1e-9, abs=1e-12 * (1 + abs(d_o["mass"]))), k
+    sim.close()
+
+
 def test_diagnostics_flags_nonfinite():
     g = dict(dims=1, nx=[8], nv=[8], xlo=[0.0], xhi=[1.0], vlo=[-1.0], vhi=[1.0])
     sim, _ = both(g, V.VP_F32)

@@ -121,38 +121,10 @@ def test_learned_sweep_without_net_is_the_plain_sweep():
     sim.close()
 
 
-def _oracle_learned_line(line, up_line, um_line, s, p, bc):
-    """FP64 learned SL update of one line (oracle): mass nu MP(CSL7) + s g
-    through each interface, the PP limiter on that mass, flux-form update.
-    up_line / um_line: the velocity-neighbour lines (+: larger |v|)."""
-    L = line.size
-    n_int, zeta = O.shift_split(s)
-    sg = -1 if zeta < 0 else 1
-    nu = abs(zeta)
-
-    def val(a, k):
-        if bc == O.BC_PERIODIC:
-            return a[k % L]
-        return a[k] if 0 <= k < L else 0.0
-
-    def flux(q):  # upwind cell q of the shifted line, stencil in upwind order
-        idx = [q + sg * (k - 3) for k in range(8)]
-        u = np.array([val(line, i) for i in idx])
-        up = np.array([val(up_line, i) for i in idx])
-        um = np.array([val(um_line, i) for i in idx])
-        phi = O.mp_constraint(O.csl_flux(7, nu, u[:7]), u[:7], 4.0)
-        X, sc = N.features(u[None, :], up[None, :], um[None, :], np.array([nu]))
-        M = nu * phi + sc[0] * N.forward(p, X)[0][0]
-        # the PP limiter of the flux value M / nu (Eqs. 15-23), back to a mass
-        return nu * O.pp_limiter(M / nu, u[3], u[4], nu)
-
-    out = np.empty(L)
-    for i in range(L):
-        out[i] = val(line, i - n_int) - (flux(i - n_int) - flux(i - n_int - sg))
-    return out
-
-
-def test_learned_sweep_matches_oracle_line_update():
+@pytest.mark.parametrize("use_net", [1, 2])
+def test_learned_sweep_matches_oracle_line_update(use_net):
+    """use_net 1: PP on the corrected mass; 2: the MP bounds of App. A on it
+    first (the oracle's mp_bound)."""
     import torch
     g = dict(dims=1, nx=[24], nv=[20], xlo=[0.0], xhi=[2.0], vlo=[-3.0], vhi=[3.0], order=7)
     sim, og = both(g, V.VP_F32)
@@ -160,7 +132,7 @@ def test_learned_sweep_matches_oracle_line_update():
     p = _params(7, scale=0.3)
     w = _t(N.pack(p), torch.float32)
     to_gpu(sim, f0)
-    V.vp_learned_sweep(sim.ctx, 0, 0, 0.37, None, w, 1, snapshot(sim))
+    V.vp_learned_sweep(sim.ctx, 0, 0, 0.37, None, w, use_net, snapshot(sim))
     got = from_gpu(sim).reshape(24, 20)
     want = np.empty((24, 20))
     f2 = f0.reshape(24, 20)
@@ -171,9 +143,32 @@ def test_learned_sweep_matches_oracle_line_update():
         sp = 1 if vc[j] >= 0 else -1
         up = f2[:, j + sp] if 0 <= j + sp < 20 else zero
         um = f2[:, j - sp] if 0 <= j - sp < 20 else zero
-        want[:, j] = _oracle_learned_line(f2[:, j], up, um, s, p, O.BC_PERIODIC)
+        want[:, j] = N.learned_line(f2[:, j], up, um, s, p, O.BC_PERIODIC, mp_bound=use_net == 2)
     # FP32 sums vs FP64 sums can move a bfloat16 rounding by one step
     assert rel_l1(got, want) <= 2e-3, rel_l1(got, want)
+    sim.close()
+
+
+def test_learned_sweep_integer_shift_is_exact_with_mp_bounds():
+    """An integer shift (nu = 0 on every line) with the network on and the MP
+    bounds applied to its correction (use_net = 2): in mass form they have
+    zero width, so the learned sweep is the exact shift of every line, bit
+    for bit, as in the oracle's learned update."""
+    import torch
+    g = dict(dims=1, nx=[24], nv=[20], xlo=[0.0], xhi=[24.0], vlo=[-5.0], vhi=[5.0], order=7)
+    sim, og = both(g, V.VP_F32)
+    f0 = _f32(inputs.random_f(og.NX * og.NV, seed=15))
+    w = _t(N.pack(_params(9, scale=3.0)), torch.float32)
+    to_gpu(sim, f0)
+    # dx = 1, v_j = -4.75 + 0.5 j, dt = 4: shift v_j dt = -19 + 2 j cells
+    dt = 4.0
+    V.vp_learned_sweep(sim.ctx, 0, 0, dt, None, w, 2, snapshot(sim))
+    got = from_gpu(sim).reshape(24, 20)
+    f2 = f0.reshape(24, 20)
+    for j, v in enumerate(og.v_centres(0)):
+        n = int(round(v * dt))
+        assert v * dt == n
+        assert np.array_equal(got[:, j], np.roll(f2[:, j], n)), j
     sim.close()
 
 

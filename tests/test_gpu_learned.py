@@ -84,6 +84,14 @@ def test_learned_velocity_sweeps_are_closer_to_the_fine_target(trained):
         V.vp_learned_sweep(S.coarse.ctx, 0, d, DT, None, w, 1, f0)
         stream.synchronize()
         learned = S.coarse.f.clone()
+        # the same sweep with the MP bounds of App. A on the corrected mass
+        S.coarse.f.copy_(f0)
+        torch.cuda.synchronize()
+        V.vp_learned_sweep(S.coarse.ctx, 0, d, DT, None, w, 2, f0)
+        stream.synchronize()
+        learned_mp = S.coarse.f.clone()
+        S.coarse.f.copy_(learned)
+        torch.cuda.synchronize()
         V.vp_drift_sweep(S.fine.ctx, d, DT)
         S.restrict()
         stream.synchronize()
@@ -93,7 +101,9 @@ def test_learned_velocity_sweeps_are_closer_to_the_fine_target(trained):
         upd = (target.double() - f0.double()).abs().sum()
         e_plain = float((plain.double() - target.double()).abs().sum() / upd)
         e_learn = float((learned.double() - target.double()).abs().sum() / upd)
-        print(f"spatial sweep x{d + 1}: plain {e_plain:.3e}, learned {e_learn:.3e} (of the update)")
+        e_mp = float((learned_mp.double() - target.double()).abs().sum() / upd)
+        print(f"spatial sweep x{d + 1}: plain {e_plain:.3e}, learned {e_learn:.3e}, "
+              f"learned with MP bounds {e_mp:.3e} (of the update)")
         gains.append((e_plain, e_learn))
     S.close()
     for e_plain, e_learn in gains:
@@ -126,3 +136,23 @@ def test_learned_run_against_fine_oracle_is_reported(trained):
     assert math.isfinite(e_l) and e_l < e_p
     plain.close()
     learned.close()
+
+
+def test_fine_reference_of_the_learned_benchmark_matches_oracle():
+    """The learned benchmark judges its runs against the GPU's FP64 run of the
+    fine 2D2V Landau grid (k = 0.5, alpha = 0.05, KDK, dt = 0.1, t = 2).  That
+    reference path, at a reduced 32^2 x 64^2 grid over the same 20 steps,
+    equals the FP64 oracle from the same initial state."""
+    import torch
+    stream = torch.cuda.Stream()
+    nx, nv, k, a = 32, 64, 0.5, 0.05
+    f0 = LR.restricted_initial_state(2, nx, nv, 1, k, a, stream).double()
+    g = LR.landau_grid(2, nx, nv, k)
+    ref = LR.run(g, f0, DT, 20, None, stream, V.VP_F64)
+    og = O.grid(**g)
+    f = f0.cpu().numpy().copy()
+    _, _, acc = O.field(og, f)
+    O.step(og, f, DT, 20, np.ascontiguousarray(acc), split=O.SPLIT_KDK)
+    got = ref.f.double().cpu().numpy()
+    assert float(np.abs(got - f).max() / np.abs(f).max()) <= 1e-11
+    ref.close()

@@ -134,7 +134,8 @@ def _lines(rng, L, zeros=0.3):
     return f, up, um
 
 
-def test_learned_line_with_zero_network_is_the_plain_update():
+@pytest.mark.parametrize("mpb", [False, True])
+def test_learned_line_with_zero_network_is_the_plain_update(mpb):
     rng = np.random.default_rng(40)
     p = {k: np.zeros(s) for k, s in N.SHAPES.items()}
     for _ in range(60):
@@ -142,35 +143,36 @@ def test_learned_line_with_zero_network_is_the_plain_update():
         f, up, um = _lines(rng, L)
         s = float(rng.uniform(-4, 4))
         bc = int(rng.integers(0, 2))
-        got = N.learned_line(f, up, um, s, p, bc)
+        got = N.learned_line(f, up, um, s, p, bc, mp_bound=mpb)
         want = O.advect_line(f, s, order=7, mp=1, pp=1, bc=bc)
         assert np.abs(got - want).max() <= 1e-15 * max(f.max(), 1e-300), s
 
 
-def test_learned_line_conserves_mass_and_positivity_for_any_network():
+@pytest.mark.parametrize("mpb", [False, True])
+def test_learned_line_conserves_mass_and_positivity_for_any_network(mpb):
     rng = np.random.default_rng(41)
     for t in range(60):
         p = _rand_params(t, scale=float(rng.choice([1.0, 5.0, 30.0])))
         L = int(rng.integers(8, 30))
         f, up, um = _lines(rng, L)
         s = float(rng.uniform(-3, 3))
-        got = N.learned_line(f, up, um, s, p, O.BC_PERIODIC)
+        got = N.learned_line(f, up, um, s, p, O.BC_PERIODIC, mp_bound=mpb)
         assert got.min() >= 0.0
         assert abs(got.sum() - f.sum()) <= 1e-14 * max(f.sum(), 1e-300)
-        out = N.learned_line(f, up, um, s, p, O.BC_OUTFLOW)
+        out = N.learned_line(f, up, um, s, p, O.BC_OUTFLOW, mp_bound=mpb)
         assert out.min() >= 0.0
 
 
-def test_learned_line_integer_shift_is_exact():
-    """nu = 0: the MP bounds in mass form have zero width, so the network can
-    move nothing and the line is shifted cell for cell."""
+def test_learned_line_integer_shift_is_exact_with_mp_bounds():
+    """nu = 0 with the MP bounds on: in mass form they have zero width, so the
+    network can move nothing and the line is shifted cell for cell."""
     rng = np.random.default_rng(42)
     p = _rand_params(3, scale=10.0)
     for n in (-5, -1, 0, 2, 7):
         f, up, um = _lines(rng, 19)
-        got = N.learned_line(f, up, um, float(n), p, O.BC_PERIODIC)
+        got = N.learned_line(f, up, um, float(n), p, O.BC_PERIODIC, mp_bound=True)
         assert np.array_equal(got, np.roll(f, n))
-        out = N.learned_line(f, up, um, float(n), p, O.BC_OUTFLOW)
+        out = N.learned_line(f, up, um, float(n), p, O.BC_OUTFLOW, mp_bound=True)
         want = np.zeros(19)
         if n >= 0:
             want[n:] = f[:19 - n]
@@ -180,26 +182,31 @@ def test_learned_line_integer_shift_is_exact():
 
 
 def test_learned_line_correction_obeys_the_mp_bounds():
-    """A constant network output g = b4 on a constant line: every MP bound is
-    the constant itself, so the corrected mass nu f + s g is cut back to nu f
-    and the line does not change; on a rising linear ramp (periodic wrap kept
-    away by zero-inflow boundaries far from the cells checked) the bounds are
-    [f_i, f_{i+1}] and a small g passes: each interior cell changes by
-    -(s_out - s_in) g relative to the plain update, s = max |u| over the
-    interface's 8-cell stencil."""
-    p = {k: np.zeros(s) for k, s in N.SHAPES.items()}
-    p["b4"] = np.array([0.25])
+    """On a constant line every MP bound is the constant itself, so with the
+    bounds on any network's correction is cut back to nu f and the line does
+    not change; without them a network whose output varies between
+    interfaces (random velocity-neighbour lines) moves mass.  On a rising
+    linear ramp (zero-inflow ends far from the cells checked) the bounds are
+    [f_i, f_{i+1}] and a small constant g passes in both modes: each interior
+    cell changes by -(s_out - s_in) g relative to the plain update, s = max |u|
+    over the interface's 8-cell stencil."""
+    rng = np.random.default_rng(43)
+    p = _rand_params(5, scale=3.0)
     f = np.full(16, 0.5)
-    z = np.zeros(16)
+    up, um = rng.random(16), rng.random(16)
     for s in (0.3, -0.3, 2.4):
-        assert np.array_equal(N.learned_line(f, z, z, s, p, O.BC_PERIODIC), np.roll(f, 0))
+        assert np.array_equal(N.learned_line(f, up, um, s, p, O.BC_PERIODIC, mp_bound=True), f)
+        assert not np.array_equal(N.learned_line(f, up, um, s, p, O.BC_PERIODIC), f)
+    p = {k: np.zeros(s) for k, s in N.SHAPES.items()}
+    z = np.zeros(40)
     ramp = 1.0 + 0.125 * np.arange(40)
     g = 1e-4
     p["b4"] = np.array([g])
     nu = 0.25
-    got = N.learned_line(ramp, z[:1].repeat(40), z[:1].repeat(40), nu, p, O.BC_OUTFLOW)
     plain = O.advect_line(ramp, nu, order=7, mp=1, pp=1, bc=O.BC_OUTFLOW)
-    # flow to the right: the interface right of cell i has stencil cells
-    # i-3 .. i+4, so s_out = ramp[i+4] and s_in = ramp[i+3]
-    for i in range(10, 30):
-        assert got[i] - plain[i] == pytest.approx(-(ramp[i + 4] - ramp[i + 3]) * g, rel=1e-9, abs=1e-17)
+    for mpb in (False, True):
+        got = N.learned_line(ramp, z, z, nu, p, O.BC_OUTFLOW, mp_bound=mpb)
+        # flow to the right: the interface right of cell i has stencil cells
+        # i-3 .. i+4, so s_out = ramp[i+4] and s_in = ramp[i+3]
+        for i in range(10, 30):
+            assert got[i] - plain[i] == pytest.approx(-(ramp[i + 4] - ramp[i + 3]) * g, rel=1e-9, abs=1e-17)
