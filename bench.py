@@ -53,8 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sweep-reps", type=int, default=3)
-    p.add_argument("--sweep-impl", type=int, default=0, choices=[0, 1, 2],
-                   help="0 auto, 1 staged-load kernels, 2 TMA pipeline")
+    p.add_argument("--sweep-impl", type=int, default=0, choices=[0, 1, 2, 3],
+                   help="0 auto, 1 staged-load kernels, 2 TMA pipeline, 3 two lines per thread")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--no-learned", action="store_true")

@@ -209,7 +209,10 @@ int vp_sync(vp_ctx *ctx);
 /*
  * vp_set_option -- implementation choices (no effect on results):
  *   VP_OPT_SWEEP_IMPL: 0 automatic, 1 staged-load kernels only, 2 prefer the
- *                      TMA-pipelined strided-axis kernel;
+ *                      TMA-pipelined strided-axis kernel, 3 prefer the
+ *                      staged-load strided kernel that walks two lines per
+ *                      thread with packed FP32 pair arithmetic (FP32 grids;
+ *                      the same bits as 1);
  *   VP_OPT_AUTOTUNE:   1 (default) times candidate tile shapes of each sweep
  *                      geometry on its first use (with a zero shift, which
  *                      leaves f unchanged) and keeps the fastest; 0 uses

@@ -388,7 +388,7 @@ int vp_poisson_solve(vp_ctx *c, const double *rho_dev, double *phi_dev, double *
 int vp_set_option(vp_ctx *c, int option, long long value) {
     if (!c) return VP_EINVAL;
     if (option == VP_OPT_SWEEP_IMPL) {
-        if (value < 0 || value > 2) return vp_fail(c, VP_EINVAL, "sweep implementation must be 0, 1 or 2");
+        if (value < 0 || value > 3) return vp_fail(c, VP_EINVAL, "sweep implementation must be 0 .. 3");
         c->opt_impl = (int)value;
     } else if (option == VP_OPT_AUTOTUNE) {
         c->opt_autotune = value != 0;

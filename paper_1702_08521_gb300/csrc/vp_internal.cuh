@@ -61,7 +61,7 @@ struct SweepGeo {
     int W, nseg, R;
     // divisors of the launch: cdiv, cmod, tiles per outer index, W (or R),
     // nseg, L, 16-byte pieces per tile row
-    FastDiv fd_cdiv, fd_cmod, fd_tpo, fd_w, fd_nseg, fd_l, fd_wv;
+    FastDiv fd_cdiv, fd_cmod, fd_tpo, fd_w, fd_nseg, fd_l, fd_wv, fd_w2;
     unsigned tpo;
 };
 
@@ -72,7 +72,8 @@ struct SweepGeo {
 // tile configuration of one sweep geometry (chosen by the autotuner)
 struct SweepTune {
     int valid;
-    int impl;   // 1: staged loads (k_sweep_cols / k_sweep_rows), 2: TMA pipeline
+    int impl;   // 1: staged loads (k_sweep_cols / k_sweep_rows), 2: TMA pipeline,
+                // 3: staged loads with two lines per thread (FP32 strided sweeps)
     int W, nseg, ctas_per_sm;
 };
 

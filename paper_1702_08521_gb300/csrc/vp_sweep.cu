@@ -46,9 +46,18 @@ struct PtrStore {
 
 // staged-load strided sweep: tile = W columns x the whole line, staged as
 // rows GP..GP+L-1 of a [(L + 2 GP)][W] shared tile; zero-inflow lines get GP =
-// VP_GHOST zero rows on each side, periodic lines none
-template <typename T, int ORDER, bool PERIODIC, bool FULL>
-__global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
+// VP_GHOST zero rows on each side, periodic lines none.  PAIR (FP32 only): a
+// thread walks two adjacent columns at once with the packed pair arithmetic
+// (W / 2 threads per segment row); a pair whose lines differ in their integer
+// shift or direction is walked one line after the other.
+// largest CTA of the two-line kernels and the CTAs per SM their register
+// budget must allow
+#define VP_PAIR_THREADS 512
+#define VP_PAIR_MINB 1
+
+template <typename T, int ORDER, bool PERIODIC, bool FULL, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? VP_PAIR_THREADS : 512, PAIR ? VP_PAIR_MINB : 1)
+    k_sweep_cols(T *__restrict__ f,
                                                     const LineShift<T> *__restrict__ tab,
                                                     SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -96,24 +105,59 @@ __global__ void __launch_bounds__(512) k_sweep_cols(T *__restrict__ f,
         }
     }
     __syncthreads();
-    const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
-    const int cc = (int)(threadIdx.x - seg * (unsigned)W);
-    if (cc < wc && (int)seg < geo.nseg) {
-        const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
+    constexpr int G1 = PERIODIC ? 1 : VP_GHOST;
+    if constexpr (PAIR) {
+        const unsigned seg = fdiv(threadIdx.x, geo.fd_w2);
+        const int cc = 2 * (int)(threadIdx.x - seg * (unsigned)(W >> 1));
+        if (cc >= wc || (int)seg >= geo.nseg) return;
         const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
         const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
-        const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
-        PtrStore<T> st{base + cc + (long long)i0 * geo.inner, (long long)sh.sigma * geo.inner};
-        walk<T, ORDER, PERIODIC, FULL, PERIODIC ? 1 : VP_GHOST>(data + cc, W, L, sh, r0, r1, (T)lp.alpha,
-                                                                 lp.mp, lp.pp, st);
+        const LineShift<float> sa = tab[line_class(geo, o, c0 + cc)];
+        if (cc + 1 < wc) {
+            const LineShift<float> sb = tab[line_class(geo, o, c0 + cc + 1)];
+            if (sa.n == sb.n && sa.sigma == sb.sigma) {
+                const vp_core::LineShiftP2 sh = vp_core::pair_shift(sa, sb);
+                const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+                PtrStore<vp_core::P2> st{reinterpret_cast<vp_core::P2 *>(base + cc + (long long)i0 * geo.inner),
+                                         (long long)sh.sigma * (geo.inner >> 1)};
+                walk<vp_core::P2, ORDER, PERIODIC, FULL, G1>(reinterpret_cast<const vp_core::P2 *>(data + cc),
+                                                             W >> 1, L, sh, r0, r1, vp_core::P2((float)lp.alpha),
+                                                             lp.mp, lp.pp, st);
+                return;
+            }
+            const int i1 = sb.sigma > 0 ? r0 : r1 - 1;
+            PtrStore<T> st{base + cc + 1 + (long long)i1 * geo.inner, (long long)sb.sigma * geo.inner};
+            walk<T, ORDER, PERIODIC, FULL, G1>(data + cc + 1, W, L, sb, r0, r1, (T)lp.alpha, lp.mp, lp.pp, st);
+        }
+        const int i0 = sa.sigma > 0 ? r0 : r1 - 1;
+        PtrStore<T> st{base + cc + (long long)i0 * geo.inner, (long long)sa.sigma * geo.inner};
+        walk<T, ORDER, PERIODIC, FULL, G1>(data + cc, W, L, sa, r0, r1, (T)lp.alpha, lp.mp, lp.pp, st);
+    } else {
+        const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
+        const int cc = (int)(threadIdx.x - seg * (unsigned)W);
+        if (cc < wc && (int)seg < geo.nseg) {
+            const LineShift<T> sh = tab[line_class(geo, o, c0 + cc)];
+            const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+            const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
+            const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+            PtrStore<T> st{base + cc + (long long)i0 * geo.inner, (long long)sh.sigma * geo.inner};
+            walk<T, ORDER, PERIODIC, FULL, G1>(data + cc, W, L, sh, r0, r1, (T)lp.alpha, lp.mp, lp.pp, st);
+        }
     }
 }
 
 // contiguous-axis sweep: R lines per CTA.  Input rows at odd pitch P with a
 // zero ghost on each side, results to a second shared tile (odd pitch Q), then
-// copied out with 16-byte coalesced stores.
-template <typename T, int ORDER, bool PERIODIC, bool FULL>
-__global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
+// copied out with 16-byte coalesced stores.  PAIR (FP32 only): lines 2q and
+// 2q + 1 are interleaved element by element in shared memory (pair pitch 2P,
+// 2Q) so that one thread walks both with 8-byte loads and stores and the
+// packed pair arithmetic; a pair whose lines differ in their integer shift or
+// direction, and the odd last line of a ragged tile, are walked one line at
+// a time (element stride 2).  The 16-lane phases of 8-byte accesses stay
+// conflict-free because P is odd.
+template <typename T, int ORDER, bool PERIODIC, bool FULL, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? VP_PAIR_THREADS : 512, PAIR ? VP_PAIR_MINB : 1)
+    k_sweep_rows(T *__restrict__ f,
                                                     const LineShift<T> *__restrict__ tab,
                                                     SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -127,12 +171,17 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
     const int nl = (int)((geo.outer - l0) < R ? (geo.outer - l0) : R);
     T *base = f + l0 * L;
     const int tot = nl * L;
+    // shared-memory index of cell pos of line r in the input / output tile
+    auto iidx = [&](int r, int pos) -> int {
+        return PAIR ? (r >> 1) * (2 * P) + 2 * (GP + pos) + (r & 1) : r * P + GP + pos;
+    };
+    auto oidx = [&](int r, int pos) -> int { return PAIR ? (r >> 1) * (2 * Q) + 2 * pos + (r & 1) : r * Q + pos; };
     if (GP > 0) {
         constexpr int G = GP > 0 ? GP : 1;
         for (int e = threadIdx.x; e < nl * G; e += blockDim.x) {
             const int r = e / G, k = e - r * G;
-            in[r * P + k] = T(0);
-            in[r * P + G + L + k] = T(0);
+            in[iidx(r, k - G)] = T(0);
+            in[iidx(r, L + k)] = T(0);
         }
     }
     constexpr int VEC = 16 / sizeof(T);
@@ -152,8 +201,9 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const T *xv = reinterpret_cast<const T *>(&x[u]);
+                const int i0 = iidx(r, pos);
 #pragma unroll
-                for (int k = 0; k < VEC; ++k) in[r * P + GP + pos + k] = xv[k];
+                for (int k = 0; k < VEC; ++k) in[i0 + (PAIR ? 2 * k : k)] = xv[k];
                 r += dr;
                 pos += dp;
                 if (pos >= L) {
@@ -165,8 +215,9 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         for (; e < tot; e += st) {
             const float4 x = *reinterpret_cast<const float4 *>(base + e);
             const T *xv = reinterpret_cast<const T *>(&x);
+            const int i0 = iidx(r, pos);
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) in[r * P + GP + pos + k] = xv[k];
+            for (int k = 0; k < VEC; ++k) in[i0 + (PAIR ? 2 * k : k)] = xv[k];
             r += dr;
             pos += dp;
             if (pos >= L) {
@@ -178,7 +229,7 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         const int dr = (int)fdiv(blockDim.x, geo.fd_l), dp = blockDim.x - dr * L;
         int r = (int)fdiv(threadIdx.x, geo.fd_l), pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            in[r * P + GP + pos] = base[e];
+            in[iidx(r, pos)] = base[e];
             r += dr;
             pos += dp;
             if (pos >= L) {
@@ -188,16 +239,51 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         }
     }
     __syncthreads();
-    const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
-    const int line = (int)(threadIdx.x - seg * (unsigned)R);
-    if (line < nl && (int)seg < geo.nseg) {
-        const LineShift<T> sh = tab[line_class(geo, (unsigned)(l0 + line), 0u)];
-        const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
-        const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
-        const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
-        PtrStore<T> st{out + line * Q + i0, (long long)sh.sigma};
-        walk<T, ORDER, PERIODIC, FULL, PERIODIC ? 1 : VP_GHOST>(in + line * P + GP, 1, L, sh, r0, r1,
-                                                                 (T)lp.alpha, lp.mp, lp.pp, st);
+    constexpr int G1 = PERIODIC ? 1 : VP_GHOST;
+    if constexpr (PAIR) {
+        const unsigned seg = fdiv(threadIdx.x, geo.fd_w2);
+        const int line = 2 * (int)(threadIdx.x - seg * (unsigned)(R >> 1));
+        if (line < nl && (int)seg < geo.nseg) {
+            const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+            const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
+            const LineShift<float> sa = tab[line_class(geo, (unsigned)(l0 + line), 0u)];
+            bool paired = false;
+            if (line + 1 < nl) {
+                const LineShift<float> sb = tab[line_class(geo, (unsigned)(l0 + line + 1), 0u)];
+                if (sa.n == sb.n && sa.sigma == sb.sigma) {
+                    const vp_core::LineShiftP2 sh = vp_core::pair_shift(sa, sb);
+                    const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+                    PtrStore<vp_core::P2> st{reinterpret_cast<vp_core::P2 *>(out + oidx(line, i0)), sh.sigma};
+                    walk<vp_core::P2, ORDER, PERIODIC, FULL, G1>(
+                        reinterpret_cast<const vp_core::P2 *>(in + iidx(line, 0)), 1, L, sh, r0, r1,
+                        vp_core::P2((float)lp.alpha), lp.mp, lp.pp, st);
+                    paired = true;
+                } else {
+                    const int i1 = sb.sigma > 0 ? r0 : r1 - 1;
+                    PtrStore<T> st{out + oidx(line + 1, i1), 2LL * sb.sigma};
+                    walk<T, ORDER, PERIODIC, FULL, G1>(in + iidx(line + 1, 0), 2, L, sb, r0, r1, (T)lp.alpha,
+                                                       lp.mp, lp.pp, st);
+                }
+            }
+            if (!paired) {
+                const int i0 = sa.sigma > 0 ? r0 : r1 - 1;
+                PtrStore<T> st{out + oidx(line, i0), 2LL * sa.sigma};
+                walk<T, ORDER, PERIODIC, FULL, G1>(in + iidx(line, 0), 2, L, sa, r0, r1, (T)lp.alpha, lp.mp,
+                                                   lp.pp, st);
+            }
+        }
+    } else {
+        const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
+        const int line = (int)(threadIdx.x - seg * (unsigned)R);
+        if (line < nl && (int)seg < geo.nseg) {
+            const LineShift<T> sh = tab[line_class(geo, (unsigned)(l0 + line), 0u)];
+            const int r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+            const int r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
+            const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+            PtrStore<T> st{out + line * Q + i0, (long long)sh.sigma};
+            walk<T, ORDER, PERIODIC, FULL, G1>(in + line * P + GP, 1, L, sh, r0, r1, (T)lp.alpha, lp.mp, lp.pp,
+                                               st);
+        }
     }
     __syncthreads();
     if (vec) {
@@ -207,8 +293,9 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         for (int e = threadIdx.x * VEC; e < tot; e += st) {
             float4 x;
             T *xv = reinterpret_cast<T *>(&x);
+            const int o0 = oidx(r, pos);
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) xv[k] = out[r * Q + pos + k];
+            for (int k = 0; k < VEC; ++k) xv[k] = out[o0 + (PAIR ? 2 * k : k)];
             *reinterpret_cast<float4 *>(base + e) = x;
             r += dr;
             pos += dp;
@@ -221,7 +308,7 @@ __global__ void __launch_bounds__(512) k_sweep_rows(T *__restrict__ f,
         const int dr = (int)fdiv(blockDim.x, geo.fd_l), dp = blockDim.x - dr * L;
         int r = (int)fdiv(threadIdx.x, geo.fd_l), pos = threadIdx.x - r * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            base[e] = out[r * Q + pos];
+            base[e] = out[oidx(r, pos)];
             r += dr;
             pos += dp;
             if (pos >= L) {
@@ -349,10 +436,16 @@ __global__ void k_shift_table(LineShift<T> *__restrict__ tab, int nclass, int ki
 
 template <typename T, int ORDER, bool PER, bool FULL>
 void set_attrs_one() {
-    cudaFuncSetAttribute(k_sweep_cols<T, ORDER, PER, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sweep_cols<T, ORDER, PER, FULL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    cudaFuncSetAttribute(k_sweep_rows<T, ORDER, PER, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if constexpr (sizeof(T) == 4)
+        cudaFuncSetAttribute(k_sweep_cols<T, ORDER, PER, FULL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    cudaFuncSetAttribute(k_sweep_rows<T, ORDER, PER, FULL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    if constexpr (sizeof(T) == 4)
+        cudaFuncSetAttribute(k_sweep_rows<T, ORDER, PER, FULL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
     cudaFuncSetAttribute(k_sweep_cols_tma<T, ORDER, PER, FULL>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -424,6 +517,13 @@ bool tma_eligible(const vp_ctx *c, const SweepGeo &geo, int W) {
            (reinterpret_cast<uintptr_t>(c->f) & 15) == 0;
 }
 
+// the pair walker: FP32, even columns per tile and row stride (8-byte pairs)
+template <typename T>
+bool pair_eligible(const vp_ctx *c, const SweepGeo &geo, int W) {
+    return sizeof(T) == 4 && geo.inner > 1 && geo.inner % 2 == 0 && W % 2 == 0 &&
+           (reinterpret_cast<uintptr_t>(c->f) & 7) == 0;
+}
+
 // line classes and tile coordinates are computed in 32-bit arithmetic
 inline bool geo_fits_32(const SweepGeo &geo) { return geo.outer < (1LL << 32) && geo.inner < (1LL << 32); }
 
@@ -436,15 +536,20 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     const int L = geo.L;
     int W = tu.W;
     if (geo.inner < W) W = (int)geo.inner;
+    const bool pair = tu.impl == 3 && pair_eligible<T>(c, geo, W);
+    // walkers per segment row: W lines, or W / 2 line pairs; at most 512 threads
+    const int per_row = pair ? W >> 1 : W;
+    int nseg = tu.nseg;
+    while (nseg > 1 && per_row * nseg > (pair ? VP_PAIR_THREADS : 512)) nseg >>= 1;
     geo.W = W;
-    geo.nseg = tu.nseg;
-    const int threads = ((W * tu.nseg + 31) / 32) * 32;
+    geo.nseg = nseg;
+    const int threads = ((per_row * nseg + 31) / 32) * 32;
     const long long tiles = geo.outer * ((geo.inner + W - 1) / W);
     if (tiles >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
     geo.tpo = (unsigned)((geo.inner + W - 1) / W);
     geo.fd_tpo = make_fastdiv(geo.tpo);
     geo.fd_w = make_fastdiv((unsigned)W);
-    geo.fd_nseg = make_fastdiv((unsigned)tu.nseg);
+    geo.fd_nseg = make_fastdiv((unsigned)nseg);
     geo.fd_wv = make_fastdiv((unsigned)(W / (16 / sizeof(T)) > 0 ? W / (16 / sizeof(T)) : 1));
     const int order = c->g.order;
     const bool per = geo.periodic != 0;
@@ -477,10 +582,20 @@ int launch_cols(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
                                                                                 c->opt_wait_limit)
         VP_DISPATCH(order, per, full, VP_LAUNCH);
 #undef VP_LAUNCH
+    } else if (pair) {
+        const size_t smem = (size_t)(L + 2 * ghost_rows(geo)) * W * sizeof(T);
+        if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
+        const int pthreads = threads;
+        geo.fd_w2 = make_fastdiv((unsigned)(W >> 1));
+#define VP_LAUNCH(O, P, F) \
+    k_sweep_cols<T, O, P, F, sizeof(T) == 4><<<(unsigned)tiles, pthreads, smem, c->stream>>>(f, tab, geo, lp)
+        VP_DISPATCH(order, per, full, VP_LAUNCH);
+#undef VP_LAUNCH
     } else {
         const size_t smem = (size_t)(L + 2 * ghost_rows(geo)) * W * sizeof(T);
         if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
-#define VP_LAUNCH(O, P, F) k_sweep_cols<T, O, P, F><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp)
+#define VP_LAUNCH(O, P, F) \
+    k_sweep_cols<T, O, P, F, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp)
         VP_DISPATCH(order, per, full, VP_LAUNCH);
 #undef VP_LAUNCH
     }
@@ -503,21 +618,37 @@ int launch_rows(vp_ctx *c, SweepGeo geo, const SweepTune &tu) {
     const int L = geo.L;
     int R = tu.W;
     if (geo.outer < R) R = (int)geo.outer;
+    const bool pair = tu.impl == 3 && sizeof(T) == 4;
+    if (pair && (R & 1)) ++R;  // a single ragged tile keeps an empty slot
+    // walkers per segment row: R lines, or R / 2 line pairs; at most 512 threads
+    const int per_row = pair ? R >> 1 : R;
+    int nseg = tu.nseg;
+    while (nseg > 1 && per_row * nseg > (pair ? VP_PAIR_THREADS : 512)) nseg >>= 1;
     geo.R = R;
-    geo.nseg = tu.nseg;
+    geo.nseg = nseg;
     geo.fd_w = make_fastdiv((unsigned)R);
-    geo.fd_nseg = make_fastdiv((unsigned)tu.nseg);
+    geo.fd_nseg = make_fastdiv((unsigned)nseg);
     geo.fd_l = make_fastdiv((unsigned)L);
     const long long blocks = (geo.outer + R - 1) / R;
     if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "sweep has too many tiles");
     const size_t smem = rows_smem<T>(L, R, ghost_rows(geo));
     if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line of %d cells too long to stage", L);
-    const int threads = ((R * tu.nseg + 31) / 32) * 32;
+    const int threads = ((per_row * nseg + 31) / 32) * 32;
     const bool per = geo.periodic != 0;
     const bool full = c->g.mp && c->g.pp;
-#define VP_LAUNCH(O, P, F) k_sweep_rows<T, O, P, F><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp)
-    VP_DISPATCH(c->g.order, per, full, VP_LAUNCH);
+    if (pair) {
+        geo.fd_w2 = make_fastdiv((unsigned)(R >> 1));
+        const int pthreads = threads;
+#define VP_LAUNCH(O, P, F) \
+    k_sweep_rows<T, O, P, F, sizeof(T) == 4><<<(unsigned)blocks, pthreads, smem, c->stream>>>(f, tab, geo, lp)
+        VP_DISPATCH(c->g.order, per, full, VP_LAUNCH);
 #undef VP_LAUNCH
+    } else {
+#define VP_LAUNCH(O, P, F) \
+    k_sweep_rows<T, O, P, F, false><<<(unsigned)blocks, threads, smem, c->stream>>>(f, tab, geo, lp)
+        VP_DISPATCH(c->g.order, per, full, VP_LAUNCH);
+#undef VP_LAUNCH
+    }
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
@@ -540,8 +671,9 @@ SweepTune default_tune(const vp_ctx *c, const SweepGeo &geo) {
         nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
         tu.W = W;
         tu.nseg = nseg;
-        const int want = c->opt_impl ? c->opt_impl : 2;
-        tu.impl = (want == 2 && tma_eligible<T>(c, geo, W < geo.inner ? W : (int)geo.inner)) ? 2 : 1;
+        const int want = c->opt_impl ? c->opt_impl : 3;
+        const int Weff = W < geo.inner ? W : (int)geo.inner;
+        tu.impl = (want == 2 && tma_eligible<T>(c, geo, Weff)) ? 2 : (want == 3 && pair_eligible<T>(c, geo, Weff)) ? 3 : 1;
     } else {
         int R = 4096 / L;
         R = R < 32 ? 32 : (R > 128 ? 128 : R);
@@ -551,7 +683,8 @@ SweepTune default_tune(const vp_ctx *c, const SweepGeo &geo) {
         nseg = nseg > maxseg ? maxseg : (nseg < 1 ? 1 : nseg);
         tu.W = R;
         tu.nseg = nseg;
-        tu.impl = 1;
+        const int want = c->opt_impl ? c->opt_impl : 3;
+        tu.impl = want == 3 && sizeof(T) == 4 && R % 2 == 0 ? 3 : 1;
     }
     return tu;
 }
@@ -560,7 +693,7 @@ template <typename T>
 int launch_sweep_t(vp_ctx *c, int kick, int dim) {
     const SweepGeo geo = vp_make_geo(c, kick, dim);
     SweepTune tu = c->tune[kick][dim];
-    if (!tu.valid || (c->opt_impl && geo.inner > 1 && tu.impl != c->opt_impl)) tu = default_tune<T>(c, geo);
+    if (!tu.valid || (c->opt_impl && tu.impl != c->opt_impl)) tu = default_tune<T>(c, geo);
     if (c->opt_impl == 1) tu.impl = 1;
     if (geo.inner > 1) return launch_cols<T>(c, geo, tu);
     return launch_rows<T>(c, geo, tu);
@@ -580,18 +713,21 @@ int tune_t(vp_ctx *c, int kick, int dim) {
     SweepTune cand[kMaxCand];
     int nc = 0;
     if (geo.inner > 1) {
-        const int impls[2] = {2, 1};
+        const int impls[3] = {3, 2, 1};
         // lines too long for a 32-column tile take 4-16 columns and more segments
         const bool longl = (size_t)(geo.L + 2 * ghost_rows(geo)) * 32 * sizeof(T) > 200 * 1024;
-        for (int ii = 0; ii < 2; ++ii) {
+        for (int ii = 0; ii < 3; ++ii) {
             if (c->opt_impl && impls[ii] != c->opt_impl) continue;
             for (int W = longl ? 4 : 32; W <= (longl ? 16 : 128); W *= 2)
                 for (int nseg = 1; nseg <= (longl ? 64 : 8); nseg *= 2) {
-                    const int th = W * nseg;
-                    if (th < 64 || th > 512 || nseg > geo.L || (longl && nseg * 8 > geo.L)) continue;
+                    const int th = (impls[ii] == 3 ? W / 2 : W) * nseg;
+                    if (th < (impls[ii] == 3 ? 32 : 64) || th > (impls[ii] == 3 ? VP_PAIR_THREADS : 512) ||
+                        nseg > geo.L || (longl && nseg * 8 > geo.L))
+                        continue;
                     const int Weff = geo.inner < W ? (int)geo.inner : W;
                     if (impls[ii] == 2 && !tma_eligible<T>(c, geo, Weff)) continue;
-                    if (impls[ii] == 1 && (size_t)(geo.L + 2 * ghost_rows(geo)) * W * sizeof(T) > 200 * 1024)
+                    if (impls[ii] == 3 && !pair_eligible<T>(c, geo, Weff)) continue;
+                    if (impls[ii] != 2 && (size_t)(geo.L + 2 * ghost_rows(geo)) * W * sizeof(T) > 200 * 1024)
                         continue;
                     if (nc < kMaxCand) cand[nc++] = SweepTune{1, impls[ii], W, nseg, 0};
                 }
@@ -599,13 +735,18 @@ int tune_t(vp_ctx *c, int kick, int dim) {
     } else {
         // long lines take fewer lines per CTA (the staged tile must fit) and
         // more segments per line (segments of at least 8 cells)
-        for (int R = 8; R <= 128; R *= 2)
-            for (int nseg = 1; nseg <= 64; nseg *= 2) {
-                const int th = R * nseg;
-                if (th < 64 || th > 512 || nseg * 8 > geo.L) continue;
-                if (rows_smem<T>(geo.L, R, ghost_rows(geo)) > 200 * 1024) continue;
-                if (nc < kMaxCand) cand[nc++] = SweepTune{1, 1, R, nseg, 0};
-            }
+        for (int impl = 1; impl <= 3; impl += 2) {
+            if ((c->opt_impl == 1 && impl != 1) || (c->opt_impl == 3 && impl != 3) || (impl == 3 && sizeof(T) != 4))
+                continue;
+            for (int R = 8; R <= 128; R *= 2)
+                for (int nseg = 1; nseg <= 64; nseg *= 2) {
+                    const int th = (impl == 3 ? R / 2 : R) * nseg;
+                    if (th < (impl == 3 ? 32 : 64) || th > (impl == 3 ? VP_PAIR_THREADS : 512) || nseg * 8 > geo.L)
+                        continue;
+                    if (rows_smem<T>(geo.L, R, ghost_rows(geo)) > 200 * 1024) continue;
+                    if (nc < kMaxCand) cand[nc++] = SweepTune{1, impl, R, nseg, 0};
+                }
+        }
     }
     if (nc == 0) {
         c->tune[kick][dim] = best;

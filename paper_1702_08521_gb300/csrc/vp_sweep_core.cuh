@@ -18,6 +18,70 @@ namespace vp_core {
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// ---- two lines at once ---------------------------------------------------------
+//
+// P2 holds one value of each of two lines that a thread walks in lockstep.
+// Additions, multiplications and fused multiply-adds are the packed FP32
+// pair instructions of sm_100+ (one issue slot for both lines, each half
+// rounded exactly as the scalar instruction would round it); min, max and
+// comparisons are per half.  Every line therefore gets bit for bit the
+// result of the one-line walk, whichever of the two walks runs it.
+// the scalar overloads stay visible next to the pair overloads below
+using ::fma;
+using ::fmax;
+using ::fmin;
+
+struct P2 {
+    float2 v;
+    P2() = default;
+    __device__ __forceinline__ explicit P2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ P2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2(__fadd2_rn(a.v, b.v)); }
+// a - b as a + (-1) b: the product is exact, so this rounds as the subtraction
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ P2 operator-(P2 a) { return P2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ P2 fma(P2 a, P2 b, P2 c) { return P2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ P2 fmin(P2 a, P2 b) { return P2(make_float2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y))); }
+__device__ __forceinline__ P2 fmax(P2 a, P2 b) { return P2(make_float2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y))); }
+// both lines equal (the flat-stencil test asks it of both lines of a pair)
+__device__ __forceinline__ bool operator==(P2 a, P2 b) { return a.v.x == b.v.x && a.v.y == b.v.y; }
+
+// shift decompositions of a pair of lines walked together (equal n and sigma)
+struct LineShiftP2 {
+    P2 w[7];
+    P2 nu;
+    int n;
+    int sigma;
+};
+__device__ __forceinline__ LineShiftP2 pair_shift(const LineShift<float> &a, const LineShift<float> &b) {
+    LineShiftP2 s;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) s.w[k] = P2(make_float2(a.w[k], b.w[k]));
+    s.nu = P2(make_float2(a.nu, b.nu));
+    s.n = a.n;
+    s.sigma = a.sigma;
+    return s;
+}
+
+// whether the walker tests for warp-wide flat stencils (and then skips the
+// interpolant and the bounds); the result is the same either way
+template <typename T>
+struct FlatSkip {
+    static constexpr bool on = true;
+};
+template <>
+struct FlatSkip<P2> {
+    static constexpr bool on = true;
+};
+
+// 4/3 in the arithmetic's precision
+template <typename T>
+__device__ __forceinline__ T c43() { return T(4) / T(3); }
+template <>
+__device__ __forceinline__ P2 c43<P2>() { return P2(4.0f / 3.0f); }
+
 // minmod of four: min if all > 0, max if all < 0, else 0 (= max(min,0) + min(max,0))
 template <typename T>
 __device__ __forceinline__ T mm4(T a, T b, T c, T d) {
@@ -40,6 +104,12 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
 }
 __device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 __device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ P2 min3(P2 a, P2 b, P2 c) {
+    return P2(make_float2(min3(a.v.x, b.v.x, c.v.x), min3(a.v.y, b.v.y, c.v.y)));
+}
+__device__ __forceinline__ P2 max3(P2 a, P2 b, P2 c) {
+    return P2(make_float2(max3(a.v.x, b.v.x, c.v.x), max3(a.v.y, b.v.y, c.v.y)));
+}
 
 // curvature d_j = u_{j-1} - 2 u_j + u_{j+1} (App. A)
 template <typename T>
@@ -72,7 +142,7 @@ __device__ __forceinline__ T mp_clamp(T phi, T um1, T u0, T u1, T alpha, T m4m, 
     const T back = u0 - um1;
     const T ful = fma(alpha, back, u0);
     const T fmd = fma(T(0.5), u0 + u1, T(-0.5) * m4p);
-    const T flc = fma(T(4) / T(3), m4m, fma(T(0.5), back, u0));
+    const T flc = fma(c43<T>(), m4m, fma(T(0.5), back, u0));
     const T lo = fmax(min3(u0, u1, fmd), min3(u0, ful, flc));
     const T hi = fmin(max3(u0, u1, fmd), max3(u0, ful, flc));
     return fmin(fmax(phi, lo), hi);
@@ -126,6 +196,8 @@ __device__ __forceinline__ T mp_limit(T phi, T um2, T um1, T u0, T u1, T u2, T a
 // may take out of a non-negative cell so that two of them leave it >= 0.
 __device__ __forceinline__ float half_rd(float u) { return __fmul_rd(u, 0.5f); }
 __device__ __forceinline__ double half_rd(double u) { return __dmul_rd(u, 0.5); }
+__device__ __forceinline__ P2 half_rd(P2 u) { return P2(__fmul2_rd(u.v, make_float2(0.5f, 0.5f))); }
+__device__ __forceinline__ P2 mul_rn(P2 a, P2 b) { return P2(__fmul2_rn(a.v, b.v)); }
 
 // PP limiter (Sec. 2.1.1, Eqs. 15-23) on the mass M = nu Phi that an interface
 // carries from its upwind cell u0 into u1.  For u0, u1 >= 0 and 0 < nu <= 1/2
@@ -173,8 +245,8 @@ __device__ __forceinline__ T flux(const LineShift<T> &sh, T um3, T um2, T um1, T
 
 // The CSL interpolant and, for the line walker, the MP constraint as a clamp
 // (no branch) with d^{M4} at both faces of u0 passed in.
-template <typename T, int ORDER, bool FULL>
-__device__ __forceinline__ T flux_walk(const LineShift<T> &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
+template <typename T, int ORDER, bool FULL, typename SH>
+__device__ __forceinline__ T flux_walk(const SH &sh, T um3, T um2, T um1, T u0, T u1, T u2, T u3,
                                        T alpha, int mp, T m4m, T m4p) {
     T phi;
     if (ORDER == 7) {
@@ -208,8 +280,8 @@ __device__ __forceinline__ T flux_walk(const LineShift<T> &sh, T um3, T um2, T u
 // The update is the flux form of Eq. 49 in masses, f' = (u - M_out) + M_in.
 // store(i, v) writes the new value of cell i.
 
-template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, typename Store>
-__device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, const LineShift<T> &sh,
+template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, typename Store, typename SH>
+__device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, const SH &sh,
                                      int r0, int r1, T alpha, int mp, int pp, Store store) {
     if (r0 >= r1) return;
     const int sg = sh.sigma;
@@ -272,8 +344,8 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
         T phi;                                                                                    \
         if (FULL || mp) {                                                                         \
             const T dp = curv(u0_, u1_, w[(K + 6) & 7]);                                          \
-            const bool flat = w[(K + 3) & 7] == u0_ && u0_ == u1_;                                \
-            if (__all_sync(__activemask(), flat)) {                                               \
+            if (FlatSkip<T>::on &&                                                                \
+                __all_sync(__activemask(), w[(K + 3) & 7] == u0_ && u0_ == u1_)) {                \
                 phi = u0_;                                                                        \
                 m4m = T(0);                                                                       \
             } else {                                                                              \

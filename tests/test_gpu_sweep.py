@@ -74,11 +74,12 @@ TMA_CASES = [
 
 
 @pytest.mark.parametrize("dims,nx,nv", TMA_CASES)
-@pytest.mark.parametrize("impl", [1, 2])
+@pytest.mark.parametrize("impl", [1, 2, 3])
 @pytest.mark.parametrize("precision", [V.VP_F64, V.VP_F32])
 def test_sweep_kernels_agree_with_oracle(dims, nx, nv, impl, precision):
-    """Both strided-axis kernels (staged loads, TMA pipeline) against the
-    oracle, with the autotuner on (it must leave f untouched)."""
+    """The strided-axis kernels (staged loads, TMA pipeline, staged loads with
+    two lines per thread) against the oracle, with the autotuner on (it must
+    leave f untouched)."""
     g = grid(dims, nx, nv, order=7, xbc=1 if dims == 3 else 0)
     sim, og = both(g, precision)
     V.vp_set_option(sim.ctx, V.VP_OPT_SWEEP_IMPL, impl)
@@ -101,7 +102,7 @@ def test_sweep_kernels_agree_with_oracle(dims, nx, nv, impl, precision):
             else:
                 assert rel_l1(f_g, f_o) <= 2e-6, (kick, d)
             tu = V.vp_get_tuning(sim.ctx, kick, d)
-            assert tu["impl"] in (1, 2)
+            assert tu["impl"] in (1, 2, 3)
             if impl == 1:
                 assert tu["impl"] == 1
     sim.close()
@@ -198,7 +199,7 @@ def test_sweep_bits_do_not_depend_on_tuning(dims, nx, nv):
              order=7)
     n = int(np.prod(nx)) * int(np.prod(nv))
     f0 = (inputs.random_f(n, seed=21, zeros=0.3) ** 2).astype(np.float32)
-    setups = [(0, 0), (1, 0), (2, 0), (0, 1), (0, 1), (1, 1)]  # (sweep impl, autotune)
+    setups = [(0, 0), (1, 0), (2, 0), (3, 0), (0, 1), (0, 1), (1, 1), (3, 1)]  # (sweep impl, autotune)
     sweeps = [(1, d) for d in range(dims)] + [(0, d) for d in range(dims)]
     results = []
     for impl, tune in setups:
