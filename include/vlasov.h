@@ -315,13 +315,13 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
 
 /* one sweep of the grid of ctx (FP32, order 7) with the network correction
  * (use_net = 1: PP on the corrected mass; use_net = 2: MP bounds then PP;
- * drifts only) or without it (use_net = 0: identical to vp_drift_sweep /
- * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); f_snap_dev: a copy
- * of f taken before the sweep (device, vp_num_cells floats), read for the
- * velocity neighbours when use_net > 0; NULL: the library copies f into a
- * buffer of its own (allocated on first use, freed by vp_destroy) on ctx's
- * stream; ignored when use_net = 0; in place.  VP_ENOTSUP for use_net with
- * kick = 1, VP_EINVAL for use_net outside 0..2. */
+ * drifts only) or without it (use_net = 0: the same call as vp_drift_sweep /
+ * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); in place.  Each CTA
+ * stages all velocity cells of the sweep's velocity axis for its lines, so
+ * every line's velocity neighbours are read before any cell is written:
+ * f_snap_dev is not read (kept in the signature; may be NULL).  At most 256
+ * velocity cells on that axis (VP_ENOTSUP beyond).  VP_ENOTSUP for use_net
+ * with kick = 1, VP_EINVAL for use_net outside 0..2. */
 int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
                      const float *wts_dev, int use_net, const float *f_snap_dev);
 
@@ -350,6 +350,14 @@ int vp_fine_flux(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_
  * NULL to query the sizes. */
 int vp_fluxnet_line_map(const vp_grid *fine, const vp_grid *coarse, int factor, int kick, int dim,
                         long long *map_host, long long *n_coarse_lines, int *group);
+
+/* Coefficients of the cell-pair training loss: for pair t with left and
+ * right interface samples li[t], ri[t] (indices into sc, the samples' scales
+ * s from vp_make_samples) coef[2t] = -s_l / m, coef[2t + 1] = s_r / m,
+ * m = max(s_l, s_r), and (weight not NULL) weight[t] = m^importance, the
+ * pair's draw weight.  Device arrays; asynchronous on `stream`. */
+int vp_pair_coefs(const float *sc, const long long *li, const long long *ri, long long n, double importance,
+                  float *coef, double *weight, void *stream);
 
 /* G_coarse[l][j] = scale * mean_g G_fine[map[l][g]][j] (device arrays) */
 int vp_group_mean(const double *G_fine, long long n_coarse_lines, int nout, const long long *map_dev,

@@ -163,7 +163,6 @@ void free_buffers(vp_ctx *c) {
     cudaFree(c->d_diag);
     cudaFree(c->d_flag);
     cudaFree(c->d_status);
-    cudaFree(c->d_snap);
     cudaFree(c->d_netfrag);
     if (c->graph.valid) cudaGraphExecDestroy(c->graph.exec);
 }

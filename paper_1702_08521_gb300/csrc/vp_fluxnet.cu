@@ -29,6 +29,7 @@
 
 #include "vp_internal.cuh"
 #include "vp_sweep_core.cuh"
+#include "vp_umma.cuh"
 
 namespace {
 
@@ -103,7 +104,7 @@ __device__ __forceinline__ float net_features(const float *u, const float *up, c
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[8 + k] = (up[k] - um[k]) * (0.5f * inv);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) x[16 + k] = (0.5f * (up[k] + um[k]) - u[k]) * inv;
+    for (int k = 0; k < 8; ++k) x[16 + k] = fmaf(0.5f, up[k] + um[k], -u[k]) * inv;
     x[24] = nu;
     return s;
 }
@@ -437,6 +438,22 @@ __global__ void k_make_samples(const float *__restrict__ fc, long long outer, in
     if (sc) sc[t] = s;
 }
 
+// cell pairs of the training loss: the residual of the cell between
+// interfaces l and r is (s_r (g_r - y_r) - s_l (g_l - y_l)) / max(s_l, s_r),
+// so the pair's coefficients are (-s_l / m, s_r / m), m = max(s_l, s_r); the
+// draw weight of the pair is m^importance (1 for importance 0)
+__global__ void k_pair_coefs(const float *__restrict__ sc, const long long *__restrict__ li,
+                             const long long *__restrict__ ri, long long n, double importance,
+                             float *__restrict__ coef, double *__restrict__ weight) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double sl = sc[li[t]], sr = sc[ri[t]];
+    const double m = sl > sr ? sl : sr;
+    coef[2 * t] = (float)(-(sl / m));
+    coef[2 * t + 1] = (float)(sr / m);
+    if (weight) weight[t] = importance > 0.0 ? pow(m, importance) : 1.0;
+}
+
 // coarse-interface masses from fine ones: mean over `group` fine lines of
 // every fine value, scaled by `scale` (fine -> coarse cell units)
 __global__ void k_group_mean(const double *__restrict__ Gf, long long ncl, int nout, const long long *map,
@@ -452,40 +469,25 @@ __global__ void k_group_mean(const double *__restrict__ Gf, long long ncl, int n
 
 // ---- inference: the learned coarse sweep, network on the tensor cores -------------------
 //
-// A CTA takes NL consecutive lines of the sweep.  Phase 0 stages the lines
-// and, from the snapshot, their velocity-difference lines (u+ - u-) / 2 and
-// velocity-curvature lines (u+ + u-) / 2 - u in shared memory (consecutive
-// threads read consecutive lines: coalesced for strided sweeps), with the
-// lines' shift decompositions.  Phase 1 computes every interface's limited
-// mass: the plain MP mass, plus s g from the network on the tensor cores
-// (described at the loop), then (use_net = 2) the MP bounds, and the PP
-// limiter.  Phase 2: one thread per
-// cell writes the flux-form update.  Interface k of a line is the k-th one
-// the upwind walk meets: its upwind cell is q_k = q_0 + k sigma,
-// q_0 = (sigma > 0 ? 0 : L - 1) - n - sigma; the k-th cell of the walk
-// (k >= 1) takes M_{k-1} in and M_k out.
+// A CTA stages a tile of lines of the drift along x_d in shared memory: all L
+// cells of each line, for every velocity index j of the axis v_d (the line
+// class) times a block of the other indices, so that the velocity neighbours
+// of every line (j +- 1, the +/- lines of the features) are in the tile and no
+// other CTA reads the tile's lines: the update is written to f in place,
+// without a snapshot.  Each lane then walks one line upwind -> downwind as the
+// plain line walker does (8-cell windows of the line and of its velocity
+// difference and curvature in registers, one new row per interface, the MP
+// curvature and d^{M4} carried), and at every interface the warp's 32 lanes
+// form one 32-row feature tile for the network on the tensor cores.  The
+// interface mass (plain MP mass plus s g, MP bounds when asked, PP) leaves the
+// upwind cell and enters the next, so each cell is written once:
+// f' = (u - M_out) + M_in.
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 128;  // one line per thread, one 128-row MMA operand per interface step
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// D = A B + C with C = (c.x, c.y) in both row halves of the lane's fragment
-__device__ __forceinline__ void mma_bf16_c(float (&d)[4], const uint32_t (&a)[4], uint2 b, float2 c) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%10,%11,%10,%11};"
-        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y), "f"(c.x), "f"(c.y));
 }
 
 // bf16(max(lo, 0)) in the low half, bf16(max(hi, 0)) in the high half
@@ -495,366 +497,305 @@ __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
     return d;
 }
 
-// four 8x8 bf16 matrices from shared memory, one row address per lane
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr)
-                 : "memory");
-}
-
-// ReLU, round to bf16 and re-pack accumulators as the next layer's A fragments
-__device__ __forceinline__ void relu_pack(const float (&acc)[4][4], uint32_t (&a)[2][4]) {
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-        a[kb][0] = pack_relu_bf16(acc[2 * kb][0], acc[2 * kb][1]);
-        a[kb][1] = pack_relu_bf16(acc[2 * kb][2], acc[2 * kb][3]);
-        a[kb][2] = pack_relu_bf16(acc[2 * kb + 1][0], acc[2 * kb + 1][1]);
-        a[kb][3] = pack_relu_bf16(acc[2 * kb + 1][2], acc[2 * kb + 1][3]);
-    }
-}
-
-// per-line data of a learned-sweep CTA
-struct LLine {
-    long long base;  // offset of row 0
-    int sp;          // +1 / -1: the velocity neighbour with larger |v| is at +sp
-    int has_p, has_m;
-    int q0;          // upwind cell of the walk's first interface (unwrapped)
+// tile of a learned sweep: columns col = (g cmod + j) T + t hold the line with
+// inner index c = c_tile + g cmod cdiv + j cdiv + t (class j); tiles per outer
+// index: (inner / (G cmod cdiv)) (cdiv / T)
+struct LTile {
+    long long outer, inner, cdiv, cmod;
+    int L, T, G, NC, pitch;  // NC = G cmod T columns, row pitch in floats
+    long long tpo;           // tiles per outer index
+    long long tblocks;       // t blocks per group block: cdiv / T
 };
 
-constexpr int kLG = 8;   // staged rows on each side of a learned-sweep line
-constexpr int kFS = 80;  // bytes per feature row (32 bf16 + 16 pad: conflict-free ldmatrix)
+// Network operands for the tensor cores, prepared once per call from the
+// FP32 master weights: W1, W2, W3 (32 outputs x 48 inputs) and w4 (row 0 of a
+// 16 x 48 matrix) as bf16 in the canonical K-major layout.  Inputs 0-31 are
+// the layer's inputs (W1 zero beyond its 25 features); every A row carries
+// the constant 1 in columns 32 and 33, and the operands hold the bias there
+// as a bf16 pair, b = bf16(b) + bf16(b - bf16(b)), so the accumulator starts
+// from the bias to 16 significant bits and no epilogue adds it.
+constexpr int kOpW = 32 * vp_umma::kK * 2;    // bytes of one 32-row bf16 operand
+constexpr int kOpW4 = 16 * vp_umma::kK * 2;   // 16 rows
+constexpr int kOpBytes = 3 * kOpW + kOpW4;
+constexpr int kOpAlloc = (kOpBytes + 127) / 128 * 128;
 
-// network weights in the order the learned sweep keeps them in shared memory:
-// B fragments of the three hidden layers [layer][k block][n tile][lane][2],
-// the w4 fragments [k block][lane] (w4 in column 0 of B), then b1 b2 b3,
-// bf16(w4) and b4 (129 floats, padded to 132)
-constexpr int kFragWords = 3 * 2 * 4 * 32 * 2 + 2 * 32 * 2 + 132;
-static_assert(kFragWords % 4 == 0, "fragment block is copied in 16-byte units");
-
-__global__ void k_net_frags(const float *__restrict__ wts, uint32_t *__restrict__ out) {
-    uint2 *w4f = reinterpret_cast<uint2 *>(out + 3 * 2 * 4 * 32 * 2);
-    float *wvec = reinterpret_cast<float *>(w4f + 2 * 32);
-    for (int e = threadIdx.x; e < 3 * 2 * 4 * 32; e += blockDim.x) {
-        const int lane = e & 31, frag = e >> 5;  // frag = (layer * 2 + kb) * 4 + nt
-        const int nt = frag & 3, kb = (frag >> 2) & 1, layer = frag >> 3;
-        const int off = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
+__global__ void k_net_umma(const float *__restrict__ wts, unsigned char *__restrict__ out) {
+    constexpr int K = vp_umma::kK;
+    for (int e = threadIdx.x; e < 3 * 32 * K + 16 * K; e += blockDim.x) {
+        int layer, n, k;
+        if (e < 3 * 32 * K) {
+            layer = e / (32 * K);
+            n = (e / K) % 32;
+            k = e % K;
+        } else {
+            layer = 3;
+            n = (e - 3 * 32 * K) / K;
+            k = (e - 3 * 32 * K) % K;
+        }
         const int kin = layer == 0 ? NF : H;
-        const int n = 8 * nt + (lane >> 2), k0 = 16 * kb + 2 * (lane & 3), k1 = k0 + 8;
-        auto wv = [&](int k) { return k < kin ? wts[off + n * kin + k] : 0.f; };
-        out[2 * e] = pack_bf16(wv(k0), wv(k0 + 1));
-        out[2 * e + 1] = pack_bf16(wv(k1), wv(k1 + 1));
-    }
-    for (int e = threadIdx.x; e < 2 * 32; e += blockDim.x) {
-        const int lane = e & 31, kb = e >> 5, k0 = 16 * kb + 2 * (lane & 3);
-        const float *w4 = wts + OFF_W4;
-        w4f[e] = (lane >> 2) == 0 ? make_uint2(pack_bf16(w4[k0], w4[k0 + 1]), pack_bf16(w4[k0 + 8], w4[k0 + 9]))
-                                  : make_uint2(0u, 0u);
-    }
-    for (int e = threadIdx.x; e < 132; e += blockDim.x) {
-        const int grp = e / H, n = e - grp * H;
-        wvec[e] = grp == 0   ? wts[OFF_B1 + n]
-                  : grp == 1 ? wts[OFF_B2 + n]
-                  : grp == 2 ? wts[OFF_B3 + n]
-                  : grp == 3 ? bfr(wts[OFF_W4 + n])
-                  : e == 4 * H ? wts[OFF_B4]
-                               : 0.f;
+        float w = 0.f, b = 0.f;
+        if (layer < 3) {
+            const int base = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
+            w = k < kin ? wts[base + n * kin + k] : 0.f;
+            b = wts[(layer == 0 ? OFF_B1 : (layer == 1 ? OFF_B2 : OFF_B3)) + n];
+        } else if (n == 0) {
+            w = k < H ? wts[OFF_W4 + k] : 0.f;
+            b = wts[OFF_B4];
+        }
+        const float bh = __bfloat162float(__float2bfloat16_rn(b));
+        const float v = k < 32 ? w : k == 32 ? bh : k == 33 ? b - bh : 0.f;
+        const uint32_t off = (uint32_t)(layer * kOpW) + vp_umma::kmajor_offset(n, k);
+        *reinterpret_cast<__nv_bfloat16 *>(out + off) = __float2bfloat16_rn(v);
     }
 }
 
-// divisors of the line index (host-precomputed; used when every line index fits 32 bits)
-struct LineDiv {
-    FastDiv inner, cdiv, cmod;
-    int fast;
-};
+constexpr int kLC = 4;                        // interfaces per line in one network batch
+constexpr int kABytes = 128 * vp_umma::kK * 2;  // one 128 x 48 bf16 feature operand
+
+// bf16 columns 0-31 of row r (in w) of an operand in the canonical layout
+__device__ __forceinline__ void store_row(unsigned char *op, int r, const uint32_t (&w)[16]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+        *reinterpret_cast<uint4 *>(op + vp_umma::kmajor_offset(r, 8 * kk)) =
+            make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
+}
+
+// The three hidden layers and the output layer for `nb` operands of 128
+// feature rows (operand b at A + b kABytes, accumulator columns 32 b .. 32 b
+// + 31), on the tensor cores: one thread issues each layer's MMAs (three
+// k-blocks of 16) and commits them to the mbarrier; every thread then reads
+// its own row back from tensor memory, applies ReLU, rounds to bf16 and
+// writes it as the next layer's A row.  Returns g of this thread's row of
+// each operand.  Bounded waits: on a timeout the status word is set.
+__device__ __forceinline__ void net_tc(unsigned char *A, const unsigned char *ops, uint32_t tmem, uint64_t *bar,
+                                       uint32_t &phase, int nb, float (&g)[kLC], int *status) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t a_s = vp_tma::saddr(A), w_s = vp_tma::saddr(ops);
+    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int layer = 0; layer < 4; ++layer) {
+        vp_umma::fence_proxy_async();
+        vp_umma::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            vp_umma::fence_after_sync();
+            const uint32_t idesc = vp_umma::idesc_bf16_f32(128, layer < 3 ? 32 : 16);
+            const uint64_t bd = vp_umma::smem_desc(w_s + (uint32_t)(layer * kOpW), 128, vp_umma::kSBO);
+            for (int b = 0; b < nb; ++b) {
+                const uint64_t ad = vp_umma::smem_desc(a_s + (uint32_t)(b * kABytes), 128, vp_umma::kSBO);
+#pragma unroll
+                for (int s = 0; s < vp_umma::kK / 16; ++s)  // 256 bytes per k-block: 16 to the address field
+                    vp_umma::mma_bf16(tmem + (uint32_t)(32 * b), ad + (uint64_t)(16 * s), bd + (uint64_t)(16 * s),
+                                      idesc, (uint32_t)s);
+            }
+            vp_umma::commit(bar);
+        }
+        const bool done = vp_tma::mbar_wait(bar, phase, 1u << 24);
+        phase ^= 1u;
+        if (!done) atomicExch(status, VP_ETIMEOUT);
+        vp_umma::fence_after_sync();
+        if (layer < 3) {
+            for (int b = 0; b < nb; ++b) {
+                float v[32];
+                vp_umma::ld32(tl + (uint32_t)(32 * b), v);
+                uint32_t w[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) w[i] = pack_relu_bf16(v[2 * i], v[2 * i + 1]);
+                store_row(A + b * kABytes, threadIdx.x, w);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < kLC; ++b) g[b] = b < nb ? vp_umma::ld1(tl + (uint32_t)(32 * b)) : 0.f;
+        }
+    }
+}
 
 template <bool PERIODIC>
-__global__ void __launch_bounds__(kTcThreads) k_learned_sweep(float *__restrict__ f, long long outer, int L,
-                                                              long long inner, int from_inner, long long cdiv,
-                                                              long long cmod,
-                                                              const LineShift<float> *__restrict__ tab,
-                                                              const uint4 *__restrict__ netfrag, double lo,
-                                                              double dvel, float alpha,
-                                                              int use_net, const float *__restrict__ fsnap,
-                                                              int lgNL, LineDiv ldv) {
-    extern __shared__ __align__(16) unsigned char tsm[];
-    const int NL = 1 << lgNL;
-    const int NI = NL * (L + 1);  // interface e = k * NL + l (line l, k-th interface of its walk)
-    const int LP = L + 2 * kLG;   // staged rows: -kLG .. L + kLG - 1
-    uint32_t *wfrag = reinterpret_cast<uint32_t *>(tsm);  // [3][2][4][32 lanes][2] B fragments
-    uint2 *w4f = reinterpret_cast<uint2 *>(wfrag + 3 * 2 * 4 * 32 * 2);  // [2][32 lanes] w4 in column 0
-    float *wvec = reinterpret_cast<float *>(w4f + 2 * 32);  // b1 b2 b3 w4(bf16) b4: 129
-    LineShift<float> *shs = reinterpret_cast<LineShift<float> *>(wvec + 132);
-    LLine *lls = reinterpret_cast<LLine *>(shs + NL);
-    float *lines = reinterpret_cast<float *>(lls + NL);  // [LP][NL], row r at (r + kLG)
-    float *dvl = lines + NL * LP;                         // [LP][NL] velocity differences
-    float *cvl = dvl + NL * LP;                           // [LP][NL] velocity curvatures
-    float *mass = cvl + NL * LP;                          // [L + 1][NL] interface masses
-    // per warp: 32 feature rows of kFS bytes
-    unsigned char *fbuf = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(mass + (size_t)NL * (L + 1)) + 15) & ~static_cast<uintptr_t>(15));
-    const long long nlines = outer * inner;
-    const long long l0 = (long long)blockIdx.x * NL;
-    const int nl = (int)(nlines - l0 < NL ? nlines - l0 : NL);
-    // phase 0: network fragments, per-line data, then the lines and their
-    // velocity-difference and velocity-curvature lines
-    if (use_net) {
-        uint4 *dst = reinterpret_cast<uint4 *>(tsm);
-        for (int e = threadIdx.x; e < kFragWords / 4; e += blockDim.x) dst[e] = netfrag[e];
-    }
-    for (int l = threadIdx.x; l < NL; l += blockDim.x) {
-        LLine ll{0, 1, 0, 0, 0};
-        LineShift<float> sh{};
-        sh.sigma = 1;
-        if (l < nl) {
-            const long long line = l0 + l;
-            long long o, c, cls;
-            if (ldv.fast) {
-                const unsigned ou = fdiv((unsigned)line, ldv.inner);
-                o = ou;
-                c = (unsigned)line - ou * ldv.inner.d;
-                cls = from_inner ? fmod_u(fdiv((unsigned)c, ldv.cdiv), ldv.cmod) : fdiv(ou, ldv.cdiv);
-            } else {
-                o = line / inner;
-                c = line % inner;
-                cls = from_inner ? (c / cdiv) % cmod : o / cdiv;
-            }
-            sh = tab[cls];
-            ll.base = o * L * inner + c;
-            if (use_net) {  // drift lines: +sp is the neighbour with larger |v|
-                ll.sp = vp_core::cell_centre(lo, dvel, (int)cls) >= 0.0 ? 1 : -1;
-                ll.has_p = cls + ll.sp >= 0 && cls + ll.sp < cmod;
-                ll.has_m = cls - ll.sp >= 0 && cls - ll.sp < cmod;
-            }
-            int n = sh.n;
-            if (PERIODIC) {  // the shift modulo L, nearest to zero
-                n %= L;
-                if (n > L / 2) n -= L;
-                if (n < -(L / 2)) n += L;
-                sh.n = n;
-            }
-            ll.q0 = (sh.sigma > 0 ? 0 : L - 1) - n - sh.sigma;
-        }
-        shs[l] = sh;
-        lls[l] = ll;
-    }
-    __syncthreads();
-    const int lt = threadIdx.x & (NL - 1), rt = threadIdx.x >> lgNL, rstep = blockDim.x >> lgNL;
-    if (lt < nl) {
-        // four rows per thread in flight: all loads first, then the stores
-        const LLine ll = lls[lt];
-        const long long pofs = ll.sp * cdiv;
-        constexpr int B = 4;
-        for (int r0 = rt; r0 < LP; r0 += B * rstep) {
-            float v[B], up[B], um[B];
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const int r = r0 + j * rstep;
-                int rr = r - kLG;  // line row
-                if (PERIODIC) {
-                    if (L >= kLG) {  // staged rows reach at most kLG beyond either end
-                        rr += rr < 0 ? L : 0;
-                        rr -= rr >= L ? L : 0;
-                    } else {
-                        while (rr < 0) rr += L;
-                        while (rr >= L) rr -= L;
-                    }
-                }
-                const bool in = r < LP && (PERIODIC || (rr >= 0 && rr < L));
-                const long long a = ll.base + (long long)rr * inner;
-                v[j] = in ? f[a] : 0.f;
-                up[j] = in && use_net && ll.has_p ? fsnap[a + pofs] : 0.f;
-                um[j] = in && use_net && ll.has_m ? fsnap[a - pofs] : 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const int r = r0 + j * rstep;
-                if (r < LP) {
-                    lines[r * NL + lt] = v[j];
-                    if (use_net) {
-                        dvl[r * NL + lt] = 0.5f * (up[j] - um[j]);
-                        cvl[r * NL + lt] = 0.5f * (up[j] + um[j]) - v[j];
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // row q of staged line l: direct inside the staged rows, wrapped (periodic)
-    // or zero (outflow) beyond them (only for shifts of more than kLG - 5 cells)
-    auto row = [&](const float *ln, int l, int q) -> float {
-        if (q < -kLG || q >= L + kLG) {
-            if constexpr (PERIODIC) {
-                while (q < 0) q += L;
-                while (q >= L) q -= L;
-            } else {
-                return 0.f;
-            }
-        }
-        return ln[(q + kLG) * NL + l];
+__global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__ f, LTile tl,
+                                                             const LineShift<float> *__restrict__ tab,
+                                                             const uint4 *__restrict__ netops, double lo,
+                                                             double dvel, float alpha, int mode,
+                                                             int *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    unsigned char *A = tsm;                                // kLC operands of 128 x 32 bf16
+    unsigned char *ops = tsm + kLC * kABytes;              // W1 W2 W3 w4, biases
+    float *tile = reinterpret_cast<float *>(ops + kOpAlloc);  // [L][pitch]
+    const int L = tl.L, NC = tl.NC, pitch = tl.pitch, T = tl.T;
+    const int cmod = (int)tl.cmod;
+    const long long o = (long long)blockIdx.x / tl.tpo;
+    const long long tin = (long long)blockIdx.x - o * tl.tpo;
+    const long long gb = tin / tl.tblocks, tb = tin - gb * tl.tblocks;
+    // inner index of column col
+    auto col_c = [&](int col) -> long long {
+        const int t = col % T, jg = col / T;
+        const int j = jg % cmod, g = jg / cmod;
+        return (gb * tl.G + g) * tl.cmod * tl.cdiv + (long long)j * tl.cdiv + tb * T + t;
     };
-    if (!use_net) {
-        // phase 1 without the network: limited mass of every interface (CSL7, MP, PP)
-        for (int e = threadIdx.x; e < NI; e += blockDim.x) {
-            const int l = e & (NL - 1), k = e >> lgNL;
-            if (l >= nl) continue;
-            const LineShift<float> &sh = shs[l];
-            const int sg = sh.sigma;
-            const int q = lls[l].q0 + k * sg;
-            const int qa = q - 3 * sg, qb = q + 3 * sg;
-            float u[7];
-            if (min(qa, qb) >= -kLG && max(qa, qb) < L + kLG) {
-                const int st = sg * NL;
-                const float *pu = lines + (qa + kLG) * NL + l;
+    const long long obase = o * (long long)L * tl.inner;
+    // phase 0: network operands, tensor memory, mbarrier, the tile
+    for (int e = threadIdx.x; e < kOpAlloc / 16; e += blockDim.x)
+        reinterpret_cast<uint4 *>(ops)[e] = netops[e];
+    // columns 32-47 of every A row: 1, 1 (the bias pair), then zeros
+    for (int b = 0; b < kLC; ++b)
 #pragma unroll
-                for (int m = 0; m < 7; ++m) u[m] = pu[m * st];
-            } else {
+        for (int kk = 4; kk < vp_umma::kK / 8; ++kk)
+            *reinterpret_cast<uint4 *>(A + b * kABytes + vp_umma::kmajor_offset(threadIdx.x, 8 * kk)) =
+                kk == 4 ? make_uint4(pack_bf16(1.f, 1.f), 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x < 32) vp_umma::tmem_alloc(&tslot, 32 * kLC);
+    if (threadIdx.x == 0) {
+        vp_tma::mbar_init(&bar, 1);
+        vp_tma::fence_mbar_init();
+    }
+    {
+        // eight loads in flight per thread; a thread keeps its column, so the
+        // column's inner index is computed once
+        const int rstep = blockDim.x / NC > 0 ? (int)blockDim.x / NC : 1;
+        const int col = (int)threadIdx.x % NC, r0 = (int)threadIdx.x / NC;
+        if ((int)threadIdx.x < rstep * NC) {
+            const float *src = f + obase + col_c(col);
+            constexpr int U = 8;
+            int r = r0;
+            for (; r + (U - 1) * rstep < L; r += U * rstep) {
+                float v[U];
 #pragma unroll
-                for (int m = 0; m < 7; ++m) u[m] = row(lines, l, qa + m * sg);
+                for (int k = 0; k < U; ++k) v[k] = src[(long long)(r + k * rstep) * tl.inner];
+#pragma unroll
+                for (int k = 0; k < U; ++k) tile[(r + k * rstep) * pitch + col] = v[k];
             }
+            for (; r < L; r += rstep) tile[r * pitch + col] = src[(long long)r * tl.inner];
+        }
+    }
+    vp_umma::fence_before_sync();
+    __syncthreads();
+    vp_umma::fence_after_sync();
+    const uint32_t tmem = tslot;
+    uint32_t phase = 0;
+    const int col = threadIdx.x;
+    const bool ok = col < NC;
+    const int colc = ok ? col : 0;
+    // the line's shift and its velocity neighbours (+: larger |v|)
+    const int j = (colc / T) % cmod;
+    const LineShift<float> sh = tab[j];
+    const int sg = sh.sigma;
+    const float nu = sh.nu;
+    const int sp = vp_core::cell_centre(lo, dvel, j) >= 0.0 ? 1 : -1;
+    const int cp = (j + sp >= 0 && j + sp < cmod) ? colc + sp * T : -1;
+    const int cm = (j - sp >= 0 && j - sp < cmod) ? colc - sp * T : -1;
+    int n = sh.n;
+    if (PERIODIC) {  // the shift modulo L
+        n %= L;
+        if (n < 0) n += L;
+    }
+    // source row of the upwind cell of interface 0 (the cell before the
+    // walk's first cell), unwrapped for zero-inflow lines
+    const int q = (sg > 0 ? 0 : L - 1) - n - sg;
+    auto wrap = [&](int r) -> int {
+        if (PERIODIC) {
+            r %= L;
+            if (r < 0) r += L;
+        }
+        return r;
+    };
+    // cell value, velocity difference and velocity curvature at row r (wrapped
+    // for periodic lines; outside [0, L) zero for zero-inflow lines)
+    auto fetch_w = [&](int r, float &u, float &dv, float &cv) {
+        const bool in = ok && (PERIODIC || (r >= 0 && r < L));
+        u = in ? tile[r * pitch + colc] : 0.f;
+        const float up = in && cp >= 0 ? tile[r * pitch + cp] : 0.f;
+        const float um = in && cm >= 0 ? tile[r * pitch + cm] : 0.f;
+        dv = up - um;
+        cv = fmaf(0.5f, up + um, -u);
+    };
+    float u[8], dv[8], cv[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) fetch_w(wrap(q + (m - 3) * sg), u[m], dv[m], cv[m]);
+    // the row entering the window after interface k: q + 5 sg, wrapped incrementally
+    int rn = wrap(q + 5 * sg);
+    // MP carries: curvature of the upwind cell, d^{M4} at its upwind face
+    float dc = vp_core::curv(u[2], u[3], u[4]);
+    float m4m = vp_core::dm4(vp_core::curv(u[1], u[2], u[3]), dc);
+    float Min = 0.f;
+    const long long cbase = obase + col_c(colc);
+#pragma unroll 1
+    for (int k0 = 0; k0 <= L; k0 += kLC) {
+        const int nb = L + 1 - k0 < kLC ? L + 1 - k0 : kLC;
+        float Mp[kLC], sc[kLC], mlo[kLC], mhi[kLC], u3[kLC], u4[kLC];
+#pragma unroll
+        for (int b = 0; b < kLC; ++b) {
+            if (b >= nb) break;
+            // plain mass of interface k0 + b (CSL7, MP bounds as a clamp)
+            const float dp = vp_core::curv(u[3], u[4], u[5]);
+            const float m4p = vp_core::dm4(dc, dp);
             float phi = sh.w[0] * u[0];
 #pragma unroll
             for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
-            phi = vp_core::mp_limit(phi, u[1], u[2], u[3], u[4], u[5], alpha);
-            mass[e] = vp_core::pp_clamp(vp_core::mul_rn(sh.nu, phi), vp_core::half_rd(u[3]),
-                                        vp_core::half_rd(u[4]));
+            vp_core::mp_lohi_carried(u[2], u[3], u[4], alpha, m4m, m4p, mlo[b], mhi[b]);
+            Mp[b] = vp_core::mul_rn(nu, fminf(fmaxf(phi, mlo[b]), mhi[b]));
+            u3[b] = u[3];
+            u4[b] = u[4];
+            // feature row (columns 0-7 stencil, 8-15 velocity difference,
+            // 16-23 velocity curvature, 24 nu, 25-31 zero), as net_features
+            float s = 0.f;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) s = fmaxf(s, fabsf(u[m]));
+            s += 1e-30f;
+            sc[b] = s;
+            const float inv = 1.0f / s;
+            const float hinv = 0.5f * inv;
+            uint32_t w[16];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) w[m] = pack_bf16((u[2 * m] - u[3]) * inv, (u[2 * m + 1] - u[3]) * inv);
+            w[1] = pack_bf16((u[2] - u[3]) * inv, 0.f);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) w[4 + m] = pack_bf16(dv[2 * m] * hinv, dv[2 * m + 1] * hinv);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) w[8 + m] = pack_bf16(cv[2 * m] * inv, cv[2 * m + 1] * inv);
+            w[12] = pack_bf16(nu, 0.f);
+            w[13] = w[14] = w[15] = 0u;
+            store_row(A + b * kABytes, threadIdx.x, w);
+            // advance the window and the MP carries
+            dc = dp;
+            m4m = m4p;
+            float un, dvn, cvn;
+            fetch_w(rn, un, dvn, cvn);
+            rn += sg;
+            if (PERIODIC) {
+                rn = rn == L ? 0 : rn;
+                rn = rn < 0 ? L - 1 : rn;
+            }
+#pragma unroll
+            for (int m = 0; m < 7; ++m) {
+                u[m] = u[m + 1];
+                dv[m] = dv[m + 1];
+                cv[m] = cv[m + 1];
+            }
+            u[7] = un;
+            dv[7] = dvn;
+            cv[7] = cvn;
         }
-    } else {
-        // phase 1 with the network: a warp takes 32 interfaces (two 16-row MMA
-        // tiles).  Lane i computes interface i's plain MP mass and its feature
-        // row (bf16, columns 0-7 stencil, 8-15 velocity difference, 16-23
-        // velocity curvature, 24 nu, 25-31 zero) into the warp's buffer;
-        // ldmatrix turns the rows into A fragments; the layers run with
-        // mma.sync (biases as the C operand, FP32 accumulation, ReLU and bf16
-        // rounding in one conversion); the output layer is an MMA with w4 in
-        // column 0 of B; lane i then adds s g and applies the PP limiter (after
-        // the MP bounds when use_net = 2).
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = lane & 3;
-        unsigned char *fb = fbuf + warp * 32 * kFS;
-        const uint32_t fb_s = static_cast<uint32_t>(__cvta_generic_to_shared(fb));
-        // this lane's ldmatrix row: matrix lane >> 3 holds rows +8 (odd) and columns +8 (>= 2)
-        const uint32_t ldm = fb_s + (uint32_t)(((lane & 7) + 8 * ((lane >> 3) & 1)) * kFS + 16 * (lane >> 4));
-        const uint2 *wf2 = reinterpret_cast<const uint2 *>(wfrag);
-        const float2 b4c = make_float2(t == 0 ? wvec[4 * H] : 0.f, 0.f);
-        const int nit = (NI + 31) >> 5;
-        for (int it = warp; it < nit; it += blockDim.x >> 5) {
-            const int e = (it << 5) + lane;
-            const int l = e & (NL - 1), k = e >> lgNL;
-            const bool ok = e < NI && l < nl;
-            float Mp = 0.f, s = 1.f, u3 = 0.f, u4 = 0.f, nu = 0.f, mlo = 0.f, mhi = 0.f;
-            uint4 p0 = make_uint4(0u, 0u, 0u, 0u), p1 = p0, p2 = p0, p3 = p0;
-            if (ok) {
-                const LineShift<float> &sh = shs[l];
-                const int sg = sh.sigma;
-                const int q = lls[l].q0 + k * sg;
-                nu = sh.nu;
-                float u[8], dv[8], cv[8];
-                const int qa = q - 3 * sg, qb = q + 4 * sg;
-                if (min(qa, qb) >= -kLG && max(qa, qb) < L + kLG) {
-                    const int st = sg * NL;
-                    const float *pu = lines + (qa + kLG) * NL + l;
+        float g[kLC];
+        net_tc(A, ops, tmem, &bar, phase, nb, g, status);
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        u[m] = pu[m * st];
-                        dv[m] = pu[NL * LP + m * st];
-                        cv[m] = pu[2 * NL * LP + m * st];
-                    }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        u[m] = row(lines, l, qa + m * sg);
-                        dv[m] = row(dvl, l, qa + m * sg);
-                        cv[m] = row(cvl, l, qa + m * sg);
-                    }
-                }
-                float phi = sh.w[0] * u[0];
-#pragma unroll
-                for (int m = 1; m < 7; ++m) phi = fmaf(sh.w[m], u[m], phi);
-                // MP bounds of this stencil (App. A steps 4-6); the plain
-                // mass and, after the network, the corrected one are clamped
-                // into them (the constraint equals the clamp, see mp_clamp)
-                vp_core::mp_lohi(u[1], u[2], u[3], u[4], u[5], alpha, mlo, mhi);
-                mlo = vp_core::mul_rn(nu, mlo);
-                mhi = vp_core::mul_rn(nu, mhi);
-                Mp = fminf(fmaxf(vp_core::mul_rn(nu, phi), mlo), mhi);
-                u3 = u[3];
-                u4 = u[4];
-                s = 0.f;
-#pragma unroll
-                for (int m = 0; m < 8; ++m) s = fmaxf(s, fabsf(u[m]));
-                s += 1e-30f;
-                const float inv = 1.0f / s;
-                p0 = make_uint4(pack_bf16((u[0] - u3) * inv, (u[1] - u3) * inv),
-                                pack_bf16((u[2] - u3) * inv, 0.f), pack_bf16((u[4] - u3) * inv, (u[5] - u3) * inv),
-                                pack_bf16((u[6] - u3) * inv, (u[7] - u3) * inv));
-                p1 = make_uint4(pack_bf16(dv[0] * inv, dv[1] * inv), pack_bf16(dv[2] * inv, dv[3] * inv),
-                                pack_bf16(dv[4] * inv, dv[5] * inv), pack_bf16(dv[6] * inv, dv[7] * inv));
-                p2 = make_uint4(pack_bf16(cv[0] * inv, cv[1] * inv), pack_bf16(cv[2] * inv, cv[3] * inv),
-                                pack_bf16(cv[4] * inv, cv[5] * inv), pack_bf16(cv[6] * inv, cv[7] * inv));
-                p3.x = pack_bf16(nu, 0.f);
+        for (int b = 0; b < kLC; ++b) {
+            if (b >= nb) break;
+            float M = fmaf(sc[b], g[b], Mp[b]);
+            if (mode == 2) M = fminf(fmaxf(M, vp_core::mul_rn(nu, mlo[b])), vp_core::mul_rn(nu, mhi[b]));
+            M = vp_core::pp_clamp(M, vp_core::half_rd(u3[b]), vp_core::half_rd(u4[b]));
+            // the cell whose source is u3 takes M in from the previous interface
+            const int k = k0 + b;
+            if (ok && k >= 1) {
+                const int i = sg > 0 ? k - 1 : L - k;
+                f[cbase + (long long)i * tl.inner] = (u3[b] - M) + Min;
             }
-            uint4 *fr = reinterpret_cast<uint4 *>(fb + lane * kFS);
-            fr[0] = p0;
-            fr[1] = p1;
-            fr[2] = p2;
-            fr[3] = p3;
-            __syncwarp();
-            uint32_t a[2][2][4];  // [tile][k block][fragment]
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int kb = 0; kb < 2; ++kb) ldsm_x4(a[j][kb], ldm + (uint32_t)(j * 16 * kFS + kb * 32));
-            __syncwarp();
-            float acc[2][4][4];
-#pragma unroll
-            for (int layer = 0; layer < 3; ++layer) {
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const float2 b = *reinterpret_cast<const float2 *>(wvec + layer * H + 8 * nt + 2 * t);
-                    const uint2 bb0 = wf2[((layer * 2 + 0) * 4 + nt) * 32 + lane];
-                    const uint2 bb1 = wf2[((layer * 2 + 1) * 4 + nt) * 32 + lane];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        mma_bf16_c(acc[j][nt], a[j][0], bb0, b);
-                        mma_bf16(acc[j][nt], a[j][1], bb1.x, bb1.y);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 2; ++j) relu_pack(acc[j], a[j]);
-            }
-            float g[2][4];
-            const uint2 w40 = w4f[lane], w41 = w4f[32 + lane];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                mma_bf16_c(g[j], a[j][0], w40, b4c);
-                mma_bf16(g[j], a[j][1], w41.x, w41.y);
-            }
-            // row r of tile j sits in lane 4 (r mod 8), element 0 (r < 8) or 2
-            const int src = (lane & 7) << 2;
-            const float g00 = __shfl_sync(0xffffffffu, g[0][0], src);
-            const float g02 = __shfl_sync(0xffffffffu, g[0][2], src);
-            const float g10 = __shfl_sync(0xffffffffu, g[1][0], src);
-            const float g12 = __shfl_sync(0xffffffffu, g[1][2], src);
-            const float gi = (lane & 16) ? ((lane & 8) ? g12 : g10) : ((lane & 8) ? g02 : g00);
-            if (ok) {
-                float M = fmaf(s, gi, Mp);
-                if (use_net == 2) M = fminf(fmaxf(M, mlo), mhi);
-                mass[e] = vp_core::pp_clamp(M, vp_core::half_rd(u3), vp_core::half_rd(u4));
-            }
+            Min = M;
         }
     }
+    vp_umma::fence_before_sync();
     __syncthreads();
-    // phase 2: the flux-form update, one thread per cell (consecutive
-    // threads: consecutive lines)
-    if (lt < nl) {
-        const int sg = shs[lt].sigma, q0 = lls[lt].q0;
-        const long long base = lls[lt].base;
-        for (int kr = rt; kr < L; kr += rstep) {
-            const int k = kr + 1;                  // the cell between interfaces k - 1 and k
-            const int i = sg > 0 ? k - 1 : L - k;  // the k-th cell of the walk
-            const float v = row(lines, lt, q0 + k * sg) - (mass[k * NL + lt] - mass[(k - 1) * NL + lt]);
-            f[base + (long long)i * inner] = v;
-        }
+    if (threadIdx.x < 32) {
+        vp_umma::fence_after_sync();
+        vp_umma::tmem_dealloc(tmem, 32 * kLC);
     }
 }
 
@@ -931,11 +872,10 @@ LineGeo line_geo(const vp_grid &g, long long NX, long long NV, int kick, int dim
 
 int vp_learned_prepare(vp_ctx *c) {
     if (c->learned_ready) return VP_OK;
-    if (!c->d_snap) VP_CUDA_TRY(c, cudaMalloc(&c->d_snap, (size_t)c->ncell * sizeof(float)));
-    if (!c->d_netfrag) VP_CUDA_TRY(c, cudaMalloc(&c->d_netfrag, kFragWords * sizeof(uint32_t)));
-    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (!c->d_netfrag) VP_CUDA_TRY(c, cudaMalloc(&c->d_netfrag, kOpAlloc));
+    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
-    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
     c->learned_ready = 1;
     return VP_OK;
@@ -945,6 +885,7 @@ extern "C" {
 
 int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
                      int use_net, const float *f_snap) {
+    (void)f_snap;  // the tile holds every line's velocity neighbours: no snapshot is needed
     if (!c || !c->f) return VP_EINVAL;
     if (c->g.precision != VP_F32 || c->g.order != 7)
         return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
@@ -952,57 +893,55 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
     if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
         return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
+    if (!use_net) return kick ? vp_kick_sweep(c, dim, dt, accel_dev) : vp_drift_sweep(c, dim, dt);
     int rc = vp_learned_prepare(c);
     if (rc != VP_OK) return rc;
-    if (use_net && !f_snap) {
-        // snapshot of f before the sweep in the library-owned buffer
-        VP_CUDA_TRY(c, cudaMemcpyAsync(c->d_snap, c->f, (size_t)c->ncell * sizeof(float),
-                                       cudaMemcpyDeviceToDevice, c->stream));
-        f_snap = static_cast<const float *>(c->d_snap);
-    }
     const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
+    // tile: every class j of its lines times a block of the other indices,
+    // about 128 lines (columns)
+    LTile tl{};
+    tl.outer = q.outer;
+    tl.inner = q.inner;
+    tl.cdiv = q.cdiv;
+    tl.cmod = q.cmod;
+    tl.L = q.L;
+    const long long NG = q.inner / (q.cmod * q.cdiv);
+    const int target = 128;
+    if (q.cmod > kTcThreads)
+        return vp_fail(c, VP_ENOTSUP, "more than %d velocity cells on the sweep's axis", kTcThreads);
+    if (q.cmod * q.cdiv <= target) {
+        tl.T = (int)q.cdiv;
+        long long G = target / (q.cmod * q.cdiv);
+        while (G > 1 && NG % G) --G;
+        tl.G = (int)(G < 1 ? 1 : G);
+    } else {
+        tl.G = 1;
+        long long T = target / q.cmod;
+        if (T < 1) T = 1;
+        while (T > 1 && q.cdiv % T) --T;
+        tl.T = (int)T;
+    }
+    tl.NC = (int)(tl.G * q.cmod * tl.T);
+    tl.pitch = (tl.NC + 31) / 32 * 32;
+    tl.tblocks = q.cdiv / tl.T;
+    tl.tpo = (NG / tl.G) * tl.tblocks;
+    const int threads = kTcThreads;  // one 128-row operand: a thread per row, rows >= NC are idle
+    const size_t smem = (size_t)kLC * kABytes + kOpAlloc + (size_t)q.L * tl.pitch * sizeof(float);
+    if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "lines too long for the learned sweep");
+    const long long blocks = q.outer * tl.tpo;
+    if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "learned sweep has too many tiles");
     rc = vp_launch_shift_table(c, kick, dim, dt, accel_dev);
     if (rc != VP_OK) return rc;
-    if (use_net) {
-        k_net_frags<<<1, 256, 0, c->stream>>>(wts, static_cast<uint32_t *>(c->d_netfrag));
-        c->launches++;
-    }
-    // lines per CTA: a power of two, at most 16; the largest that leaves room
-    // for 7 CTAs per SM (28 warps, as many as the registers allow), else the
-    // largest within 48 KB of shared memory
-    auto smem_for = [&](int nl) {
-        return (size_t)kFragWords * sizeof(uint32_t) + nl * (sizeof(LineShift<float>) + sizeof(LLine)) +
-               3 * (size_t)nl * (q.L + 2 * kLG) * sizeof(float) + (size_t)nl * (q.L + 1) * sizeof(float) + 16 +
-               (size_t)(kTcThreads / 32) * 32 * kFS;
-    };
-    int lgNL = 4;
-    while (lgNL > 0 && smem_for(1 << lgNL) > 31 * 1024) --lgNL;
-    if (smem_for(1 << lgNL) > 31 * 1024) {
-        lgNL = 4;
-        while (lgNL > 0 && smem_for(1 << lgNL) > 48 * 1024) --lgNL;
-    }
-    const int NL = 1 << lgNL;
-    const size_t smem = smem_for(NL);
-    if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "line too long for the learned sweep");
-    const long long nl = q.outer * q.inner;
-    const unsigned blocks = (unsigned)((nl + NL - 1) / NL);
+    k_net_umma<<<1, 256, 0, c->stream>>>(wts, static_cast<unsigned char *>(c->d_netfrag));
+    c->launches++;
     const LineShift<float> *tab = static_cast<const LineShift<float> *>(c->d_shift);
-    const uint4 *frag = static_cast<const uint4 *>(c->d_netfrag);
-    LineDiv ldv{};
-    ldv.fast = nl <= 0xFFFFFFFFll && q.inner <= 0xFFFFFFFFll && q.cdiv <= 0xFFFFFFFFll && q.cmod <= 0xFFFFFFFFll;
-    if (ldv.fast) {
-        ldv.inner = make_fastdiv((unsigned)q.inner);
-        ldv.cdiv = make_fastdiv((unsigned)q.cdiv);
-        ldv.cmod = make_fastdiv((unsigned)q.cmod);
-    }
+    const uint4 *ops = static_cast<const uint4 *>(c->d_netfrag);
     if (q.periodic)
-        k_learned_sweep<true><<<blocks, kTcThreads, smem, c->stream>>>(
-            static_cast<float *>(c->f), q.outer, q.L, q.inner, q.from_inner, q.cdiv, q.cmod, tab, frag, q.lo,
-            q.dvel, (float)c->g.alpha, use_net, f_snap, lgNL, ldv);
+        k_learned_walk<true><<<(unsigned)blocks, threads, smem, c->stream>>>(
+            static_cast<float *>(c->f), tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
     else
-        k_learned_sweep<false><<<blocks, kTcThreads, smem, c->stream>>>(
-            static_cast<float *>(c->f), q.outer, q.L, q.inner, q.from_inner, q.cdiv, q.cmod, tab, frag, q.lo,
-            q.dvel, (float)c->g.alpha, use_net, f_snap, lgNL, ldv);
+        k_learned_walk<false><<<(unsigned)blocks, threads, smem, c->stream>>>(
+            static_cast<float *>(c->f), tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
     return VP_OK;
@@ -1035,6 +974,15 @@ int vp_restrict_velocity(const float *f_fine, float *f_coarse, long long NX, int
     const long long n = NX * (nf1 / factor1) * (nf2 / factor2);
     k_restrict_v2<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         f_fine, f_coarse, NX, nf1, nf2, factor1, factor2);
+    return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}
+
+int vp_pair_coefs(const float *sc, const long long *li, const long long *ri, long long n, double importance,
+                  float *coef, double *weight, void *stream) {
+    if (!sc || !li || !ri || !coef || n < 0 || !(importance >= 0.0)) return VP_EINVAL;
+    if (n == 0) return VP_OK;
+    k_pair_coefs<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(sc, li, ri, n,
+                                                                                            importance, coef, weight);
     return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
 }
 

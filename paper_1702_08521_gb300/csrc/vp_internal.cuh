@@ -122,7 +122,6 @@ struct vp_ctx {
     int *d_flag;                        // non-finite flag
     long long launches;
     int *d_status;                      // device-side error word (bounded waits)
-    void *d_snap;                       // copy of f before a learned sweep (allocated on first use)
     void *d_netfrag;                    // network weights in MMA fragment order (allocated on first use)
     int learned_ready;                  // learned-sweep buffers allocated, kernel attributes set
     int opt_impl;                       // 0 auto, 1 staged, 2 TMA

@@ -138,13 +138,18 @@ __device__ __forceinline__ T dm4(T x, T y) {
 // of phi into [f_min, f_max] for every phi.  m4m / m4p are d^{M4} at the
 // upwind / downwind face of the upwind cell u0.
 template <typename T>
-__device__ __forceinline__ T mp_clamp(T phi, T um1, T u0, T u1, T alpha, T m4m, T m4p) {
+__device__ __forceinline__ void mp_lohi_carried(T um1, T u0, T u1, T alpha, T m4m, T m4p, T &lo, T &hi) {
     const T back = u0 - um1;
     const T ful = fma(alpha, back, u0);
     const T fmd = fma(T(0.5), u0 + u1, T(-0.5) * m4p);
     const T flc = fma(c43<T>(), m4m, fma(T(0.5), back, u0));
-    const T lo = fmax(min3(u0, u1, fmd), min3(u0, ful, flc));
-    const T hi = fmin(max3(u0, u1, fmd), max3(u0, ful, flc));
+    lo = fmax(min3(u0, u1, fmd), min3(u0, ful, flc));
+    hi = fmin(max3(u0, u1, fmd), max3(u0, ful, flc));
+}
+template <typename T>
+__device__ __forceinline__ T mp_clamp(T phi, T um1, T u0, T u1, T alpha, T m4m, T m4p) {
+    T lo, hi;
+    mp_lohi_carried(um1, u0, u1, alpha, m4m, m4p, lo, hi);
     return fmin(fmax(phi, lo), hi);
 }
 

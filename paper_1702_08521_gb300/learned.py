@@ -114,21 +114,24 @@ class Sampler:
             li = (base + torch.arange(Lc, device="cuda")).reshape(-1)
             ri = (base + right).reshape(-1)
             ok = torch.isfinite(y[li]) & torch.isfinite(y[ri])
-            li, ri = li[ok], ri[ok]
-            sl, sr = sc[li].double(), sc[ri].double()
-            sm = torch.maximum(sl, sr)
-            if keep and li.numel() > keep:
+            li, ri = li[ok].contiguous(), ri[ok].contiguous()
+            npair = li.numel()
+            # the pairs' loss coefficients and draw weights (library kernel)
+            coef = torch.empty(2 * npair, dtype=torch.float32, device="cuda")
+            wgt = torch.empty(npair, dtype=torch.float64, device="cuda")
+            V.vp_pair_coefs(sc, li, ri, npair, importance, coef, wgt, self.stream)
+            coef = coef.view(npair, 2)
+            if keep and npair > keep:
                 # draw on the GPU, seeded from the caller's generator
                 gen = torch.Generator(device="cuda")
                 gen.manual_seed(int(rng.integers(0, 2 ** 62)))
-                wgt = sm ** importance if importance > 0 else torch.ones_like(sm)
                 nz = int((wgt > 0).sum())
                 sel = torch.multinomial(wgt, min(keep, nz), replacement=False, generator=gen)
-                li, ri, sl, sr, sm = li[sel], ri[sel], sl[sel], sr[sel], sm[sel]
+                li, ri, coef = li[sel], ri[sel], coef[sel]
             idx = torch.stack([li, ri], dim=1).reshape(-1)
             Xv = X.view(ns, NFEAT)[idx]
             yv = y[idx]
-            cv = torch.stack([-(sl / sm), sr / sm], dim=1).reshape(-1).float()
+            cv = coef.reshape(-1)
         self.stream.synchronize()
         return Xv, yv, cv
 
@@ -274,6 +277,28 @@ def restricted_initial_state(dims: int, nx: int, nv_fine: int, factor: int, k: f
     fine.sync()
     fine.close()
     return out
+
+
+def run_sweeps(grid: dict, f0, dt: float, steps: int, wts, use_net: int, stream=None):
+    """The KDK run of vp_learned_step issued sweep by sweep (not graphed):
+    half kicks, learned drifts (x_D .. x_1) with the given use_net mode,
+    field solve, half kicks.  For accuracy comparisons of the modes."""
+    sim = V.Simulation(grid, precision=V.VP_F32, stream=stream)
+    sim.stream.wait_stream(sim.torch.cuda.current_stream())
+    with sim.torch.cuda.stream(sim.stream):
+        sim.f.copy_(f0.to(sim.f.dtype))
+    sim.field()
+    D = grid["dims"]
+    for _ in range(steps):
+        for d in range(D):
+            V.vp_kick_sweep(sim.ctx, d, 0.5 * dt, sim.accel[d * sim.NX:])
+        for d in reversed(range(D)):
+            V.vp_learned_sweep(sim.ctx, 0, d, dt, None, wts, use_net)
+        sim.field()
+        for d in range(D):
+            V.vp_kick_sweep(sim.ctx, d, 0.5 * dt, sim.accel[d * sim.NX:])
+    sim.sync()
+    return sim
 
 
 def run(grid: dict, f0, dt: float, steps: int, wts=None, stream=None, precision: int = V.VP_F32):

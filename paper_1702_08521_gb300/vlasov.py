@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_fine_flux": (I, [P, I, I, D, P, I, P]),
             "vp_fluxnet_line_map": (I, [GP, GP, I, I, I, P, P, P]),
             "vp_group_mean": (I, [P, LL, I, P, I, D, P, P]),
+            "vp_pair_coefs": (I, [P, P, P, LL, D, P, P, P]),
             "vp_restrict_velocity": (I, [P, P, LL, I, I, I, I, P]),
             "vp_make_samples": (I, [P, I, I, D, P, P, D, P, P, P]),
             "vp_net_grad": (I, [P, P, P, LL, I, P, P, P, P]),
@@ -410,6 +411,11 @@ def vp_group_mean(G_fine, n_coarse_lines: int, nout: int, map_dev, group: int, s
                   stream=None) -> None:
     _rc(load().vp_group_mean(_ptr(G_fine), n_coarse_lines, nout, _ptr(map_dev), group, scale,
                              _ptr(G_coarse), _sh(stream)), "group mean")
+
+
+def vp_pair_coefs(sc, li, ri, n: int, importance: float, coef, weight=None, stream=None) -> None:
+    _rc(load().vp_pair_coefs(_ptr(sc), _ptr(li), _ptr(ri), int(n), float(importance), _ptr(coef),
+                             _ptr(weight), _sh(stream)), "pair coefficients")
 
 
 def vp_restrict_velocity(f_fine, f_coarse, NX: int, nf1: int, nf2: int, factor1: int, factor2: int,
