@@ -263,11 +263,20 @@ def ensemble_bench(steps: int, warmup: int = 3):
     b.record(stream)
     V.vp_ensemble_sync(ens)
     ms = a.elapsed_time(b) / steps
+    # algorithmic bytes of a step: every sweep reads and writes each cell once
+    # (8 B per FP32 cell-update), the density moment reads each cell once (4 B)
+    alg = 8 * updates_per_step + 4 * cells
+    peak, peak_kind = peaks()
     out = {"workload": "ensemble 512 x 1D1V + 8 x 2D2V 64^2x64^2 (PCG64 seed 1702), FP32 MP7+PP, KDK",
            "runs": len(draws), "cells": cells, "steps": steps, "ms_per_step": ms,
            "value": updates_per_step / (ms / 1e3), "unit": "cell-updates/s",
            "launches_per_step": (V.vp_ensemble_launch_count(ens) - l0) / steps,
-           "tiles": V.vp_ensemble_get_tiles(ens)}
+           "tiles": V.vp_ensemble_get_tiles(ens),
+           "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "algorithmic_bytes_per_step": alg,
+                        "kernel": "k_ensemble (one persistent launch per step)",
+                        "peak_source": f"{peak_kind} HBM copy bandwidth",
+                        "working_set_gb": round(4 * cells / 1e9, 2)}}
     V.vp_ensemble_destroy(ens)
     del pool
     return out

@@ -298,7 +298,11 @@ __device__ void density_points(const float *pool, const RunDesc &r, long long x0
 
 // batched in-place radix-2 FFT of a row-major [n0][n1] (or [n0]) complex
 // array in shared memory along `axis`; sign -1 forward, +1 inverse (no 1/n)
-__device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sign) {
+// tw[j] = (cos, sin)(2 pi j / 256), j < 128: the twiddles of every power-of-two
+// length up to 256 (length len uses every (256 / len)-th entry)
+constexpr int kTwN = 256;
+
+__device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sign, const double2 *__restrict__ tw) {
     const int n = axis == 0 ? n0 : n1;
     const int lines = dims == 1 ? 1 : (axis == 0 ? n1 : n0);
     const int stride = (dims == 1 || axis == 1) ? 1 : n1;   // element stride along the axis
@@ -323,8 +327,8 @@ __device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sig
             const int l = t / (n / 2), b = t - l * (n / 2);
             const int grp = b / half, k = b - grp * half;
             const int i0 = grp * len + k, i1 = i0 + half;
-            double sn, cs;
-            sincospi((double)sign * 2.0 * (double)k / (double)len, &sn, &cs);
+            const double2 twk = tw[k * (kTwN / len)];
+            const double cs = twk.x, sn = sign < 0 ? -twk.y : twk.y;
             double2 *pu = a + l * lstride + i0 * stride, *pv = a + l * lstride + i1 * stride;
             const double2 u = *pu, v = *pv;
             const double2 tw = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
@@ -335,44 +339,23 @@ __device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sig
     }
 }
 
-__device__ double lap_eig(int order, double theta) {
-    // eigenvalue (times h^2) of the symmetric discrete Laplacian stencil of
-    // Eqs. C1, C5, C6: -(4 / den) sum_m b_m sin^2(m theta / 2)
-    double b1 = 1.0, b2 = 0.0, b3 = 0.0, den = 1.0;
-    if (order == 4) {
-        b1 = 16.0;
-        b2 = -1.0;
-        den = 12.0;
-    } else if (order == 6) {
-        b1 = 270.0;
-        b2 = -27.0;
-        b3 = 2.0;
-        den = 180.0;
-    }
-    const double s1 = sin(0.5 * theta), s2 = sin(theta), s3 = sin(1.5 * theta);
-    return -4.0 * (b1 * s1 * s1 + b2 * s2 * s2 + b3 * s3 * s3) / den;
-}
-
 // periodic Poisson + FDA force of one run, all in one CTA (NX <= 4096)
-__device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *acc_pool, double2 *a) {
+__device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *acc_pool, double2 *a,
+                            const double2 *__restrict__ tw, const double *__restrict__ green) {
     const int D = r.dims;
     const int n0 = r.nx[0], n1 = D == 2 ? r.nx[1] : 1;
     const long long NX = r.NX;
     for (long long x = threadIdx.x; x < NX; x += blockDim.x)
         a[x] = make_double2(ldcg(rho_pool + r.rho_off + x) - r.rho_bg, 0.0);
     __syncthreads();
-    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, -1);
-    const double kTwoPi = 6.283185307179586476925286766559;
+    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, -1, tw);
+    // S / lambda(k) / NX of the run, tabulated at creation (0 at k = 0)
     for (long long x = threadIdx.x; x < NX; x += blockDim.x) {
-        const int k0 = (int)(D == 2 ? x / n1 : x);
-        const int k1 = (int)(D == 2 ? x % n1 : 0);
-        double lam = lap_eig(r.pois_order, kTwoPi * (double)k0 / (double)n0) / (r.hx[0] * r.hx[0]);
-        if (D == 2) lam += lap_eig(r.pois_order, kTwoPi * (double)k1 / (double)n1) / (r.hx[1] * r.hx[1]);
-        const double sc = (k0 == 0 && k1 == 0) ? 0.0 : r.coupling / lam / (double)NX;
+        const double sc = green[r.rho_off + x];
         a[x] = make_double2(a[x].x * sc, a[x].y * sc);
     }
     __syncthreads();
-    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, +1);
+    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, +1, tw);
     // a = -grad phi by the 2/4/6-point FDA (Eqs. C9-C11)
     double c1 = 1.0, c2 = 0.0, c3 = 0.0, den = 2.0;
     if (r.pois_order == 4) {
@@ -385,18 +368,20 @@ __device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *ac
         c3 = 1.0;
         den = 60.0;
     }
+    const double sc0 = -1.0 / (den * r.hx[0]), sc1 = D == 2 ? -1.0 / (den * r.hx[1]) : 0.0;
     for (long long x = threadIdx.x; x < NX; x += blockDim.x) {
         const int i0 = (int)(D == 2 ? x / n1 : x);
         const int i1 = (int)(D == 2 ? x % n1 : 0);
         for (int d = 0; d < D; ++d) {
+            // power-of-two axes: periodic neighbours by masking
             auto at = [&](int off) -> double {
                 int j0 = i0, j1 = i1;
-                if (d == 0) j0 = ((i0 + off) % n0 + n0) % n0;
-                else j1 = ((i1 + off) % n1 + n1) % n1;
+                if (d == 0) j0 = (i0 + off) & (n0 - 1);
+                else j1 = (i1 + off) & (n1 - 1);
                 return a[j0 * n1 + j1].x;
             };
             const double g = c1 * (at(1) - at(-1)) + c2 * (at(2) - at(-2)) + c3 * (at(3) - at(-3));
-            acc_pool[r.acc_off + (long long)d * NX + x] = -g / (den * r.hx[d]);
+            acc_pool[r.acc_off + (long long)d * NX + x] = g * (d == 0 ? sc0 : sc1);
         }
     }
 }
@@ -407,7 +392,8 @@ __global__ void __launch_bounds__(kThreads) k_ensemble(float *__restrict__ pool,
                                                        const EnsItem *__restrict__ items, int nitems,
                                                        unsigned *__restrict__ ctr, double *acc_pool,
                                                        double *rho_pool, EnsParams P,
-                                                       int *__restrict__ status) {
+                                                       int *__restrict__ status, const double2 *__restrict__ tw,
+                                                       const double *__restrict__ green) {
     extern __shared__ __align__(16) unsigned char ens_smem[];
     __shared__ int s_item;
     __shared__ int s_ok;
@@ -450,7 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_ensemble(float *__restrict__ pool,
                 __threadfence_block();
                 __syncthreads();
             }
-            poisson_run(r, rho_pool, acc_pool, reinterpret_cast<double2 *>(ens_smem));
+            poisson_run(r, rho_pool, acc_pool, reinterpret_cast<double2 *>(ens_smem), tw, green);
         }
         __threadfence();
         __syncthreads();
@@ -489,6 +475,8 @@ struct vp_ens {
     float *pool;
     long long pool_cells;
     double *d_acc, *d_rho;
+    double2 *d_tw;     // FFT twiddles (kTwN / 2 entries)
+    double *d_green;   // per run: S / lambda(k) / NX at every Fourier mode (rho layout)
     long long acc_total, rho_total;
     RunDesc *d_runs;
     EnsItem *d_items_step, *d_items_field;
@@ -528,7 +516,7 @@ static int build_stages(RunDesc &r, int W, int R, int xpt, int &slot) {
         s.cls_from_inner = from_inner;
         s.cdiv = cdiv;
         s.cmod = cmod;
-        // tile width: the requested W, halved until the staged tile fits 36 KB
+        // tile width: the requested W, halved until the staged tile fits kTileBytes
         int w = W;
         while (w > 8 && (size_t)(L + (per ? 0 : 2 * VP_GHOST)) * w * sizeof(float) > kTileBytes) w /= 2;
         if (inner < w) w = (int)inner;
@@ -636,10 +624,12 @@ static int launch_pass(vp_ens *e, const EnsItem *items, int nitems, double dt) {
     const int grid = e->ctas_per_sm * e->sm_count;
     if (e->P.order == 7)
         k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
-                                                             e->d_acc, e->d_rho, P, e->d_status);
+                                                             e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
+                                                             e->d_green);
     else
         k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
-                                                             e->d_acc, e->d_rho, P, e->d_status);
+                                                             e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
+                                                             e->d_green);
     e->launches++;
     const cudaError_t er = cudaGetLastError();
     if (er != cudaSuccess) return ens_fail(e, VP_ECUDA, cudaGetErrorString(er));
@@ -724,6 +714,46 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
     }
     cudaMemset(e->d_acc, 0, sizeof(double) * aoff);
     cudaMemset(e->d_status, 0, sizeof(int));
+    {
+        // FFT twiddles and every run's Green factors S / lambda(k) / NX (the
+        // eigenvalues of the 2/4/6-point discrete Laplacians, Eqs. C1, C5, C6)
+        std::vector<double2> tw(kTwN / 2);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int j = 0; j < kTwN / 2; ++j) tw[j] = make_double2(std::cos(two_pi * j / kTwN), std::sin(two_pi * j / kTwN));
+        std::vector<double> green((size_t)roff, 0.0);
+        auto lap = [](int order, double theta) {
+            double b1 = 1.0, b2 = 0.0, b3 = 0.0, den = 1.0;
+            if (order == 4) {
+                b1 = 16.0;
+                b2 = -1.0;
+                den = 12.0;
+            } else if (order == 6) {
+                b1 = 270.0;
+                b2 = -27.0;
+                b3 = 2.0;
+                den = 180.0;
+            }
+            const double s1 = std::sin(0.5 * theta), s2 = std::sin(theta), s3 = std::sin(1.5 * theta);
+            return -4.0 * (b1 * s1 * s1 + b2 * s2 * s2 + b3 * s3 * s3) / den;
+        };
+        for (const RunDesc &r : e->runs) {
+            const int n0 = r.nx[0], n1 = r.dims == 2 ? r.nx[1] : 1;
+            for (long long x = 0; x < r.NX; ++x) {
+                const int k0 = (int)(x / n1), k1 = (int)(x % n1);
+                double lam = lap(r.pois_order, two_pi * k0 / n0) / (r.hx[0] * r.hx[0]);
+                if (r.dims == 2) lam += lap(r.pois_order, two_pi * k1 / n1) / (r.hx[1] * r.hx[1]);
+                green[(size_t)(r.rho_off + x)] = (k0 == 0 && k1 == 0) ? 0.0 : r.coupling / lam / (double)r.NX;
+            }
+        }
+        if (cudaMalloc(&e->d_tw, sizeof(double2) * tw.size()) != cudaSuccess ||
+            cudaMalloc(&e->d_green, sizeof(double) * green.size()) != cudaSuccess ||
+            cudaMemcpy(e->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(e->d_green, green.data(), sizeof(double) * green.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            vp_ensemble_destroy(e);
+            return VP_ENOMEM;
+        }
+    }
     int rc = upload_plan(e);
     if (rc) {
         vp_ensemble_destroy(e);
@@ -746,6 +776,8 @@ void vp_ensemble_destroy(vp_ens *e) {
     cudaStreamSynchronize(e->stream);
     cudaFree(e->d_acc);
     cudaFree(e->d_rho);
+    cudaFree(e->d_tw);
+    cudaFree(e->d_green);
     cudaFree(e->d_ctr);
     cudaFree(e->d_status);
     cudaFree(e->d_runs);
@@ -812,11 +844,11 @@ int vp_ensemble_field(vp_ens *e) {
         if (e->P.order == 7)
             k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
                                                                  (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status);
+                                                                 P, e->d_status, e->d_tw, e->d_green);
         else
             k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
                                                                  (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status);
+                                                                 P, e->d_status, e->d_tw, e->d_green);
         e->launches++;
         if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "field pass failed");
     }
