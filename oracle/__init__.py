@@ -128,6 +128,7 @@ def _load():
             "vpo_kick_sweep_rk": (I, [GP, P, I, D, P]),
             "vpo_drift_sweep": (I, [GP, P, I, D]),
             "vpo_kick_sweep": (I, [GP, P, I, D, P]),
+            "vpo_drift_unsplit": (I, [GP, P, D]),
             "vpo_density_moment": (None, [GP, P, P]),
             "vpo_poisson_solve": (I, [GP, P, P, P]),
             "vpo_diagnostics": (None, [GP, P, P, P, P, I, P]),
@@ -248,6 +249,14 @@ def kick_sweep(g: Grid, f: np.ndarray, dim: int, dt: float, accel_dim) -> None:
         raise ValueError("accel_dim must hold NX values")
     if _load().vpo_kick_sweep(ctypes.byref(g), _p(_check_f(g, f)), dim, dt, _p(a)) != 0:
         raise ValueError("bad kick sweep arguments")
+
+
+def drift_unsplit(g: Grid, f: np.ndarray, dt: float) -> None:
+    """In-place unsplit advection in physical space (Test-1d, reading R23):
+    f <- f + sum_d (A_d f - f), every A_d (the drift_sweep along x_d) applied
+    to the same f."""
+    if _load().vpo_drift_unsplit(ctypes.byref(g), _p(_check_f(g, f)), dt) != 0:
+        raise ValueError("bad unsplit drift arguments")
 
 
 def drift_sweep_rk(g: Grid, f: np.ndarray, dim: int, dt: float) -> None:

@@ -409,6 +409,39 @@ int vpo_kick_sweep(const vpo_grid *g, double *f, int dim, double dt, const doubl
     return 0;
 }
 
+/* Unsplit advection in physical space (Sec. 3.1, Test-1d; Sec. 2.4 names it
+ * as the alternative to directional splitting).  R23: the paper does not print
+ * the update it timed; the reading taken is the flux form with every
+ * direction's SL-MPP fluxes taken from f^n in one conservative update,
+ *   f^{n+1} = f^n + sum_d (A_d f^n - f^n),
+ * A_d f^n the 1D line update along x_d (Eq. 49, exactly what vpo_drift_sweep
+ * along d makes of f^n).  Each increment A_d f^n - f^n is a difference of
+ * interface masses along d, so the update conserves mass; it needs f^n kept
+ * whole while the increments are formed (the extra storage the paper cites).
+ * Positivity is not guaranteed: each direction's PP limiter allows a cell to
+ * lose half of itself through each face, i.e. up to D times its content over
+ * all 2D faces; the paper keeps the CFL number below 0.1 for this reason. */
+int vpo_drift_unsplit(const vpo_grid *g, double *f, double dt) {
+    if (!grid_ok(g)) return -1;
+    const long n = vpo_nx_total(g) * vpo_nv_total(g);
+    double *a = (double *)malloc(sizeof(double) * n);   /* A_d f^n */
+    double *inc = (double *)calloc(n, sizeof(double));  /* sum_d (A_d f^n - f^n) */
+    if (!a || !inc) {
+        free(a);
+        free(inc);
+        return -1;
+    }
+    for (int d = 0; d < g->dx; ++d) {
+        memcpy(a, f, sizeof(double) * n);
+        vpo_drift_sweep(g, a, d, dt);
+        for (long i = 0; i < n; ++i) inc[i] += a[i] - f[i];
+    }
+    for (long i = 0; i < n; ++i) f[i] += inc[i];
+    free(a);
+    free(inc);
+    return 0;
+}
+
 /* The sweeps above with RK--MPP5 in place of the SL update (Sec. 2.1.1);
  * -1 if any line's |c dt / Delta| >= 1/2 (those lines are left unchanged). */
 int vpo_drift_sweep_rk(const vpo_grid *g, double *f, int dim, double dt) {

@@ -84,6 +84,7 @@ int vpo_drift_sweep_rk(const vpo_grid *g, double *f, int dim, double dt);
 int vpo_kick_sweep_rk(const vpo_grid *g, double *f, int dim, double dt, const double *accel_dim);
 int vpo_drift_sweep(const vpo_grid *g, double *f, int dim, double dt);
 int vpo_kick_sweep(const vpo_grid *g, double *f, int dim, double dt, const double *accel_dim);
+int vpo_drift_unsplit(const vpo_grid *g, double *f, double dt);
 void vpo_density_moment(const vpo_grid *g, const double *f, double *rho);
 int vpo_poisson_solve(const vpo_grid *g, const double *rho, double *phi, double *accel);
 void vpo_diagnostics(const vpo_grid *g, const double *f, const double *rho, const double *phi,

@@ -121,6 +121,16 @@ def advect_1d(n: int, shape: int, order: int = 7, mp: int = 1, pp: int = 1,
                 ic=(IC_ADVECT, [float(shape)]))
 
 
+def advect_2d(n: int, shape: int, order: int = 7, mp: int = 1, pp: int = 1, n2: int = None) -> dict:
+    """Test-1d two-dimensional advection: n x n2 cells on the unit square,
+    periodic, one velocity cell per axis centred on (c_x, c_y) = (1, 0.5)."""
+    n2 = n if n2 is None else n2
+    return dict(name=f"advect_2d_{n}x{n2}",
+                grid=_grid(2, [n, n2], [1, 1], [0.0, 0.0], [1.0, 1.0], [0.5, 0.0], [1.5, 1.0], order=order,
+                           mp=mp, pp=pp),
+                ic=(IC_ADVECT, [float(shape)]))
+
+
 def random_f(shape, seed: int, *, zeros: float = 0.3, dtype=np.float64) -> np.ndarray:
     """Non-negative structured noise: a smooth bump field times a random mask
     with exact zeros, plus small-scale noise (stresses MP and PP branches)."""

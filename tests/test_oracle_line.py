@@ -209,3 +209,114 @@ def test_oracle_grid_struct_matches_its_header():
     defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define\s+VPO_(\w+)\s+(-?\d+)", src, flags=re.M)}
     for n in ("IC_LANDAU", "IC_TWOSTREAM", "IC_PLUMMER", "IC_ADVECT", "IC_SPHERE", "BC_PERIODIC", "BC_OUTFLOW"):
         assert getattr(O, n) == defs[n], n
+
+
+# ---- unsplit advection (Test-1d, reading R23) --------------------------------
+
+def _g2(n, order=7, n2=None, **kw):
+    return O.grid(**{**inputs.advect_2d(n, 1, order=order, n2=n2)["grid"], **kw})
+
+
+@pytest.mark.parametrize("order", [5, 7])
+def test_unsplit_on_product_data_is_the_sum_of_the_1d_increments(order):
+    """For f = g(x) h(y) with g, h > 0 every x line is h_j g and every y line
+    g_i h, and the SL-MPP update (CSL flux, MP bounds, PP clamp) is positively
+    homogeneous, so the unsplit step is h A_x g + g A_y h - g h with A_x, A_y
+    the 1D line updates, while a split step would give (A_x g)(A_y h).
+    Shifts with integer parts and both signs (c = (1, -0.5) scaled by dt)."""
+    n1, n2 = 23, 17
+    g = O.grid(2, [n1, n2], [1, 1], [0, 0], [1, 1], [0.5, -1.0], [1.5, 0.0], order=order)
+    rng = np.random.default_rng(41)
+    gx = 0.2 + rng.random(n1) ** 2
+    hy = 0.2 + rng.random(n2) ** 2
+    gx[5:8] = gx[5]  # a flat run (the MP bounds collapse there)
+    for dt in (0.37 / n1, 2.71 / n1):
+        f = np.outer(gx, hy).ravel().copy()
+        O.drift_unsplit(g, f, dt)
+        ax = O.advect_line(gx, 1.0 * dt * n1, order=order)
+        ay = O.advect_line(hy, -0.5 * dt * n2, order=order)
+        want = np.outer(ax, hy) + np.outer(gx, ay) - np.outer(gx, hy)
+        assert np.allclose(f.reshape(n1, n2), want, rtol=0, atol=1e-14)
+        split = np.outer(ax, ay)
+        assert np.abs(split - want).max() > 1e-4  # the cross term the unsplit step drops
+
+
+def test_unsplit_equals_split_on_sum_separable_data():
+    """f = 1 + (sin 2 pi x + sin 2 pi y) / 2 (Eq. 66): an x line is a 1D profile
+    plus a constant, which the x update carries unchanged, so unsplit and split
+    steps both give A_x g + A_y h (to rounding) -- the reason the paper sees
+    the same errors with both on its Test-1d profiles."""
+    g = _g2(24)
+    f0 = O.init_f(g, O.IC_ADVECT, [1.0])
+    fu, fs = f0.copy(), f0.copy()
+    dt = 0.02 / 24
+    for _ in range(30):
+        O.drift_unsplit(g, fu, dt)
+        O.drift_sweep(g, fs, 1, dt)
+        O.drift_sweep(g, fs, 0, dt)
+    assert np.abs(fu - fs).max() < 1e-13
+    assert np.abs(fu - f0).max() > 1e-2
+
+
+@pytest.mark.parametrize("order,slope", [(5, 4.8), (7, 6.8)])
+def test_unsplit_sine_order_at_the_papers_cfl(order, slope):
+    """Test-1d with the unsplit method at nu = 0.02 (Sec. 3.1): the 2D sine keeps
+    the scheme's spatial order, N = 16, 32, 64 to t = 0.5."""
+    def err(n):
+        g = _g2(n, order)
+        f = O.init_f(g, O.IC_ADVECT, [1.0])
+        dt = 0.02 / n
+        steps = int(round(0.5 / dt))
+        for _ in range(steps):
+            O.drift_unsplit(g, f, dt)
+        x, y, t = g.x_centres(0)[:, None], g.x_centres(1)[None, :], steps * dt
+        ex = 1 + 0.5 * np.sin(2 * np.pi * (x - t)) + 0.5 * np.sin(2 * np.pi * (y - 0.5 * t))
+        return np.abs(f.reshape(n, n) - ex).sum() / np.abs(ex).sum()
+    errs = [err(n) for n in (16, 32, 64)]
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(slopes >= slope), (errs, slopes)
+
+
+def test_unsplit_rectangle_needs_the_small_cfl():
+    """Test-1d rectangle (Eq. 65), N = 32, t = 0.25: at nu = 0.02 the unsplit
+    method stays within [0, 1]; at nu = 0.45 it overshoots and goes negative
+    (the paper keeps nu below 0.1 for the unsplit runs), while the split
+    sweeps stay non-negative at any nu."""
+    def run(nu, unsplit):
+        g = _g2(32)
+        f = O.init_f(g, O.IC_ADVECT, [0.0])
+        dt = nu / 32
+        for _ in range(int(round(0.25 / dt))):
+            if unsplit:
+                O.drift_unsplit(g, f, dt)
+            else:
+                O.drift_sweep(g, f, 1, dt)
+                O.drift_sweep(g, f, 0, dt)
+        return f
+    f = run(0.02, True)
+    assert f.min() >= 0.0 and f.max() <= 1.0
+    f = run(0.45, True)
+    assert f.min() < -1e-5 and f.max() > 1.05
+    assert run(0.45, False).min() >= 0.0
+
+
+def test_unsplit_conserves_mass_and_constants():
+    """Periodic space: sum f is kept to rounding (each increment is a
+    difference of interface masses); a constant stays constant.  2D2V and 3D
+    space with several velocities per axis."""
+    rng = np.random.default_rng(5)
+    for dims, nx, nv in ((2, [12, 9], [4, 3]), (3, [6, 5, 7], [2, 3, 2])):
+        g = O.grid(dims, nx, nv, [0.0] * dims, [1.0] * dims, [-2.0] * dims, [2.0] * dims, order=7)
+        f = inputs.random_f(g.NX * g.NV, seed=9)
+        m0 = f.sum()
+        for dt in (0.013, 0.21):
+            O.drift_unsplit(g, f, dt)
+        assert abs(f.sum() - m0) < 1e-12 * m0
+        c = np.full(g.NX * g.NV, 0.375)
+        O.drift_unsplit(g, c, 0.3)
+        assert np.all(c == 0.375)
+    g = O.grid(2, [8, 8], [2, 2], [0, 0], [1, 1], [-1, -1], [1, 1], xbc=O.BC_OUTFLOW)
+    f = rng.random(g.NX * g.NV)
+    m0 = f.sum()
+    O.drift_unsplit(g, f, 0.05)
+    assert f.sum() < m0  # zero inflow: mass leaves through the boundaries
