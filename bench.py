@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--learned-draws", type=int, default=64)
     p.add_argument("--ensemble-steps", type=int, default=20)
     p.add_argument("--no-schemes", action="store_true", help="skip the SL-MPP5 / RK-MPP5 sweep comparison")
+    p.add_argument("--no-unsplit", action="store_true", help="skip the split / unsplit Test-1d step comparison")
     p.add_argument("--collapse", action="store_true",
                    help="add the Sec. 3.4 uniform-sphere collapse (64^3 x 32^3 to t = 8T)")
     p.add_argument("--convergence", action="store_true",
@@ -362,6 +363,71 @@ def scheme_compare_bench(sim, cfg, reps: int = 2):
     tot = {k: sum(r[k + "_ms"] for r in out.values()) for k in ("sl_mpp5", "rk_mpp5")}
     out["all_kinds"] = {"sl_mpp5_ms": round(tot["sl_mpp5"], 4), "rk_mpp5_ms": round(tot["rk_mpp5"], 4),
                         "ratio": round(tot["rk_mpp5"] / tot["sl_mpp5"], 3)}
+    return out
+
+
+def unsplit_bench(cases=((512, 1, 400), (4096, 1, 100), (4096, 2, 40)), reps: int = 3):
+    """Test-1d cost comparison (Sec. 3.1): time per step of the split step (x2
+    sweep then x1 sweep, each its shift table and sweep launch) and of the
+    unsplit step (one launch from f^n into a second array, ping-pong) on the
+    2D sine (Eq. 66) at nu = 0.02 for c_x = 1, FP32 SL-MPP7 with MP and PP.
+    Cases (n, velocity cells per axis, steps): 512^2 is the paper's largest
+    mesh (1 MB, L2-resident: launch-bound on both sides); 4096^2 (67 MB, two
+    arrays of it in the unsplit ping-pong); 4096^2 x 2^2 velocities (four
+    Test-1d problems at once, 268 MB, larger than L2: HBM-bound).  Best of
+    `reps` timed runs (CUDA events on the library stream) after a warm-up that
+    also tunes the sweeps.  Algorithmic bytes per step: 2 x 4 B per cell
+    unsplit (f^n in, f^{n+1} out), 2 x 2 x 4 B split (two in-place sweeps)."""
+    import torch
+    from paper_1702_08521_gb300 import inputs
+    from paper_1702_08521_gb300 import vlasov as V
+    peak, kind = peaks()
+    out = {}
+    for n, nv, k in cases:
+        cfg = inputs.advect_2d(n, 1, nv=nv)
+        sim = V.Simulation(cfg["grid"], precision=V.VP_F32)
+        V.vp_init_f(sim.ctx, *cfg["ic"])
+        sc = torch.empty_like(sim.f)
+        dt = 0.02 / n
+
+        def split(m):
+            for _ in range(m):
+                V.vp_drift_sweep(sim.ctx, 1, dt)
+                V.vp_drift_sweep(sim.ctx, 0, dt)
+
+        def unsplit(m):
+            V.vp_drift_unsplit(sim.ctx, dt, m, sc)
+
+        ncell = n * n * nv * nv
+        row = {"cells": ncell, "steps": k}
+        for name, fn in (("split", split), ("unsplit", unsplit)):
+            fn(4)
+            sim.sync()
+            best = 1e30
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(sim.stream)
+                fn(k)
+                b.record(sim.stream)
+                b.synchronize()
+                best = min(best, a.elapsed_time(b) / k)
+            sim.sync()
+            row[name + "_ms_per_step"] = round(best, 5)
+            nbytes = (8 if name == "unsplit" else 16) * ncell
+            row[name + "_gbs"] = round(nbytes / (best * 1e-3) / 1e9, 1)
+        row["unsplit_over_split"] = round(row["unsplit_ms_per_step"] / row["split_ms_per_step"], 3)
+        if ncell * 4 > 129e6:
+            row["roofline_unsplit"] = {"bound": "hbm", "achieved": row["unsplit_gbs"], "peak": peak,
+                                       "unit": "GB/s", "frac": round(row["unsplit_gbs"] / peak, 4),
+                                       "peak_source": f"{kind} HBM copy bandwidth"}
+            row["l2"] = "inputs larger than L2"
+        elif ncell * 8 > 129e6:
+            row["l2"] = "one array fits L2, the two of the ping-pong do not"
+        else:
+            row["l2"] = "L2-resident: launch-bound"
+        out[cfg["name"]] = row
+        del sc
+        sim.close()
     return out
 
 
@@ -785,6 +851,13 @@ def main():
         except Exception as ex:  # reported, not hidden
             schemes = {"error": str(ex)[:300]}
 
+    unspl = None
+    if not args.no_unsplit and rank == 0:
+        try:
+            unspl = unsplit_bench()
+        except Exception as ex:  # reported, not hidden
+            unspl = {"error": str(ex)[:300]}
+
     # end to end through the C ABI with host buffers: H2D f, one step, D2H f
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -856,7 +929,7 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
                "sweeps": per_kind, "tuning": tuning, "ensemble": ens, "l2_resident": l2res, "learned": lrn,
-               "convergence": conv, "collapse": coll, "rk_vs_sl": schemes,
+               "convergence": conv, "collapse": coll, "rk_vs_sl": schemes, "unsplit_vs_split": unspl,
                "e2e": e2e,
                "cpu_baseline": cpu}
         print(json.dumps(out))

@@ -162,6 +162,27 @@ int vp_drift_sweep(vp_ctx *ctx, int dim, double dt);
  */
 int vp_kick_sweep(vp_ctx *ctx, int dim, double dt, const double *accel_dev);
 
+/*
+ * vp_drift_unsplit -- nsteps unsplit steps of the advection in physical space
+ * (the alternative to directional splitting of Sec. 2.4, compared in Test-1d
+ * of Sec. 3.1): every step forms both directions' SL-MPP increments from the
+ * same f^n,
+ *     f^{n+1} = f^n + (A_1 f^n - f^n) + (A_2 f^n - f^n),
+ * A_d the line update of vp_drift_sweep(d, dt) (Eq. 49 with the grid's MP
+ * constraint and PP limiter).  Mass is conserved on a periodic box;
+ * positivity is not guaranteed (each direction's PP limiter bounds what a
+ * face takes, not what four faces take together), which is why the paper runs
+ * it at CFL numbers below 0.1.
+ * scratch_dev: caller-owned device array of vp_num_cells elements of the
+ * grid's precision, 16-byte aligned, not overlapping f; the steps alternate
+ * between f and scratch_dev and the result ends in f (an odd nsteps adds one
+ * device copy).  scratch_dev's contents afterwards are unspecified.
+ * VP_ENOTSUP unless the grid has two spatial dimensions and the SL scheme, or
+ * if a line moves by more than 4 whole cells per step; VP_EINVAL for a NULL,
+ * misaligned or overlapping scratch_dev, nsteps < 0 or a non-finite dt.
+ */
+int vp_drift_unsplit(vp_ctx *ctx, double dt, int nsteps, void *scratch_dev);
+
 /* rho_dev[x] = sum_v f dV (Eq. 3 on the mesh), NX doubles, computed from the
  * float/double f with double-precision accumulation. */
 int vp_density_moment(vp_ctx *ctx, double *rho_dev);

@@ -257,6 +257,9 @@ int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out) {
     c->wp = vp_csl_weight_polys(c->g.order);
     long long ncls = c->NX;
     for (int d = 0; d < c->g.dv; ++d) ncls = c->g.nv[d] > ncls ? c->g.nv[d] : ncls;
+    long long nvsum = 0;  // the unsplit step's tables of every drift axis
+    for (int d = 0; d < c->g.dv; ++d) nvsum += c->g.nv[d];
+    ncls = nvsum > ncls ? nvsum : ncls;
     c->shift_cap = ncls;
     const size_t shift_bytes = (size_t)ncls * (c->esize == 4 ? sizeof(LineShift<float>) : sizeof(LineShift<double>));
 #define ALLOC(p, bytes)                                                     \

@@ -218,6 +218,34 @@ __device__ __forceinline__ T pp_clamp(T M, T h0, T h1) {
     return fmin(fmax(M, -h1), h0);
 }
 
+// The PP limiter in its theta form (Eqs. 15-23), as the mass nu Phi^, for an
+// interface next to a negative cell, where the clamp above is not the theta
+// blend (the unsplit step can leave cells below zero).  A binding theta is
+// scaled by (1 - 8 eps) and clamped to [0, 1]; a non-positive denominator
+// gives theta = 0, the upwind flux.
+template <typename T>
+__device__ __forceinline__ T pp_theta_mass(T phibar, T u0, T u1, T nu) {
+    const T tn = T(2) * nu;
+    const T up = u0 - tn * phibar, up_up = u0 - tn * u0;
+    const T um = u1 + tn * phibar, um_up = u1 + tn * u0;
+    T thp = T(1), thm = T(1);
+    bool binds = false;
+    if (up < T(0)) {
+        const T den = up_up - up;
+        thp = den > T(0) ? up_up / den : T(0);
+        binds = true;
+    }
+    if (um < T(0)) {
+        const T den = um_up - um;
+        thm = den > T(0) ? um_up / den : T(0);
+        binds = true;
+    }
+    T th = fmin(thp, thm);
+    if (binds) th *= T(1) - T(8) * (sizeof(T) == 4 ? T(5.9604644775390625e-8) : T(1.1102230246251565e-16));
+    th = fmin(fmax(th, T(0)), T(1));
+    return nu * (th * phibar + (T(1) - th) * u0);
+}
+
 // Interface mass on the upwind-ordered stencil (u0 = upwind cell): the CSL
 // flux, the MP constraint, times nu, then the PP limiter.  FULL: MP and PP
 // both on, so the runtime switches drop out of the loop.
@@ -283,9 +311,11 @@ __device__ __forceinline__ T flux_walk(const SH &sh, T um3, T um2, T um1, T u0, 
 // constrained flux is u_0 exactly (all MP bounds collapse onto u_0, d^{M4} at
 // the downwind face is 0) and the warp skips the interpolant and the bounds.
 // The update is the flux form of Eq. 49 in masses, f' = (u - M_out) + M_in.
-// store(i, v) writes the new value of cell i.
+// store(i, v) writes the new value of cell i.  NEG: interfaces next to a
+// negative cell take the PP limiter's theta form (pp_theta_mass) instead of
+// the clamp (scalar T only).
 
-template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, typename Store, typename SH>
+template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, bool NEG = false, typename Store, typename SH>
 __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, const SH &sh,
                                      int r0, int r1, T alpha, int mp, int pp, Store store) {
     if (r0 >= r1) return;
@@ -332,9 +362,18 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
     // hc: rounded-down half of the cell the walk is on (the upwind cell of its
     // outgoing interface)
     T hc = (FULL || pp) ? half_rd(w[4]) : T(0);
-    T fin = mul_rn(nu, flux_walk<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, mp,
-                                                 m4m, m4p));
-    if (FULL || pp) fin = pp_clamp(fin, half_rd(w[3]), hc);
+    const T phi0 = flux_walk<T, ORDER, FULL>(sh, w[0], w[1], w[2], w[3], w[4], w[5], w[6], alpha, mp, m4m, m4p);
+    T fin = mul_rn(nu, phi0);
+    if (FULL || pp) {
+        if constexpr (NEG) {
+            if (w[3] < T(0) || w[4] < T(0))
+                fin = pp_theta_mass(phi0, w[3], w[4], nu);
+            else
+                fin = pp_clamp(fin, half_rd(w[3]), hc);
+        } else {
+            fin = pp_clamp(fin, half_rd(w[3]), hc);
+        }
+    }
     if (FULL || mp) {
         dc = curv(w[3], w[4], w[5]);
         m4m = m4p;
@@ -369,7 +408,14 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
         T fout = mul_rn(nu, phi);                                                                 \
         if (FULL || pp) {                                                                         \
             const T hn = half_rd(u1_);                                                            \
-            fout = pp_clamp(fout, hc, hn);                                                        \
+            if constexpr (NEG) {                                                                  \
+                if (u0_ < T(0) || u1_ < T(0))                                                     \
+                    fout = pp_theta_mass(phi, u0_, u1_, nu);                                      \
+                else                                                                              \
+                    fout = pp_clamp(fout, hc, hn);                                                \
+            } else {                                                                              \
+                fout = pp_clamp(fout, hc, hn);                                                    \
+            }                                                                                     \
             hc = hn;                                                                              \
         }                                                                                         \
         store(i, (u0_ - fout) + fin);                                                             \

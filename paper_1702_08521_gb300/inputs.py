@@ -121,12 +121,16 @@ def advect_1d(n: int, shape: int, order: int = 7, mp: int = 1, pp: int = 1,
                 ic=(IC_ADVECT, [float(shape)]))
 
 
-def advect_2d(n: int, shape: int, order: int = 7, mp: int = 1, pp: int = 1, n2: int = None) -> dict:
+def advect_2d(n: int, shape: int, order: int = 7, mp: int = 1, pp: int = 1, n2: int = None,
+              nv: int = 1) -> dict:
     """Test-1d two-dimensional advection: n x n2 cells on the unit square,
-    periodic, one velocity cell per axis centred on (c_x, c_y) = (1, 0.5)."""
+    periodic, velocity range [0.5, 1.5] x [0, 1] in nv x nv cells (nv = 1: the
+    single velocity (c_x, c_y) = (1, 0.5) of the paper; nv = 2: four such
+    problems at once, (c_x, c_y) in {0.75, 1.25} x {0.25, 0.75})."""
     n2 = n if n2 is None else n2
-    return dict(name=f"advect_2d_{n}x{n2}",
-                grid=_grid(2, [n, n2], [1, 1], [0.0, 0.0], [1.0, 1.0], [0.5, 0.0], [1.5, 1.0], order=order,
+    tag = "" if nv == 1 else f"x{nv}x{nv}"
+    return dict(name=f"advect_2d_{n}x{n2}{tag}",
+                grid=_grid(2, [n, n2], [nv, nv], [0.0, 0.0], [1.0, 1.0], [0.5, 0.0], [1.5, 1.0], order=order,
                            mp=mp, pp=pp),
                 ic=(IC_ADVECT, [float(shape)]))
 

@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_upload_f": (I, [P, P, ctypes.c_size_t]),
             "vp_download_f": (I, [P, P, ctypes.c_size_t]),
             "vp_drift_sweep": (I, [P, I, D]),
+            "vp_drift_unsplit": (I, [P, D, I, P]),
             "vp_kick_sweep": (I, [P, I, D, P]),
             "vp_density_moment": (I, [P, P]),
             "vp_poisson_solve": (I, [P, P, P, P]),
@@ -227,6 +228,10 @@ def vp_download_f(ctx, host, nbytes: int) -> None:
 
 def vp_drift_sweep(ctx, dim: int, dt: float) -> None:
     _check(ctx, load().vp_drift_sweep(ctx, dim, dt))
+
+
+def vp_drift_unsplit(ctx, dt: float, nsteps: int, scratch) -> None:
+    _check(ctx, load().vp_drift_unsplit(ctx, dt, nsteps, _ptr(scratch)))
 
 
 def vp_kick_sweep(ctx, dim: int, dt: float, accel) -> None:
