@@ -221,6 +221,8 @@ int enqueue_step(vp_ctx *c, double dt, int split, double *acc, const float *wts)
 
 }  // namespace
 
+bool vp_capturing(const vp_ctx *c) { return capturing(c); }
+
 extern "C" {
 
 int vp_create(const vp_grid *grid, void *cuda_stream, vp_ctx **out) {
@@ -402,6 +404,7 @@ int vp_set_option(vp_ctx *c, int option, long long value) {
     }
     for (int k = 0; k < 2; ++k)
         for (int d = 0; d < 3; ++d) c->tune[k][d].valid = 0;
+    c->utune[0].valid = c->utune[1].valid = 0;
     if (c->graph.valid) {
         cudaGraphExecDestroy(c->graph.exec);
         c->graph.valid = 0;

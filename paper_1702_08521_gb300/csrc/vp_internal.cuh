@@ -77,6 +77,13 @@ struct SweepTune {
     int W, nseg, ctas_per_sm;
 };
 
+// tile of the unsplit step (T1 x1 rows x T2 x2 cells x TV velocity cells,
+// `threads` per CTA), one per halo width (4 or 8 cells)
+struct UnsplitTune {
+    int valid;
+    int T1, T2, TV, threads;
+};
+
 struct LimParams {
     double alpha;
     int mp, pp;
@@ -128,6 +135,7 @@ struct vp_ctx {
     int opt_autotune;                   // 1: time candidate tiles on first use
     unsigned opt_wait_limit;            // iterations of each bounded device-side wait
     SweepTune tune[2][3];               // [kick][dim]
+    UnsplitTune utune[2];               // unsplit step, [halo of 8 cells]
     vp_graph_cache graph;
     char err[256];
 };
@@ -180,6 +188,8 @@ inline SweepGeo vp_make_geo(const vp_ctx *c, int kick, int dim) {
 
 // launchers implemented in the kernel files; all enqueue on ctx->stream
 int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double *accel);
+// the context stream is being captured into a graph (no synchronising calls)
+bool vp_capturing(const vp_ctx *c);
 // buffers and kernel attributes of the learned sweep (outside any stream capture)
 int vp_learned_prepare(vp_ctx *c);
 // RK-MPP5 sweeps: kernel attributes once per process, one sweep (table + fused stages)

@@ -222,9 +222,10 @@ __device__ __forceinline__ T pp_clamp(T M, T h0, T h1) {
 // interface next to a negative cell, where the clamp above is not the theta
 // blend (the unsplit step can leave cells below zero).  A binding theta is
 // scaled by (1 - 8 eps) and clamped to [0, 1]; a non-positive denominator
-// gives theta = 0, the upwind flux.
+// gives theta = 0, the upwind flux.  Kept out of line so that the rare call
+// stays a branch rather than work predicated into every interface.
 template <typename T>
-__device__ __forceinline__ T pp_theta_mass(T phibar, T u0, T u1, T nu) {
+__device__ __noinline__ T pp_theta_mass(T phibar, T u0, T u1, T nu) {
     const T tn = T(2) * nu;
     const T up = u0 - tn * phibar, up_up = u0 - tn * u0;
     const T um = u1 + tn * phibar, um_up = u1 + tn * u0;

@@ -36,7 +36,8 @@ namespace {
 
 using vp_core::walk;
 
-constexpr int kThreads = 256;
+constexpr int kMaxThreads = 256;
+constexpr int kMaxSmem = 100 * 1024;
 
 struct UnsplitGeo {
     int n1, n2, NV;     // cells along x1 and x2; velocity cells per spatial point
@@ -64,29 +65,36 @@ __device__ __forceinline__ int wrap(int x, int n) {
     return x < 0 ? x + n : x;
 }
 
-// phase A: D[i] = A_1 f^n - f^n at row i of a column (c: the column's f^n)
+// phase A: D = A_1 f^n - f^n along a column (c: the column's f^n), cells in
+// walk order (running pointers, steps sigma * pitch)
 template <typename T>
 struct StoreA {
     T *d;
     const T *c;
-    int dp, p;
-    __device__ __forceinline__ void operator()(int i, T a) { d[i * dp] = a - c[i * p]; }
+    int sd, sc;
+    __device__ __forceinline__ void operator()(int, T a) {
+        *d = a - *c;
+        d += sd;
+        c += sc;
+    }
 };
 
-// phase B: D[j] <- f^n + (D[j] + (A_2 f^n - f^n)) at cell j of an x2 line
+// phase B: D <- f^n + (D + (A_2 f^n - f^n)) along an x2 line, in walk order
 template <typename T>
 struct StoreB {
     T *d;
     const T *c;
-    int tv;
-    __device__ __forceinline__ void operator()(int j, T a) {
-        const T fc = c[j * tv];
-        d[j * tv] = fc + (d[j * tv] + (a - fc));
+    int s;
+    __device__ __forceinline__ void operator()(int, T a) {
+        const T fc = *c;
+        *d = fc + (*d + (a - fc));
+        d += s;
+        c += s;
     }
 };
 
 template <typename T, int ORDER, bool FULL, int G>
-__global__ void __launch_bounds__(kThreads) k_unsplit2(const T *__restrict__ fin, T *__restrict__ fout,
+__global__ void __launch_bounds__(kMaxThreads) k_unsplit2(const T *__restrict__ fin, T *__restrict__ fout,
                                                        const LineShift<T> *__restrict__ tab, UnsplitGeo u,
                                                        LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -98,12 +106,39 @@ __global__ void __launch_bounds__(kThreads) k_unsplit2(const T *__restrict__ fin
     const int t2 = (int)(b % (unsigned)u.tiles2);
     const int t1 = (int)(b / (unsigned)u.tiles2);
     const int r0 = t1 * u.T1, j0 = t2 * u.T2, v0 = tvi * u.TV;
+    const int nt = blockDim.x;
 
     // stage rows r0 - G .. r0 + T1 + G - 1, x2 cells j0 - G .. j0 + T2 + G - 1,
     // velocities v0 .. v0 + TV - 1 (a ragged velocity tile stages zeros)
-    {
+    const long long rs = (long long)u.n2 * u.NV;  // row stride of f
+    const bool allv = u.TV == u.NV;
+    if (allv && r0 >= G && r0 + u.T1 + G <= u.n1 && j0 >= G && j0 + u.T2 + G <= u.n2) {
+        // interior tile with every velocity: each staged row is one contiguous
+        // run of f^n, no wrap and no zero fill
         const int SW = (u.T2 + 2 * G) * u.TV, SR = u.T1 + 2 * G;
-        const int dr = (int)fdiv(kThreads, u.fd_sw), dq = kThreads - dr * SW;
+        const int dr = (int)fdiv((unsigned)nt, u.fd_sw), dq = nt - dr * SW;
+        int rr = (int)fdiv(threadIdx.x, u.fd_sw), q = threadIdx.x - rr * SW;
+        const T *gp = fin + (long long)(r0 - G) * rs + (long long)(j0 - G) * u.NV + rr * rs + q;
+        T *sp = sm + rr * u.P + q;
+        const long long gstep = dr * rs + dq, gwrap = rs - SW;
+        const int sstep = dr * u.P + dq, swrap = u.P - SW;
+        for (; rr < SR;) {
+            cp_async_elem(sp, gp);
+            rr += dr;
+            q += dq;
+            gp += gstep;
+            sp += sstep;
+            if (q >= SW) {
+                q -= SW;
+                ++rr;
+                gp += gwrap;
+                sp += swrap;
+            }
+        }
+        vp_tma::cp_async_wait_all();
+    } else {
+        const int SW = (u.T2 + 2 * G) * u.TV, SR = u.T1 + 2 * G;
+        const int dr = (int)fdiv((unsigned)nt, u.fd_sw), dq = nt - dr * SW;
         int rr = (int)fdiv(threadIdx.x, u.fd_sw), q = threadIdx.x - rr * SW;
         for (; rr < SR;) {
             const int jj = (int)fdiv((unsigned)q, u.fd_tv), tv = q - jj * u.TV;
@@ -136,37 +171,63 @@ __global__ void __launch_bounds__(kThreads) k_unsplit2(const T *__restrict__ fin
     // A: x1 columns
     {
         const int cols = u.T2 * u.TV, items = cols * u.nsegA;
-        for (int it = threadIdx.x; it < items; it += kThreads) {
+        for (int it = threadIdx.x; it < items; it += nt) {
             const int seg = it / cols, col = it - seg * cols;
             const int jj = col / u.TV, tv = col - jj * u.TV;
             const int v = min(v0 + tv, u.NV - 1);
             const LineShift<T> sh = tab[(v / u.vs0) % u.nv0];
             const int ra = seg * u.T1 / u.nsegA, rb = (seg + 1) * u.T1 / u.nsegA;
+            const int i0 = sh.sigma > 0 ? ra : rb - 1;
             const T *c0 = sm + G * u.P + (jj + G) * u.TV + tv;
-            walk<T, ORDER, false, FULL, G, true>(c0, u.P, u.T1, sh, ra, rb, alpha, lp.mp, lp.pp,
-                                           StoreA<T>{D + col, c0, u.DP, u.P});
+            walk<T, ORDER, false, FULL, G, true>(
+                c0, u.P, u.T1, sh, ra, rb, alpha, lp.mp, lp.pp,
+                StoreA<T>{D + col + i0 * u.DP, c0 + i0 * u.P, sh.sigma * u.DP, sh.sigma * u.P});
         }
     }
     __syncthreads();
     // B: x2 lines
     {
         const int lines = u.T1 * u.TV, items = lines * u.nsegB;
-        for (int it = threadIdx.x; it < items; it += kThreads) {
+        for (int it = threadIdx.x; it < items; it += nt) {
             const int seg = it / lines, l = it - seg * lines;
             const int r = l / u.TV, tv = l - r * u.TV;
             const int v = min(v0 + tv, u.NV - 1);
             const LineShift<T> sh = tab[u.nv0 + (v / u.vs1) % u.nv1];
             const int ja = seg * u.T2 / u.nsegB, jb = (seg + 1) * u.T2 / u.nsegB;
+            const int j0w = sh.sigma > 0 ? ja : jb - 1;
             const T *l0 = sm + (r + G) * u.P + G * u.TV + tv;
-            walk<T, ORDER, false, FULL, G, true>(l0, u.TV, u.T2, sh, ja, jb, alpha, lp.mp, lp.pp,
-                                           StoreB<T>{D + r * u.DP + tv, l0, u.TV});
+            walk<T, ORDER, false, FULL, G, true>(
+                l0, u.TV, u.T2, sh, ja, jb, alpha, lp.mp, lp.pp,
+                StoreB<T>{D + r * u.DP + tv + j0w * u.TV, l0 + j0w * u.TV, sh.sigma * u.TV});
         }
     }
     __syncthreads();
     // C: f^{n+1} out
-    {
+    if (allv && r0 + u.T1 <= u.n1 && j0 + u.T2 <= u.n2) {
+        // whole tile with every velocity: contiguous rows of f^{n+1}
         const int W = u.T2 * u.TV;
-        const int dr = kThreads / W, dq = kThreads - dr * W;
+        const int dr = nt / W, dq = nt - dr * W;
+        int r = threadIdx.x / W, q = threadIdx.x - r * W;
+        T *gp = fout + (long long)r0 * rs + (long long)j0 * u.NV + r * rs + q;
+        const T *dp = D + r * u.DP + q;
+        const long long gstep = dr * rs + dq, gwrap = rs - W;
+        const int dstep = dr * u.DP + dq, dwrap = u.DP - W;
+        for (; r < u.T1;) {
+            *gp = *dp;
+            r += dr;
+            q += dq;
+            gp += gstep;
+            dp += dstep;
+            if (q >= W) {
+                q -= W;
+                ++r;
+                gp += gwrap;
+                dp += dwrap;
+            }
+        }
+    } else {
+        const int W = u.T2 * u.TV;
+        const int dr = nt / W, dq = nt - dr * W;
         int r = threadIdx.x / W, q = threadIdx.x - r * W;
         for (; r < u.T1;) {
             const int jj = (int)fdiv((unsigned)q, u.fd_tv), tv = q - jj * u.TV;
@@ -203,10 +264,9 @@ size_t unsplit_smem(const UnsplitGeo &u, int G) {
     return (size_t)((u.T1 + 2 * G) * u.P + u.T1 * u.DP) * sizeof(T);
 }
 
-// tile shape: the largest share of useful cells among the staged ones within
-// a shared-memory budget, at least 1024 cells per tile
+// launch geometry of one tile shape
 template <typename T>
-UnsplitGeo plan(const vp_ctx *c, int G) {
+UnsplitGeo make_geo(const vp_ctx *c, int G, const UnsplitTune &t) {
     const vp_grid &g = c->g;
     UnsplitGeo u{};
     u.n1 = g.nx[0];
@@ -217,30 +277,14 @@ UnsplitGeo plan(const vp_ctx *c, int G) {
     u.nv1 = g.nv[1];
     u.vs0 = g.nv[1];
     u.vs1 = 1;
-    // velocity cells per tile: up to a warp's worth, fewer where even the
-    // smallest tile's halo would not fit
-    double best = -1.0;
-    const int T1s[4] = {8, 16, 32, 64}, T2s[5] = {8, 16, 32, 64, 128};
-    for (int TV = u.NV < 32 ? u.NV : 32; best < 0.0 && TV >= 1; TV /= 2)
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 5; ++b) {
-                UnsplitGeo t = u;
-                t.TV = TV;
-                t.T1 = T1s[a];
-                t.T2 = T2s[b];
-                t.P = t.TV * ((t.T2 + 2 * G) | 1);
-                t.DP = t.TV * (t.T2 | 1);
-                if (unsplit_smem<T>(t, G) > 64 * 1024) continue;
-                const double eff = (double)t.T1 * t.T2 / ((double)(t.T1 + 2 * G) * (t.T2 + 2 * G));
-                const bool big = (long long)t.T1 * t.T2 * t.TV >= 1024;
-                const double score = eff + (big ? 1.0 : 0.0);
-                if (score > best) {
-                    best = score;
-                    u = t;
-                }
-            }
-    auto segs = [](int cells, int len) {
-        int s = (kThreads + cells - 1) / cells;
+    u.T1 = t.T1;
+    u.T2 = t.T2;
+    u.TV = t.TV;
+    u.P = u.TV * ((u.T2 + 2 * G) | 1);
+    u.DP = u.TV * (u.T2 | 1);
+    // walk segments: enough work items for every thread, at least 8 cells each
+    auto segs = [&](int lines, int len) {
+        int s = (t.threads + lines - 1) / lines;
         while (s > 1 && len / s < 8) --s;
         return s < 1 ? 1 : s;
     };
@@ -253,25 +297,146 @@ UnsplitGeo plan(const vp_ctx *c, int G) {
     return u;
 }
 
+// velocity cells per tile: up to a warp's worth, fewer where even the
+// smallest tile's halo would not fit the shared-memory budget
+template <typename T>
+int tile_tv(const vp_ctx *c, int G) {
+    int TV = c->NV < 32 ? (int)c->NV : 32;
+    while (TV > 1) {
+        UnsplitTune t{1, 8, 8, TV, 128};
+        if (unsplit_smem<T>(make_geo<T>(c, G, t), G) <= (size_t)kMaxSmem) break;
+        TV /= 2;
+    }
+    return TV;
+}
+
+// candidate tile shapes: T1, T2 in 16 .. 128 (8 .. 32 for wide velocity
+// tiles), 128 or 256 threads, within the shared-memory budget; the default is
+// the one with the largest share of useful cells among the staged ones (at
+// least 1024 cells, 256 threads)
+template <typename T>
+int candidates(const vp_ctx *c, int G, UnsplitTune *out, int cap, UnsplitTune *dflt) {
+    const int TV = tile_tv<T>(c, G);
+    const int lo = TV >= 8 ? 8 : 16, hi = TV >= 8 ? 32 : 128;
+    int n = 0;
+    double best = -1.0;
+    *dflt = UnsplitTune{1, 8, 8, TV, 256};
+    for (int T1 = lo; T1 <= hi; T1 *= 2)
+        for (int T2 = lo; T2 <= hi; T2 *= 2)
+            for (int th = 128; th <= 256; th *= 2) {
+                const UnsplitTune t{1, T1, T2, TV, th};
+                const UnsplitGeo u = make_geo<T>(c, G, t);
+                if (unsplit_smem<T>(u, G) > (size_t)kMaxSmem) continue;
+                if ((long long)T1 * T2 * TV < th) continue;  // a cell per thread at least
+                if (n < cap) out[n++] = t;
+                const double eff = (double)T1 * T2 / ((double)(T1 + 2 * G) * (T2 + 2 * G));
+                const double score = eff + ((long long)T1 * T2 * TV >= 1024 ? 1.0 : 0.0) +
+                                     (unsplit_smem<T>(u, G) <= 64 * 1024 ? 1.0 : 0.0);
+                if (th == 256 && score > best) {
+                    best = score;
+                    *dflt = t;
+                }
+            }
+    return n;
+}
+
 template <typename T, int ORDER, bool FULL, int G>
 void set_attr_one() {
-    cudaFuncSetAttribute(k_unsplit2<T, ORDER, FULL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_unsplit2<T, ORDER, FULL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+}
+
+template <typename T>
+void set_attrs() {
+    static bool done = false;
+    if (done) return;
+    set_attr_one<T, 5, false, 4>();
+    set_attr_one<T, 5, false, 8>();
+    set_attr_one<T, 5, true, 4>();
+    set_attr_one<T, 5, true, 8>();
+    set_attr_one<T, 7, false, 4>();
+    set_attr_one<T, 7, false, 8>();
+    set_attr_one<T, 7, true, 4>();
+    set_attr_one<T, 7, true, 8>();
+    done = true;
+}
+
+// one step a -> b with tile shape t
+template <typename T>
+int launch(vp_ctx *c, const T *a, T *b, int G, const UnsplitTune &t) {
+    const vp_grid &g = c->g;
+    const UnsplitGeo u = make_geo<T>(c, G, t);
+    const long long tiles = (long long)((u.n1 + u.T1 - 1) / u.T1) * u.tiles2 * u.tilesv;
+    if (tiles >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "unsplit step has too many tiles");
+    const size_t smem = unsplit_smem<T>(u, G);
+    const LimParams lp{g.alpha, g.mp, g.pp};
+    const bool full = g.mp && g.pp;
+    const LineShift<T> *tab = static_cast<const LineShift<T> *>(c->d_shift);
+#define VP_LAUNCH(O, F, GG) \
+    k_unsplit2<T, O, F, GG><<<(unsigned)tiles, t.threads, smem, c->stream>>>(a, b, tab, u, lp)
+    if (g.order == 7) {
+        if (full) {
+            if (G == 4) VP_LAUNCH(7, true, 4); else VP_LAUNCH(7, true, 8);
+        } else {
+            if (G == 4) VP_LAUNCH(7, false, 4); else VP_LAUNCH(7, false, 8);
+        }
+    } else {
+        if (full) {
+            if (G == 4) VP_LAUNCH(5, true, 4); else VP_LAUNCH(5, true, 8);
+        } else {
+            if (G == 4) VP_LAUNCH(5, false, 4); else VP_LAUNCH(5, false, 8);
+        }
+    }
+#undef VP_LAUNCH
+    c->launches++;
+    VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+// Autotuner: time every candidate tile shape on the bound f (f -> scratch,
+// which the call may overwrite; f is left unchanged) and keep the fastest.
+// Once per halo width, never inside a stream capture.
+template <typename T>
+int tune(vp_ctx *c, int G, T *scratch) {
+    constexpr int kCap = 48;
+    UnsplitTune cand[kCap], best;
+    const int nc = candidates<T>(c, G, cand, kCap, &best);
+    cudaEvent_t e0, e1;
+    VP_CUDA_TRY(c, cudaEventCreate(&e0));
+    VP_CUDA_TRY(c, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int rc = VP_OK;
+    for (int i = 0; i < nc && rc == VP_OK; ++i) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && rc == VP_OK; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            rc = launch<T>(c, static_cast<const T *>(c->f), scratch, G, cand[i]);
+            cudaEventRecord(e1, c->stream);
+            if (rc) break;
+            const cudaError_t se = cudaEventSynchronize(e1);
+            if (se != cudaSuccess) {
+                rc = vp_fail(c, VP_ECUDA, "unsplit candidate failed: %s", cudaGetErrorString(se));
+                break;
+            }
+            float m = 0.f;
+            cudaEventElapsedTime(&m, e0, e1);
+            ms = m < ms ? m : ms;
+        }
+        if (rc == VP_OK && ms < best_ms) {
+            best_ms = ms;
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    c->utune[G == 8] = best;
+    c->utune[G == 8].valid = 1;
+    return VP_OK;
 }
 
 template <typename T>
 int run_t(vp_ctx *c, double dt, int nsteps, void *scratch, int G) {
-    static bool attrs = false;
-    if (!attrs) {
-        set_attr_one<T, 5, false, 4>();
-        set_attr_one<T, 5, false, 8>();
-        set_attr_one<T, 5, true, 4>();
-        set_attr_one<T, 5, true, 8>();
-        set_attr_one<T, 7, false, 4>();
-        set_attr_one<T, 7, false, 8>();
-        set_attr_one<T, 7, true, 4>();
-        set_attr_one<T, 7, true, 8>();
-        attrs = true;
-    }
+    set_attrs<T>();
     const vp_grid &g = c->g;
     DriftAxes ax{};
     for (int d = 0; d < 2; ++d) {
@@ -286,35 +451,24 @@ int run_t(vp_ctx *c, double dt, int nsteps, void *scratch, int G) {
     k_drift_tables<T><<<(ne + 127) / 128, 128, 0, c->stream>>>(tab, ax, dt, c->wp);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
-    const UnsplitGeo u = plan<T>(c, G);
-    const long long tiles = (long long)((u.n1 + u.T1 - 1) / u.T1) * u.tiles2 * u.tilesv;
-    if (tiles >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "unsplit step has too many tiles");
-    const size_t smem = unsplit_smem<T>(u, G);
-    const LimParams lp{g.alpha, g.mp, g.pp};
-    const bool full = g.mp && g.pp;
     T *a = static_cast<T *>(c->f), *b = static_cast<T *>(scratch);
-    for (int s = 0; s < nsteps; ++s) {
-#define VP_LAUNCH(O, F, GG) \
-    k_unsplit2<T, O, F, GG><<<(unsigned)tiles, kThreads, smem, c->stream>>>(a, b, tab, u, lp)
-        if (g.order == 7) {
-            if (full) {
-                if (G == 4) VP_LAUNCH(7, true, 4); else VP_LAUNCH(7, true, 8);
-            } else {
-                if (G == 4) VP_LAUNCH(7, false, 4); else VP_LAUNCH(7, false, 8);
-            }
+    UnsplitTune t = c->utune[G == 8];
+    if (!t.valid) {
+        if (c->opt_autotune && !vp_capturing(c)) {
+            const int rc = tune<T>(c, G, b);
+            if (rc) return rc;
+            t = c->utune[G == 8];
         } else {
-            if (full) {
-                if (G == 4) VP_LAUNCH(5, true, 4); else VP_LAUNCH(5, true, 8);
-            } else {
-                if (G == 4) VP_LAUNCH(5, false, 4); else VP_LAUNCH(5, false, 8);
-            }
+            UnsplitTune cand[1];
+            candidates<T>(c, G, cand, 0, &t);
         }
-#undef VP_LAUNCH
-        c->launches++;
-        VP_CUDA_TRY(c, cudaGetLastError());
-        T *t = a;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        const int rc = launch<T>(c, a, b, G, t);
+        if (rc) return rc;
+        T *x = a;
         a = b;
-        b = t;
+        b = x;
     }
     if (a != c->f) {
         VP_CUDA_TRY(c, cudaMemcpyAsync(c->f, a, (size_t)c->ncell * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));

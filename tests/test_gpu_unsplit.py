@@ -32,6 +32,7 @@ CASES = [
     (vp_grid([13, 17], [2, 3], [-1.0, -2.0], [1.5, 2.0]), 0.05),  # few velocities, small shifts
     (vp_grid([20, 12], [6, 7], [-2.0, -1.0], [2.0, 1.0], xbc=O.BC_OUTFLOW), 0.1),
     (vp_grid([16, 40], [1, 1], [-1.4, -0.9], [-0.6, -0.1], xbc=O.BC_OUTFLOW, order=5), 0.011),
+    (inputs.advect_2d(200, 1, n2=150, nv=2)["grid"], 0.1 / 200),  # interior tiles (contiguous rows)
 ]
 
 
@@ -195,3 +196,21 @@ def test_unsplit_negative_cells_take_the_theta_form(precision):
     else:
         assert rel_l1(from_gpu(sim), f) <= 4e-6
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [V.VP_F64, V.VP_F32])
+def test_unsplit_tile_shape_does_not_change_bits(precision):
+    """The autotuner (every candidate tile shape launched f -> scratch once,
+    f untouched) and the fixed default shape give the same bits: every cell's
+    increments are the same walks whatever the tile."""
+    g, dt = CASES[1]
+    out = []
+    for tune in (0, 1):
+        sim, og = both(g, precision)
+        V.vp_set_option(sim.ctx, V.VP_OPT_AUTOTUNE, tune)
+        f = inputs.random_f(og.NX * og.NV, seed=12)
+        to_gpu(sim, f)
+        V.vp_drift_unsplit(sim.ctx, dt, 3, _scratch(sim))
+        out.append(from_gpu(sim))
+        sim.close()
+    assert np.array_equal(out[0], out[1])
