@@ -254,7 +254,7 @@ def ensemble_bench(steps: int, warmup: int = 3):
         cells += n
         updates_per_step += n * 3 * d["dims"]
     V.vp_ensemble_field(ens)
-    V.vp_ensemble_autotune(ens)
+    V.vp_ensemble_autotune(ens, 0.05)
     V.vp_ensemble_step(ens, 0.05, warmup)
     V.vp_ensemble_sync(ens)
     l0 = V.vp_ensemble_launch_count(ens)

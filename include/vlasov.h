@@ -235,8 +235,11 @@ int vp_sync(vp_ctx *ctx);
  *                      thread with packed FP32 pair arithmetic (FP32 grids;
  *                      the same bits as 1);
  *   VP_OPT_AUTOTUNE:   1 (default) times candidate tile shapes of each sweep
- *                      geometry on its first use (with a zero shift, which
- *                      leaves f unchanged) and keeps the fastest; 0 uses
+ *                      geometry on its first use, with that sweep's shifts,
+ *                      on a copy of a prefix of f (at most 256 MB, allocated
+ *                      for the tuning and freed; f is left unchanged; without
+ *                      room for it the defaults stay), and of the unsplit
+ *                      step (f -> scratch_dev), and keeps the fastest; 0 uses
  *                      fixed defaults;
  *   VP_OPT_WAIT_LIMIT: iterations of each bounded device-side wait in the
  *                      sweeps (the TMA kernel's tile barriers; default 2^26,
@@ -293,8 +296,11 @@ int vp_ensemble_accel(const vp_ens *ens, const double **accel_dev);
  * dividing 256), CTAs per SM of the persistent grid (0 = occupancy maximum) */
 int vp_ensemble_set_tiles(vp_ens *ens, int W, int R, int ctas_per_sm);
 int vp_ensemble_get_tiles(const vp_ens *ens, int *out3);
-/* time candidate tile shapes with whole steps at dt = 0 (f unchanged); keep the fastest; synchronises */
-int vp_ensemble_autotune(vp_ens *ens);
+/* time candidate tile shapes (W, R, CTAs per SM) with whole steps at dt from
+ * a snapshot of f and the field (allocated for the tuning, restored after
+ * every timed step, freed: the ensemble's state is unchanged); keep the
+ * fastest; synchronises.  VP_ENOMEM without room for the snapshot. */
+int vp_ensemble_autotune(vp_ens *ens, double dt);
 /* nsteps KDK steps of every run (one persistent launch each, graph replay) */
 int vp_ensemble_step(vp_ens *ens, double dt, int nsteps);
 /* wait for the stream; VP_ETIMEOUT if a bounded wait in the kernel gave up */

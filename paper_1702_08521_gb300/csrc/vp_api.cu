@@ -182,7 +182,7 @@ int sweep_all(vp_ctx *c, int kick, int dim, double dt, const double *accel) {
     // stages do not leave f bit-for-bit unchanged at dt = 0, which the tuner needs)
     if (c->g.scheme == VP_SCHEME_RK) return vp_launch_rk_sweep(c, kick, dim, dt, accel);
     if (c->opt_autotune && !c->tune[kick][dim].valid && !capturing(c))
-        if ((rc = vp_tune_sweep(c, kick, dim))) return rc;
+        if ((rc = vp_tune_sweep(c, kick, dim, dt, accel))) return rc;
     rc = vp_launch_shift_table(c, kick, dim, dt, accel);
     if (rc) return rc;
     return vp_launch_sweep(c, kick, dim);
@@ -463,10 +463,13 @@ static int run_steps(vp_ctx *c, double dt, int split, int nsteps, double *accel_
     const bool use_graph = c->stream != nullptr && c->stream != cudaStreamLegacy;
     vp_graph_cache &gc = c->graph;
     if (c->opt_autotune && !capturing(c)) {
+        // each sweep tuned at the step it appears in: KDK kicks by dt/2 and
+        // drifts by dt, DKD the other way round
+        const double hd = split == VP_SPLIT_KDK ? dt : 0.5 * dt, hk = split == VP_SPLIT_KDK ? 0.5 * dt : dt;
         for (int d = 0; d < c->g.dx; ++d)
-            if ((rc = vp_tune_sweep(c, 0, d))) return rc;
+            if ((rc = vp_tune_sweep(c, 0, d, hd, nullptr))) return rc;
         for (int d = 0; d < c->g.dv; ++d)
-            if ((rc = vp_tune_sweep(c, 1, d))) return rc;
+            if ((rc = vp_tune_sweep(c, 1, d, hk, accel_dev + d * c->NX))) return rc;
     }
     if (use_graph && !(gc.valid && gc.dt == dt && gc.split == split && gc.f == c->f && gc.acc == accel_dev &&
                       gc.wts == wts)) {

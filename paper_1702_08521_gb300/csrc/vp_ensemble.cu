@@ -25,6 +25,7 @@
 
 #include "vp_internal.cuh"
 #include "vp_sweep_core.cuh"
+#include "vp_tma.cuh"
 
 namespace {
 
@@ -141,9 +142,25 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
         sm[c] = 0.f;
         data[L * W + c] = 0.f;
     }
-    // staging: four rows per thread in flight; (row, column) advanced
-    // incrementally
-    {
+    // staging: where every row of the tile is whole and 16-byte aligned, all
+    // of it in flight at once as 16-byte cp.async.cg copies (L2, as the
+    // L1-bypass loads: earlier stages of this launch wrote it); otherwise
+    // four rows per thread in flight, (row, column) advanced incrementally
+    if (wc == W && W % 4 == 0 && s.inner % 4 == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+        const int wv = W >> 2;
+        const int dr = blockDim.x / wv, dc = blockDim.x - dr * wv;
+        int row = threadIdx.x / wv, cv = threadIdx.x - row * wv;
+        while (row < L) {
+            vp_tma::cp_async16(data + row * W + 4 * cv, base + (long long)row * s.inner + 4 * cv);
+            row += dr;
+            cv += dc;
+            if (cv >= wv) {
+                cv -= wv;
+                ++row;
+            }
+        }
+        vp_tma::cp_async_wait_all();
+    } else {
         const int dr = blockDim.x / W, dc = blockDim.x - dr * W;
         int row = threadIdx.x / W, cc = threadIdx.x - row * W;
         for (int e = threadIdx.x; e < L * W; e += 4 * blockDim.x) {
@@ -302,6 +319,25 @@ __device__ void density_points(const float *pool, const RunDesc &r, long long x0
 // length up to 256 (length len uses every (256 / len)-th entry)
 constexpr int kTwN = 256;
 
+// runs with at most this many spatial points transform in shared memory;
+// larger ones in their slice of a global scratch array (L2-resident), so the
+// kernel's shared memory is sized by the sweep tiles alone
+constexpr long long kSmemFftMax = 1024;
+
+// element access of the transform array: shared memory, or the global scratch
+// through L2 (other SMs used it in earlier launches)
+template <bool GLOBAL>
+__device__ __forceinline__ double2 ld2(const double2 *p) {
+    if constexpr (GLOBAL) return __ldcg(p);
+    else return *p;
+}
+template <bool GLOBAL>
+__device__ __forceinline__ void st2(double2 *p, double2 v) {
+    if constexpr (GLOBAL) __stcg(p, v);
+    else *p = v;
+}
+
+template <bool GLOBAL>
 __device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sign, const double2 *__restrict__ tw) {
     const int n = axis == 0 ? n0 : n1;
     const int lines = dims == 1 ? 1 : (axis == 0 ? n1 : n0);
@@ -315,9 +351,9 @@ __device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sig
         const int rj = logn ? (int)(__brev((unsigned)j) >> (32 - logn)) : 0;
         if (j < rj) {
             double2 *pa = a + l * lstride + j * stride, *pb = a + l * lstride + rj * stride;
-            const double2 tmp = *pa;
-            *pa = *pb;
-            *pb = tmp;
+            const double2 tmp = ld2<GLOBAL>(pa);
+            st2<GLOBAL>(pa, ld2<GLOBAL>(pb));
+            st2<GLOBAL>(pb, tmp);
         }
     }
     __syncthreads();
@@ -330,32 +366,35 @@ __device__ void smem_fft(double2 *a, int dims, int n0, int n1, int axis, int sig
             const double2 twk = tw[k * (kTwN / len)];
             const double cs = twk.x, sn = sign < 0 ? -twk.y : twk.y;
             double2 *pu = a + l * lstride + i0 * stride, *pv = a + l * lstride + i1 * stride;
-            const double2 u = *pu, v = *pv;
+            const double2 u = ld2<GLOBAL>(pu), v = ld2<GLOBAL>(pv);
             const double2 tw = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
-            *pu = make_double2(u.x + tw.x, u.y + tw.y);
-            *pv = make_double2(u.x - tw.x, u.y - tw.y);
+            st2<GLOBAL>(pu, make_double2(u.x + tw.x, u.y + tw.y));
+            st2<GLOBAL>(pv, make_double2(u.x - tw.x, u.y - tw.y));
         }
         __syncthreads();
     }
 }
 
-// periodic Poisson + FDA force of one run, all in one CTA (NX <= 4096)
+// periodic Poisson + FDA force of one run, all in one CTA (NX <= 4096); the
+// transform array a in shared memory or (GLOBAL) the run's global scratch
+template <bool GLOBAL>
 __device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *acc_pool, double2 *a,
                             const double2 *__restrict__ tw, const double *__restrict__ green) {
     const int D = r.dims;
     const int n0 = r.nx[0], n1 = D == 2 ? r.nx[1] : 1;
     const long long NX = r.NX;
     for (long long x = threadIdx.x; x < NX; x += blockDim.x)
-        a[x] = make_double2(ldcg(rho_pool + r.rho_off + x) - r.rho_bg, 0.0);
+        st2<GLOBAL>(a + x, make_double2(ldcg(rho_pool + r.rho_off + x) - r.rho_bg, 0.0));
     __syncthreads();
-    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, -1, tw);
+    for (int ax = 0; ax < D; ++ax) smem_fft<GLOBAL>(a, D, n0, n1, ax, -1, tw);
     // S / lambda(k) / NX of the run, tabulated at creation (0 at k = 0)
     for (long long x = threadIdx.x; x < NX; x += blockDim.x) {
         const double sc = green[r.rho_off + x];
-        a[x] = make_double2(a[x].x * sc, a[x].y * sc);
+        const double2 ax = ld2<GLOBAL>(a + x);
+        st2<GLOBAL>(a + x, make_double2(ax.x * sc, ax.y * sc));
     }
     __syncthreads();
-    for (int ax = 0; ax < D; ++ax) smem_fft(a, D, n0, n1, ax, +1, tw);
+    for (int ax = 0; ax < D; ++ax) smem_fft<GLOBAL>(a, D, n0, n1, ax, +1, tw);
     // a = -grad phi by the 2/4/6-point FDA (Eqs. C9-C11)
     double c1 = 1.0, c2 = 0.0, c3 = 0.0, den = 2.0;
     if (r.pois_order == 4) {
@@ -378,7 +417,7 @@ __device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *ac
                 int j0 = i0, j1 = i1;
                 if (d == 0) j0 = (i0 + off) & (n0 - 1);
                 else j1 = (i1 + off) & (n1 - 1);
-                return a[j0 * n1 + j1].x;
+                return ld2<GLOBAL>(a + j0 * n1 + j1).x;
             };
             const double g = c1 * (at(1) - at(-1)) + c2 * (at(2) - at(-2)) + c3 * (at(3) - at(-3));
             acc_pool[r.acc_off + (long long)d * NX + x] = g * (d == 0 ? sc0 : sc1);
@@ -387,13 +426,13 @@ __device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *ac
 }
 
 template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_ensemble(float *__restrict__ pool,
+__global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ pool,
                                                        const RunDesc *__restrict__ runs,
                                                        const EnsItem *__restrict__ items, int nitems,
                                                        unsigned *__restrict__ ctr, double *acc_pool,
                                                        double *rho_pool, EnsParams P,
                                                        int *__restrict__ status, const double2 *__restrict__ tw,
-                                                       const double *__restrict__ green) {
+                                                       const double *__restrict__ green, double2 *fftbuf) {
     extern __shared__ __align__(16) unsigned char ens_smem[];
     __shared__ int s_item;
     __shared__ int s_ok;
@@ -436,7 +475,10 @@ __global__ void __launch_bounds__(kThreads) k_ensemble(float *__restrict__ pool,
                 __threadfence_block();
                 __syncthreads();
             }
-            poisson_run(r, rho_pool, acc_pool, reinterpret_cast<double2 *>(ens_smem), tw, green);
+            if (r.NX <= kSmemFftMax)
+                poisson_run<false>(r, rho_pool, acc_pool, reinterpret_cast<double2 *>(ens_smem), tw, green);
+            else
+                poisson_run<true>(r, rho_pool, acc_pool, fftbuf + r.rho_off, tw, green);
         }
         __threadfence();
         __syncthreads();
@@ -455,7 +497,7 @@ size_t smem_need(const std::vector<RunDesc> &runs) {
             } else if (s.kind == ST_ROWS) {
                 b = (size_t)s.tw * (((s.L + 2 * VP_GHOST) | 1) + (s.L | 1)) * sizeof(float);
             } else if (s.kind == ST_POISSON) {
-                b = (size_t)r.NX * sizeof(double2);
+                b = r.NX <= kSmemFftMax ? (size_t)r.NX * sizeof(double2) : 0;
             }
             need = b > need ? b : need;
         }
@@ -477,6 +519,7 @@ struct vp_ens {
     double *d_acc, *d_rho;
     double2 *d_tw;     // FFT twiddles (kTwN / 2 entries)
     double *d_green;   // per run: S / lambda(k) / NX at every Fourier mode (rho layout)
+    double2 *d_fft;    // per run: transform scratch of runs too large for shared memory (rho layout)
     long long acc_total, rho_total;
     RunDesc *d_runs;
     EnsItem *d_items_step, *d_items_field;
@@ -625,11 +668,11 @@ static int launch_pass(vp_ens *e, const EnsItem *items, int nitems, double dt) {
     if (e->P.order == 7)
         k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
                                                              e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
-                                                             e->d_green);
+                                                             e->d_green, e->d_fft);
     else
         k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
                                                              e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
-                                                             e->d_green);
+                                                             e->d_green, e->d_fft);
     e->launches++;
     const cudaError_t er = cudaGetLastError();
     if (er != cudaSuccess) return ens_fail(e, VP_ECUDA, cudaGetErrorString(er));
@@ -707,6 +750,7 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
     build_items(e);
     if (cudaMalloc(&e->d_acc, sizeof(double) * aoff) != cudaSuccess ||
         cudaMalloc(&e->d_rho, sizeof(double) * roff) != cudaSuccess ||
+        cudaMalloc(&e->d_fft, sizeof(double2) * roff) != cudaSuccess ||
         cudaMalloc(&e->d_ctr, sizeof(unsigned) * (slot + 1)) != cudaSuccess ||
         cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess) {
         vp_ensemble_destroy(e);
@@ -776,6 +820,7 @@ void vp_ensemble_destroy(vp_ens *e) {
     cudaStreamSynchronize(e->stream);
     cudaFree(e->d_acc);
     cudaFree(e->d_rho);
+    cudaFree(e->d_fft);
     cudaFree(e->d_tw);
     cudaFree(e->d_green);
     cudaFree(e->d_ctr);
@@ -844,11 +889,11 @@ int vp_ensemble_field(vp_ens *e) {
         if (e->P.order == 7)
             k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
                                                                  (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status, e->d_tw, e->d_green);
+                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft);
         else
             k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
                                                                  (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status, e->d_tw, e->d_green);
+                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft);
         e->launches++;
         if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "field pass failed");
     }
@@ -917,9 +962,32 @@ int vp_ensemble_get_tiles(const vp_ens *e, int *out3) {
     return VP_OK;
 }
 
-int vp_ensemble_autotune(vp_ens *e) {
+int vp_ensemble_autotune(vp_ens *e, double dt) {
     if (!e || !e->pool) return VP_EINVAL;
-    // time whole steps with dt = 0 (every shift is zero: f is unchanged)
+    if (!std::isfinite(dt)) return ens_fail(e, VP_EINVAL, "dt must be finite");
+    // time whole steps at the run's dt (the limiters at work, as in the
+    // timed steps) from a snapshot of f and the field, restored afterwards:
+    // the ensemble's state is unchanged
+    float *snap_f = nullptr;
+    double *snap_acc = nullptr;
+    if (cudaMalloc(&snap_f, sizeof(float) * e->pool_cells) != cudaSuccess ||
+        cudaMalloc(&snap_acc, sizeof(double) * e->acc_total) != cudaSuccess) {
+        cudaFree(snap_f);
+        cudaGetLastError();
+        return ens_fail(e, VP_ENOMEM, "no room for the tuning snapshot");
+    }
+    auto restore = [&]() {
+        return cudaMemcpyAsync(e->pool, snap_f, sizeof(float) * e->pool_cells, cudaMemcpyDeviceToDevice,
+                               e->stream) == cudaSuccess &&
+               cudaMemcpyAsync(e->d_acc, snap_acc, sizeof(double) * e->acc_total, cudaMemcpyDeviceToDevice,
+                               e->stream) == cudaSuccess;
+    };
+    int rc = VP_OK;
+    if (cudaMemcpyAsync(snap_f, e->pool, sizeof(float) * e->pool_cells, cudaMemcpyDeviceToDevice, e->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(snap_acc, e->d_acc, sizeof(double) * e->acc_total, cudaMemcpyDeviceToDevice, e->stream) !=
+            cudaSuccess)
+        rc = ens_fail(e, VP_ECUDA, "tuning snapshot failed");
     const int Ws[3] = {32, 64, 128};
     const int Rs[2] = {32, 64};
     float best = 1e30f;
@@ -927,27 +995,30 @@ int vp_ensemble_autotune(vp_ens *e) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    for (int wi = 0; wi < 3; ++wi)
-        for (int ri = 0; ri < 2; ++ri) {
+    for (int wi = 0; wi < 3 && rc == VP_OK; ++wi)
+        for (int ri = 0; ri < 2 && rc == VP_OK; ++ri) {
             if (vp_ensemble_set_tiles(e, Ws[wi], Rs[ri], 0)) continue;
             const int maxc = e->ctas_per_sm;
-            for (int cps = maxc; cps >= 1 && cps >= maxc - 2; --cps) {
+            for (int cps = maxc; cps >= 1 && cps >= maxc - 2 && rc == VP_OK; --cps) {
                 e->ctas_per_sm = cps;
                 float ms = 1e30f;
                 for (int rep = 0; rep < 2; ++rep) {
                     cudaEventRecord(a, e->stream);
-                    int rc = launch_pass(e, e->d_items_step, (int)e->items_step.size(), 0.0);
+                    const int lr = launch_pass(e, e->d_items_step, (int)e->items_step.size(), dt);
                     cudaEventRecord(b, e->stream);
-                    if (rc || cudaEventSynchronize(b) != cudaSuccess) {
-                        cudaEventDestroy(a);
-                        cudaEventDestroy(b);
-                        return ens_fail(e, VP_ECUDA, "autotune pass failed");
+                    if (lr || cudaEventSynchronize(b) != cudaSuccess) {
+                        rc = ens_fail(e, VP_ECUDA, "autotune pass failed");
+                        break;
                     }
                     float m = 0.f;
                     cudaEventElapsedTime(&m, a, b);
                     ms = m < ms ? m : ms;
+                    if (!restore()) {
+                        rc = ens_fail(e, VP_ECUDA, "tuning restore failed");
+                        break;
+                    }
                 }
-                if (ms < best) {
+                if (rc == VP_OK && ms < best) {
                     best = ms;
                     bw = Ws[wi];
                     br = Rs[ri];
@@ -957,6 +1028,10 @@ int vp_ensemble_autotune(vp_ens *e) {
         }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    cudaStreamSynchronize(e->stream);
+    cudaFree(snap_f);
+    cudaFree(snap_acc);
+    if (rc) return rc;
     e->tuned = 1;
     return vp_ensemble_set_tiles(e, bw, br, bc);
 }

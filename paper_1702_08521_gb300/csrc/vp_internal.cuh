@@ -196,7 +196,8 @@ int vp_learned_prepare(vp_ctx *c);
 int vp_rk_setup();
 int vp_launch_rk_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel);
 int vp_launch_sweep(vp_ctx *c, int kick, int dim);
-int vp_tune_sweep(vp_ctx *c, int kick, int dim);  // outside stream capture only
+// autotune sweep (kick, dim) at its own shifts (dt, accel); outside stream capture only
+int vp_tune_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel);
 int vp_launch_moment(vp_ctx *c, double *rho);
 int vp_launch_poisson(vp_ctx *c, const double *rho, double *phi, double *acc);
 int vp_launch_diag(vp_ctx *c, int mode, double *out_dev);

@@ -699,16 +699,94 @@ int launch_sweep_t(vp_ctx *c, int kick, int dim) {
     return launch_rows<T>(c, geo, tu);
 }
 
-// Autotuner: time candidate tile shapes of one sweep geometry on the bound
-// f with a zero shift (n = 0, nu = 0 leaves f bit-for-bit unchanged) and keep
-// the fastest.  Runs once per (kind, axis), never inside a stream capture.
+// Autotuner: time candidate tile shapes of one sweep geometry with the
+// sweep's own shifts (dt, accel) on a copy of a window at the centre of f --
+// whole outer blocks, or where one block exceeds the budget the middle
+// columns of every row -- of at most kTuneBytes (larger than L2, so the
+// timing sees HBM), and keep the fastest.  The window keeps every line's
+// shift class (its offset is a whole number of class periods; a kick window
+// reads the shift table from its first spatial point), so the limiter paths
+// are timed on the state at hand where the distribution is, not on an empty
+// corner of phase space; f is left untouched.  Without room for the copy the
+// defaults stay.  Runs once per (kind, axis), never inside a stream capture.
+constexpr size_t kTuneBytes = size_t(256) << 20;
+
 template <typename T>
-int tune_t(vp_ctx *c, int kick, int dim) {
+int tune_on(vp_ctx *c, int kick, int dim, const SweepGeo &geo, const SweepGeo &sub, SweepTune best);
+
+template <typename T>
+int tune_t(vp_ctx *c, int kick, int dim, double dt, const double *accel) {
     const SweepGeo geo = vp_make_geo(c, kick, dim);
     SweepTune best = default_tune<T>(c, geo);
-    if (kick) VP_CUDA_TRY(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * c->NX, c->stream));
-    int rc = vp_launch_shift_table(c, kick, dim, 0.0, kick ? c->d_acc : nullptr);
-    if (rc) return rc;
+    SweepGeo sub = geo;
+    const size_t block = (size_t)geo.L * (size_t)geo.inner * sizeof(T);
+    size_t bytes;
+    bool pitched = false;
+    long long o0 = 0, c0 = 0;  // window offset: outer blocks, columns
+    // flattened index of the central cell of spatial axes [a, b)
+    auto centre = [&](int a, int b) {
+        long long i = 0;
+        for (int k = a; k < b; ++k) i = i * c->g.nx[k] + c->g.nx[k] / 2;
+        return i;
+    };
+    auto clampll = [](long long x, long long lo, long long hi) { return x < lo ? lo : (x > hi ? hi : x); };
+    // the window's middle: the central spatial cell (and middle velocity)
+    const long long o_mid = kick ? centre(0, c->g.dx) * geo.cdiv + geo.cdiv / 2 : centre(0, dim);
+    const long long c_mid = kick ? 0 : centre(dim + 1, c->g.dx) * c->NV + c->NV / 2;
+    if (block <= kTuneBytes) {
+        const long long no = (long long)(kTuneBytes / block);
+        sub.outer = no < geo.outer ? no : geo.outer;
+        o0 = clampll(o_mid - sub.outer / 2, 0, geo.outer - sub.outer);
+        if (!geo.cls_from_inner) o0 -= o0 % geo.cdiv;  // whole spatial points
+        bytes = (size_t)sub.outer * block;
+    } else {
+        long long ni = (long long)(kTuneBytes / ((size_t)geo.L * sizeof(T)));
+        if (ni >= 128) ni &= ~127LL;
+        if (ni < 1) ni = 1;
+        sub.outer = 1;
+        sub.inner = ni < geo.inner ? ni : geo.inner;
+        o0 = clampll(o_mid, 0, geo.outer - 1);
+        if (!geo.cls_from_inner) o0 -= o0 % geo.cdiv;
+        // whole velocity periods of the line classes, and 16-byte rows
+        const long long per = 4 * (geo.cls_from_inner ? geo.cdiv * geo.cmod : 1);
+        c0 = clampll(c_mid - sub.inner / 2, 0, geo.inner - sub.inner);
+        c0 -= c0 % per;
+        bytes = (size_t)geo.L * (size_t)sub.inner * sizeof(T);
+        pitched = true;
+    }
+    const T *src = static_cast<const T *>(c->f) + (o0 * geo.L * geo.inner + c0);
+    void *scratch = nullptr;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->tune[kick][dim] = best;
+        return VP_OK;
+    }
+    int rc = VP_OK;
+    if (pitched)
+        rc = cudaMemcpy2DAsync(scratch, (size_t)sub.inner * sizeof(T), src, (size_t)geo.inner * sizeof(T),
+                               (size_t)sub.inner * sizeof(T), (size_t)geo.L, cudaMemcpyDeviceToDevice,
+                               c->stream) == cudaSuccess ? VP_OK : vp_fail(c, VP_ECUDA, "tuning copy failed");
+    else
+        rc = cudaMemcpyAsync(scratch, src, bytes, cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess
+                 ? VP_OK : vp_fail(c, VP_ECUDA, "tuning copy failed");
+    if (rc == VP_OK) rc = vp_launch_shift_table(c, kick, dim, dt, accel);
+    if (rc == VP_OK) {
+        void *f = c->f, *tab = c->d_shift;
+        c->f = scratch;
+        if (!geo.cls_from_inner) c->d_shift = static_cast<LineShift<T> *>(c->d_shift) + o0 / geo.cdiv;
+        rc = tune_on<T>(c, kick, dim, geo, sub, best);
+        c->f = f;
+        c->d_shift = tab;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(scratch);
+    return rc;
+}
+
+// time the candidates of geometry geo on sub (the tuning copy bound as f)
+template <typename T>
+int tune_on(vp_ctx *c, int kick, int dim, const SweepGeo &geo, const SweepGeo &sub, SweepTune best) {
+    int rc = VP_OK;
     constexpr int kMaxCand = 48;
     SweepTune cand[kMaxCand];
     int nc = 0;
@@ -760,7 +838,7 @@ int tune_t(vp_ctx *c, int kick, int dim) {
         float ms = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, c->stream);
-            rc = geo.inner > 1 ? launch_cols<T>(c, geo, cand[i]) : launch_rows<T>(c, geo, cand[i]);
+            rc = geo.inner > 1 ? launch_cols<T>(c, sub, cand[i]) : launch_rows<T>(c, sub, cand[i]);
             cudaEventRecord(e1, c->stream);
             if (rc) break;
             const cudaError_t se = cudaEventSynchronize(e1);
@@ -825,8 +903,8 @@ int vp_launch_sweep(vp_ctx *c, int kick, int dim) {
     return launch_sweep_t<double>(c, kick, dim);
 }
 
-int vp_tune_sweep(vp_ctx *c, int kick, int dim) {
+int vp_tune_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel) {
     if (c->tune[kick][dim].valid) return VP_OK;
-    if (c->g.precision == VP_F32) return tune_t<float>(c, kick, dim);
-    return tune_t<double>(c, kick, dim);
+    if (c->g.precision == VP_F32) return tune_t<float>(c, kick, dim, dt, accel);
+    return tune_t<double>(c, kick, dim, dt, accel);
 }

@@ -120,7 +120,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_ensemble_accel": (I, [P, P]),
             "vp_ensemble_set_tiles": (I, [P, I, I, I]),
             "vp_ensemble_get_tiles": (I, [P, P]),
-            "vp_ensemble_autotune": (I, [P]),
+            "vp_ensemble_autotune": (I, [P, D]),
             "vp_ensemble_step": (I, [P, D, I]),
             "vp_ensemble_sync": (I, [P]),
             "vp_ensemble_set_wait_limit": (I, [P, LL]),
@@ -353,8 +353,8 @@ def vp_ensemble_get_tiles(ens) -> dict:
     return {"W": out[0], "R": out[1], "ctas_per_sm": out[2]}
 
 
-def vp_ensemble_autotune(ens) -> None:
-    _echeck(ens, load().vp_ensemble_autotune(ens))
+def vp_ensemble_autotune(ens, dt: float) -> None:
+    _echeck(ens, load().vp_ensemble_autotune(ens, dt))
 
 
 def vp_ensemble_step(ens, dt: float, nsteps: int) -> None:

@@ -116,7 +116,7 @@ def test_autotune_leaves_f_unchanged_and_graph_matches_direct():
     stream = torch.cuda.Stream()
     ens, pool = _ensemble(specs, stream)
     before = pool.clone()
-    V.vp_ensemble_autotune(ens)
+    V.vp_ensemble_autotune(ens, 0.05)  # timed steps from a snapshot, restored
     V.vp_ensemble_sync(ens)
     assert torch.equal(before, pool)
     tiles = V.vp_ensemble_get_tiles(ens)
