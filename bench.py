@@ -58,8 +58,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--no-learned", action="store_true")
-    p.add_argument("--learned-draws", type=int, default=64)
-    p.add_argument("--ensemble-steps", type=int, default=20)
+    p.add_argument("--learned-draws", type=int, default=256, help="seeded fine-run draws for the training set")
+    p.add_argument("--ensemble-steps", type=int, default=500, help="timed ensemble steps (the configured run length)")
     p.add_argument("--no-schemes", action="store_true", help="skip the SL-MPP5 / RK-MPP5 sweep comparison")
     p.add_argument("--no-unsplit", action="store_true", help="skip the split / unsplit Test-1d step comparison")
     p.add_argument("--collapse", action="store_true",
@@ -565,7 +565,7 @@ def convergence_bench(ratios=(0.5, 1.1), ns=(64, 128, 256, 512), nref: int = 102
     return out
 
 
-def learned_bench(draws: int = 64, eval_steps: int = 20):
+def learned_bench(draws: int = 256, eval_steps: int = 20):
     """Learned spatial-sweep correction on the 2D2V Landau workload
     (k = (0.5, 0.5), alpha = 0.05): coarse 64^2 x 32^2 grid, trained on pairs
     from 64^2 x 128^2 MP7 FP32 runs of seeded (k, alpha) draws (PCG64 seed
