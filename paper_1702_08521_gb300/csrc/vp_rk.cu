@@ -65,7 +65,10 @@ struct StageStore {
 };
 
 // Strided lines: a tile of W consecutive lines (columns), rows at pitch W.
-template <typename T, bool PERIODIC, bool FULL>
+// PAIR (FP32): a thread walks two adjacent columns with the packed FP32 pair
+// arithmetic (each half rounds as the scalar instruction: the same bits); a
+// pair whose lines move in opposite directions is walked one line at a time.
+template <typename T, bool PERIODIC, bool FULL, bool PAIR>
 __global__ void __launch_bounds__(512) k_rk_cols(T *__restrict__ f, const LineShift<T> *__restrict__ tab,
                                                  SweepGeo geo, LimParams lp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -105,6 +108,58 @@ __global__ void __launch_bounds__(512) k_rk_cols(T *__restrict__ f, const LineSh
         }
     }
     __syncthreads();
+    const T alpha_t = (T)lp.alpha;
+    constexpr int GW = PERIODIC ? 1 : VP_GHOST;
+    if constexpr (PAIR) {
+        using vp_core::P2;
+        const unsigned seg = fdiv(threadIdx.x, geo.fd_w2);
+        const int cc = 2 * (int)(threadIdx.x - seg * (unsigned)(W >> 1));
+        const bool act = cc < wc && (int)seg < geo.nseg;
+        LineShift<float> sa{}, sb{};
+        int r0 = 0, r1 = 0;
+        bool both = false;
+        if (act) {
+            sa = tab[vp_core::line_class(geo, o, c0 + cc)];
+            sb = cc + 1 < wc ? tab[vp_core::line_class(geo, o, c0 + cc + 1)] : sa;
+            both = cc + 1 < wc && sa.sigma == sb.sigma;  // RK lines have no integer shift
+            r0 = (int)fdiv(seg * (unsigned)L, geo.fd_nseg);
+            r1 = (int)fdiv((seg + 1) * (unsigned)L, geo.fd_nseg);
+        }
+#pragma unroll 1
+        for (int stage = 0; stage < 3; ++stage) {
+            if (act) {
+                const float ca = stage == 0 ? 0.f : (stage == 1 ? 0.75f : 1.f / 3.f);
+                const float cv = stage == 0 ? 1.f : (stage == 1 ? 0.25f : 2.f / 3.f);
+                const float *src = stage == 0 ? a0 : (stage == 1 ? b0 : c0p);
+                float *sdst = stage == 0 ? b0 : c0p;  // stages 0, 1 write shared memory
+                if (both) {
+                    const vp_core::LineShiftP2 sh = vp_core::pair_shift(sa, sb);
+                    const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
+                    P2 *dst = stage == 2 ? reinterpret_cast<P2 *>(base + cc + (long long)i0 * geo.inner)
+                                         : reinterpret_cast<P2 *>(sdst + cc + i0 * W);
+                    const long long dstep = stage == 2 ? (long long)sh.sigma * (geo.inner >> 1)
+                                                       : (long long)sh.sigma * (W >> 1);
+                    StageStore<P2> sto{dst, reinterpret_cast<const P2 *>(a0 + cc + i0 * W), dstep,
+                                       (long long)sh.sigma * (W >> 1), P2(ca), P2(cv)};
+                    vp_core::walk<P2, 5, PERIODIC, FULL, GW>(reinterpret_cast<const P2 *>(src + cc), W >> 1, L, sh,
+                                                             r0, r1, P2((float)lp.alpha), lp.mp, lp.pp, sto);
+                } else {
+                    for (int k = (cc + 1 < wc ? 1 : 0); k >= 0; --k) {
+                        const LineShift<float> &sl = k ? sb : sa;
+                        const int i0 = sl.sigma > 0 ? r0 : r1 - 1;
+                        float *dst = stage == 2 ? base + cc + k + (long long)i0 * geo.inner : sdst + cc + k + i0 * W;
+                        const long long dstep = stage == 2 ? (long long)sl.sigma * geo.inner : (long long)sl.sigma * W;
+                        StageStore<float> sto{dst, a0 + cc + k + i0 * W, dstep, (long long)sl.sigma * W, ca, cv};
+                        vp_core::walk<float, 5, PERIODIC, FULL, GW>(src + cc + k, W, L, sl, r0, r1, (float)lp.alpha,
+                                                                    lp.mp, lp.pp, sto);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    (void)alpha_t;
     const unsigned seg = fdiv(threadIdx.x, geo.fd_w);
     const int cc = (int)(threadIdx.x - seg * (unsigned)W);
     const bool act = cc < wc && (int)seg < geo.nseg;
@@ -255,16 +310,29 @@ int launch_rk(vp_ctx *c, int kick, int dim) {
         geo.fd_w = make_fastdiv((unsigned)W);
         geo.fd_nseg = make_fastdiv((unsigned)nseg);
         geo.fd_wv = make_fastdiv((unsigned)(W / (16 / sizeof(T)) > 0 ? W / (16 / sizeof(T)) : 1));
-        const int threads = ((W * nseg + 31) / 32) * 32;
+        // FP32: two adjacent lines per thread unless the staged-load one-line
+        // kernels are requested (the same bits either way)
+        const bool pair = sizeof(T) == 4 && c->opt_impl != 1 && W % 2 == 0 && geo.inner % 2 == 0 &&
+                          (reinterpret_cast<uintptr_t>(c->f) & 7) == 0;
+        geo.fd_w2 = make_fastdiv((unsigned)(W >> 1 > 0 ? W >> 1 : 1));
+        const int threads = (((pair ? W >> 1 : W) * nseg + 31) / 32) * 32;
         const bool full = c->g.mp && c->g.pp;
+#define VP_RK_COLS(PER, FULL)                                                                                  \
+    do {                                                                                                       \
+        if (pair)                                                                                              \
+            k_rk_cols<T, PER, FULL, sizeof(T) == 4><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp); \
+        else                                                                                                   \
+            k_rk_cols<T, PER, FULL, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);    \
+    } while (0)
         if (geo.periodic && full)
-            k_rk_cols<T, true, true><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+            VP_RK_COLS(true, true);
         else if (geo.periodic)
-            k_rk_cols<T, true, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+            VP_RK_COLS(true, false);
         else if (full)
-            k_rk_cols<T, false, true><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+            VP_RK_COLS(false, true);
         else
-            k_rk_cols<T, false, false><<<(unsigned)tiles, threads, smem, c->stream>>>(f, tab, geo, lp);
+            VP_RK_COLS(false, false);
+#undef VP_RK_COLS
     } else {
         const int P = (L + 2 * VP_GHOST) | 1, Q = L | 1;
         int R = 4096 / L;
@@ -296,8 +364,12 @@ int launch_rk(vp_ctx *c, int kick, int dim) {
 
 template <typename T, bool FULL>
 void rk_attrs_one() {
-    cudaFuncSetAttribute(k_rk_cols<T, true, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_rk_cols<T, false, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rk_cols<T, true, FULL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rk_cols<T, false, FULL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (sizeof(T) == 4) {
+        cudaFuncSetAttribute(k_rk_cols<T, true, FULL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_rk_cols<T, false, FULL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
     cudaFuncSetAttribute(k_rk_rows<T, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
