@@ -10,7 +10,8 @@
 // dx.  A CTA stages its lines once, runs the three stages in shared memory
 // (f^n, f^(1), f^(2) side by side, a barrier between stages) and writes
 // f^{n+1} = f^n / 3 + 2/3 (f^(2) - nu L(f^(2))) once: one HBM pass for three
-// stages.  The scheme is Eulerian: it needs |nu| < 1/2 (the PP limiter's
+// stages.  FP32 strided sweeps walk two adjacent lines per thread with the
+// packed pair arithmetic, as the SL sweeps do.  The scheme is Eulerian: it needs |nu| < 1/2 (the PP limiter's
 // condition); the shift table flags a larger one in the context's status
 // word, which vp_sync reports.
 #include "vp_sweep_core.cuh"
