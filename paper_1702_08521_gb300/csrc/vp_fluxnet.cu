@@ -1,5 +1,5 @@
 // vp_fluxnet.cu -- learned flux correction on a coarser velocity grid
-// (a spec addition to the method, not in the paper).
+// (an addition to the method, not in the paper).
 //
 // A 25 -> 32 -> 32 -> 32 -> 1 ReLU network g corrects the mass that a
 // coarse-grid spatial sweep moves through an interface:
