@@ -1,7 +1,8 @@
 """FP64 reference of the learned flux correction (test infrastructure only).
 
-Not part of the paper: the learned correction is an addition to the method.  It is restated here in plain numpy, in double precision, so that the
-GPU training and inference kernels can be checked against it.
+Not part of the paper: the learned correction is an addition to the method.
+It is restated here in plain numpy, in double precision, so that the GPU
+training and inference kernels can be checked against it.
 
 Network (per interface of a spatial sweep; upwind-ordered stencil u_{-3..4} of
 the line, u_0 = upwind cell; u+_k / u-_k: the same cells on the lines of the
