@@ -164,6 +164,7 @@ void free_buffers(vp_ctx *c) {
     cudaFree(c->d_flag);
     cudaFree(c->d_status);
     cudaFree(c->d_netfrag);
+    cudaFree(c->d_learn_out);
     if (c->graph.valid) cudaGraphExecDestroy(c->graph.exec);
 }
 

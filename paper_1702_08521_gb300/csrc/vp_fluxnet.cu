@@ -549,8 +549,16 @@ __global__ void k_net_umma(const float *__restrict__ wts, unsigned char *__restr
     }
 }
 
-constexpr int kLC = 4;                        // interfaces per line in one network batch
 constexpr int kABytes = 128 * vp_umma::kK * 2;  // one 128 x 48 bf16 feature operand
+// interfaces per line in one network batch: three operands and the weights
+// take 46.5 KB of shared memory and 128 tensor-memory columns, so four CTAs
+// share an SM (all 512 columns)
+constexpr int kLC = 3;
+// tensor-memory columns of a CTA: the power of two >= 32 that holds LC
+// accumulators of 32 columns
+__host__ __device__ constexpr uint32_t tmem_cols(int lc) {
+    return lc <= 1 ? 32u : (lc <= 2 ? 64u : (lc <= 4 ? 128u : 256u));
+}
 
 // bf16 columns 0-31 of row r (in w) of an operand in the canonical layout
 __device__ __forceinline__ void store_row(unsigned char *op, int r, const uint32_t (&w)[16]) {
@@ -567,8 +575,9 @@ __device__ __forceinline__ void store_row(unsigned char *op, int r, const uint32
 // its own row back from tensor memory, applies ReLU, rounds to bf16 and
 // writes it as the next layer's A row.  Returns g of this thread's row of
 // each operand.  Bounded waits: on a timeout the status word is set.
+template <int LC>
 __device__ __forceinline__ void net_tc(unsigned char *A, const unsigned char *ops, uint32_t tmem, uint64_t *bar,
-                                       uint32_t &phase, int nb, float (&g)[kLC], int *status) {
+                                       uint32_t &phase, int nb, float (&g)[LC], int *status) {
     const int warp = threadIdx.x >> 5;
     const uint32_t a_s = vp_tma::saddr(A), w_s = vp_tma::saddr(ops);
     const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
@@ -604,24 +613,26 @@ __device__ __forceinline__ void net_tc(unsigned char *A, const unsigned char *op
             }
         } else {
 #pragma unroll
-            for (int b = 0; b < kLC; ++b) g[b] = b < nb ? vp_umma::ld1(tl + (uint32_t)(32 * b)) : 0.f;
+            for (int b = 0; b < LC; ++b) g[b] = b < nb ? vp_umma::ld1(tl + (uint32_t)(32 * b)) : 0.f;
         }
     }
 }
 
-template <bool PERIODIC>
-__global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__ f, LTile tl,
-                                                             const LineShift<float> *__restrict__ tab,
+// Reads f^n (fin, not written during the launch) through L2 and writes the
+// updated lines to fout; a thread reads its line and the two lines of the
+// neighbouring velocity cells row by row as it walks.
+template <bool PERIODIC, int LC>
+__global__ void __launch_bounds__(kTcThreads) k_learned_walk(const float *__restrict__ fin, float *__restrict__ fout,
+                                                             LTile tl, const LineShift<float> *__restrict__ tab,
                                                              const uint4 *__restrict__ netops, double lo,
                                                              double dvel, float alpha, int mode,
                                                              int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;
-    unsigned char *A = tsm;                                // kLC operands of 128 x 32 bf16
-    unsigned char *ops = tsm + kLC * kABytes;              // W1 W2 W3 w4, biases
-    float *tile = reinterpret_cast<float *>(ops + kOpAlloc);  // [L][pitch]
-    const int L = tl.L, NC = tl.NC, pitch = tl.pitch, T = tl.T;
+    unsigned char *A = tsm;                                // LC operands of 128 x 48 bf16
+    unsigned char *ops = tsm + LC * kABytes;               // W1 W2 W3 w4, biases
+    const int L = tl.L, NC = tl.NC, T = tl.T;
     const int cmod = (int)tl.cmod;
     const long long o = (long long)blockIdx.x / tl.tpo;
     const long long tin = (long long)blockIdx.x - o * tl.tpo;
@@ -633,38 +644,19 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__
         return (gb * tl.G + g) * tl.cmod * tl.cdiv + (long long)j * tl.cdiv + tb * T + t;
     };
     const long long obase = o * (long long)L * tl.inner;
-    // phase 0: network operands, tensor memory, mbarrier, the tile
+    // phase 0: network operands, tensor memory, mbarrier
     for (int e = threadIdx.x; e < kOpAlloc / 16; e += blockDim.x)
         reinterpret_cast<uint4 *>(ops)[e] = netops[e];
     // columns 32-47 of every A row: 1, 1 (the bias pair), then zeros
-    for (int b = 0; b < kLC; ++b)
+    for (int b = 0; b < LC; ++b)
 #pragma unroll
         for (int kk = 4; kk < vp_umma::kK / 8; ++kk)
             *reinterpret_cast<uint4 *>(A + b * kABytes + vp_umma::kmajor_offset(threadIdx.x, 8 * kk)) =
                 kk == 4 ? make_uint4(pack_bf16(1.f, 1.f), 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
-    if (threadIdx.x < 32) vp_umma::tmem_alloc(&tslot, 32 * kLC);
+    if (threadIdx.x < 32) vp_umma::tmem_alloc(&tslot, tmem_cols(LC));
     if (threadIdx.x == 0) {
         vp_tma::mbar_init(&bar, 1);
         vp_tma::fence_mbar_init();
-    }
-    {
-        // eight loads in flight per thread; a thread keeps its column, so the
-        // column's inner index is computed once
-        const int rstep = blockDim.x / NC > 0 ? (int)blockDim.x / NC : 1;
-        const int col = (int)threadIdx.x % NC, r0 = (int)threadIdx.x / NC;
-        if ((int)threadIdx.x < rstep * NC) {
-            const float *src = f + obase + col_c(col);
-            constexpr int U = 8;
-            int r = r0;
-            for (; r + (U - 1) * rstep < L; r += U * rstep) {
-                float v[U];
-#pragma unroll
-                for (int k = 0; k < U; ++k) v[k] = src[(long long)(r + k * rstep) * tl.inner];
-#pragma unroll
-                for (int k = 0; k < U; ++k) tile[(r + k * rstep) * pitch + col] = v[k];
-            }
-            for (; r < L; r += rstep) tile[r * pitch + col] = src[(long long)r * tl.inner];
-        }
     }
     vp_umma::fence_before_sync();
     __syncthreads();
@@ -697,13 +689,18 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__
         }
         return r;
     };
+    // the line and its velocity neighbours in f^n (row r at r inner)
+    const float *pu = fin + obase + col_c(colc);
+    const float *pp = fin + obase + col_c(cp >= 0 ? cp : colc);
+    const float *pm = fin + obase + col_c(cm >= 0 ? cm : colc);
     // cell value, velocity difference and velocity curvature at row r (wrapped
     // for periodic lines; outside [0, L) zero for zero-inflow lines)
     auto fetch_w = [&](int r, float &u, float &dv, float &cv) {
         const bool in = ok && (PERIODIC || (r >= 0 && r < L));
-        u = in ? tile[r * pitch + colc] : 0.f;
-        const float up = in && cp >= 0 ? tile[r * pitch + cp] : 0.f;
-        const float um = in && cm >= 0 ? tile[r * pitch + cm] : 0.f;
+        const long long o = (long long)r * tl.inner;
+        u = in ? __ldg(pu + o) : 0.f;
+        const float up = in && cp >= 0 ? __ldg(pp + o) : 0.f;
+        const float um = in && cm >= 0 ? __ldg(pm + o) : 0.f;
         dv = up - um;
         cv = fmaf(0.5f, up + um, -u);
     };
@@ -718,11 +715,11 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__
     float Min = 0.f;
     const long long cbase = obase + col_c(colc);
 #pragma unroll 1
-    for (int k0 = 0; k0 <= L; k0 += kLC) {
-        const int nb = L + 1 - k0 < kLC ? L + 1 - k0 : kLC;
-        float Mp[kLC], sc[kLC], mlo[kLC], mhi[kLC], u3[kLC], u4[kLC];
+    for (int k0 = 0; k0 <= L; k0 += LC) {
+        const int nb = L + 1 - k0 < LC ? L + 1 - k0 : LC;
+        float Mp[LC], sc[LC], mlo[LC], mhi[LC], u3[LC], u4[LC];
 #pragma unroll
-        for (int b = 0; b < kLC; ++b) {
+        for (int b = 0; b < LC; ++b) {
             if (b >= nb) break;
             // plain mass of interface k0 + b (CSL7, MP bounds as a clamp)
             const float dp = vp_core::curv(u[3], u[4], u[5]);
@@ -774,10 +771,10 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__
             dv[7] = dvn;
             cv[7] = cvn;
         }
-        float g[kLC];
-        net_tc(A, ops, tmem, &bar, phase, nb, g, status);
+        float g[LC];
+        net_tc<LC>(A, ops, tmem, &bar, phase, nb, g, status);
 #pragma unroll
-        for (int b = 0; b < kLC; ++b) {
+        for (int b = 0; b < LC; ++b) {
             if (b >= nb) break;
             float M = fmaf(sc[b], g[b], Mp[b]);
             if (mode == 2) M = fminf(fmaxf(M, vp_core::mul_rn(nu, mlo[b])), vp_core::mul_rn(nu, mhi[b]));
@@ -786,7 +783,7 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__
             const int k = k0 + b;
             if (ok && k >= 1) {
                 const int i = sg > 0 ? k - 1 : L - k;
-                f[cbase + (long long)i * tl.inner] = (u3[b] - M) + Min;
+                fout[cbase + (long long)i * tl.inner] = (u3[b] - M) + Min;
             }
             Min = M;
         }
@@ -795,7 +792,7 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(float *__restrict__
     __syncthreads();
     if (threadIdx.x < 32) {
         vp_umma::fence_after_sync();
-        vp_umma::tmem_dealloc(tmem, 32 * kLC);
+        vp_umma::tmem_dealloc(tmem, tmem_cols(LC));
     }
 }
 
@@ -873,9 +870,11 @@ LineGeo line_geo(const vp_grid &g, long long NX, long long NV, int kick, int dim
 int vp_learned_prepare(vp_ctx *c) {
     if (c->learned_ready) return VP_OK;
     if (!c->d_netfrag) VP_CUDA_TRY(c, cudaMalloc(&c->d_netfrag, kOpAlloc));
-    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the updated lines of a learned sweep (copied back into f after the walk)
+    if (!c->d_learn_out) VP_CUDA_TRY(c, cudaMalloc(&c->d_learn_out, (size_t)c->ncell * sizeof(float)));
+    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_walk<true, kLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
-    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VP_CUDA_TRY(c, cudaFuncSetAttribute(k_learned_walk<false, kLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
     c->learned_ready = 1;
     return VP_OK;
@@ -885,7 +884,7 @@ extern "C" {
 
 int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
                      int use_net, const float *f_snap) {
-    (void)f_snap;  // the tile holds every line's velocity neighbours: no snapshot is needed
+    (void)f_snap;  // the walk reads f^n as it is and writes the new lines to a buffer of its own
     if (!c || !c->f) return VP_EINVAL;
     if (c->g.precision != VP_F32 || c->g.order != 7)
         return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
@@ -922,12 +921,11 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
         tl.T = (int)T;
     }
     tl.NC = (int)(tl.G * q.cmod * tl.T);
-    tl.pitch = (tl.NC + 31) / 32 * 32;
+    tl.pitch = 0;
     tl.tblocks = q.cdiv / tl.T;
     tl.tpo = (NG / tl.G) * tl.tblocks;
     const int threads = kTcThreads;  // one 128-row operand: a thread per row, rows >= NC are idle
-    const size_t smem = (size_t)kLC * kABytes + kOpAlloc + (size_t)q.L * tl.pitch * sizeof(float);
-    if (smem > 200 * 1024) return vp_fail(c, VP_ENOTSUP, "lines too long for the learned sweep");
+    const size_t smem = (size_t)kLC * kABytes + kOpAlloc;
     const long long blocks = q.outer * tl.tpo;
     if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "learned sweep has too many tiles");
     rc = vp_launch_shift_table(c, kick, dim, dt, accel_dev);
@@ -936,14 +934,18 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     c->launches++;
     const LineShift<float> *tab = static_cast<const LineShift<float> *>(c->d_shift);
     const uint4 *ops = static_cast<const uint4 *>(c->d_netfrag);
+    const float *fin = static_cast<const float *>(c->f);
+    float *fout = static_cast<float *>(c->d_learn_out);
     if (q.periodic)
-        k_learned_walk<true><<<(unsigned)blocks, threads, smem, c->stream>>>(
-            static_cast<float *>(c->f), tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
+        k_learned_walk<true, kLC><<<(unsigned)blocks, threads, smem, c->stream>>>(
+            fin, fout, tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
     else
-        k_learned_walk<false><<<(unsigned)blocks, threads, smem, c->stream>>>(
-            static_cast<float *>(c->f), tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
+        k_learned_walk<false, kLC><<<(unsigned)blocks, threads, smem, c->stream>>>(
+            fin, fout, tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
+    VP_CUDA_TRY(c, cudaMemcpyAsync(c->f, fout, (size_t)c->ncell * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->stream));
     return VP_OK;
 }
 

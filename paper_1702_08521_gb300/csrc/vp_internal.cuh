@@ -130,6 +130,7 @@ struct vp_ctx {
     long long launches;
     int *d_status;                      // device-side error word (bounded waits)
     void *d_netfrag;                    // network weights in MMA fragment order (allocated on first use)
+    void *d_learn_out;                  // learned sweep: the updated lines (allocated on first use)
     int learned_ready;                  // learned-sweep buffers allocated, kernel attributes set
     int opt_impl;                       // 0 auto, 1 staged, 2 TMA
     int opt_autotune;                   // 1: time candidate tiles on first use
