@@ -707,8 +707,26 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(const float *__rest
     float u[8], dv[8], cv[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) fetch_w(wrap(q + (m - 3) * sg), u[m], dv[m], cv[m]);
-    // the row entering the window after interface k: q + 5 sg, wrapped incrementally
+    // the row entering the window after interface k: q + (5 + k) sg, wrapped
+    // incrementally.  Rows enter as raw values (u, u+, u-) loaded one batch
+    // ahead: the next batch's rows are requested before this batch's network
+    // round trips, which hide the L2 latency.
     int rn = wrap(q + 5 * sg);
+    auto load_raw = [&](float &a, float &ap, float &am) {
+        const bool in = ok && (PERIODIC || (rn >= 0 && rn < L));
+        const long long o = (long long)rn * tl.inner;
+        a = in ? __ldg(pu + o) : 0.f;
+        ap = in && cp >= 0 ? __ldg(pp + o) : 0.f;
+        am = in && cm >= 0 ? __ldg(pm + o) : 0.f;
+        rn += sg;
+        if (PERIODIC) {
+            rn = rn == L ? 0 : rn;
+            rn = rn < 0 ? L - 1 : rn;
+        }
+    };
+    float ru[LC], rp[LC], rm[LC];
+#pragma unroll
+    for (int b = 0; b < LC; ++b) load_raw(ru[b], rp[b], rm[b]);
     // MP carries: curvature of the upwind cell, d^{M4} at its upwind face
     float dc = vp_core::curv(u[2], u[3], u[4]);
     float m4m = vp_core::dm4(vp_core::curv(u[1], u[2], u[3]), dc);
@@ -717,6 +735,9 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(const float *__rest
 #pragma unroll 1
     for (int k0 = 0; k0 <= L; k0 += LC) {
         const int nb = L + 1 - k0 < LC ? L + 1 - k0 : LC;
+        float xu[LC], xp[LC], xm[LC];  // the next batch's rows
+#pragma unroll
+        for (int b = 0; b < LC; ++b) load_raw(xu[b], xp[b], xm[b]);
         float Mp[LC], sc[LC], mlo[LC], mhi[LC], u3[LC], u4[LC];
 #pragma unroll
         for (int b = 0; b < LC; ++b) {
@@ -754,13 +775,7 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(const float *__rest
             // advance the window and the MP carries
             dc = dp;
             m4m = m4p;
-            float un, dvn, cvn;
-            fetch_w(rn, un, dvn, cvn);
-            rn += sg;
-            if (PERIODIC) {
-                rn = rn == L ? 0 : rn;
-                rn = rn < 0 ? L - 1 : rn;
-            }
+            const float un = ru[b], dvn = rp[b] - rm[b], cvn = fmaf(0.5f, rp[b] + rm[b], -un);
 #pragma unroll
             for (int m = 0; m < 7; ++m) {
                 u[m] = u[m + 1];
@@ -773,6 +788,12 @@ __global__ void __launch_bounds__(kTcThreads) k_learned_walk(const float *__rest
         }
         float g[LC];
         net_tc<LC>(A, ops, tmem, &bar, phase, nb, g, status);
+#pragma unroll
+        for (int b = 0; b < LC; ++b) {
+            ru[b] = xu[b];
+            rp[b] = xp[b];
+            rm[b] = xm[b];
+        }
 #pragma unroll
         for (int b = 0; b < LC; ++b) {
             if (b >= nb) break;
