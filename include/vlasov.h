@@ -236,9 +236,12 @@ int vp_sync(vp_ctx *ctx);
  *                      the same bits as 1);
  *   VP_OPT_AUTOTUNE:   1 (default) times candidate tile shapes of each sweep
  *                      geometry on its first use, with that sweep's shifts,
- *                      on a copy of a prefix of f (at most 256 MB, allocated
- *                      for the tuning and freed; f is left unchanged; without
- *                      room for it the defaults stay), and of the unsplit
+ *                      on a copy of a window of f (at most 256 MB of whole
+ *                      lines, centred on the box's central spatial cell so
+ *                      that it holds the populated part of phase space;
+ *                      allocated for the tuning and freed; f is left
+ *                      unchanged; without room for it the defaults stay),
+ *                      and of the unsplit
  *                      step (f -> scratch_dev), and keeps the fastest; 0 uses
  *                      fixed defaults;
  *   VP_OPT_WAIT_LIMIT: iterations of each bounded device-side wait in the
@@ -343,12 +346,16 @@ long long vp_ensemble_launch_count(const vp_ens *ens);
 /* one sweep of the grid of ctx (FP32, order 7) with the network correction
  * (use_net = 1: PP on the corrected mass; use_net = 2: MP bounds then PP;
  * drifts only) or without it (use_net = 0: the same call as vp_drift_sweep /
- * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); in place.  Each CTA
- * stages all velocity cells of the sweep's velocity axis for its lines, so
- * every line's velocity neighbours are read before any cell is written:
- * f_snap_dev is not read (kept in the signature; may be NULL).  At most 256
- * velocity cells on that axis (VP_ENOTSUP beyond).  VP_ENOTSUP for use_net
- * with kick = 1, VP_EINVAL for use_net outside 0..2. */
+ * vp_kick_sweep); wts_dev: VP_NET_NPARAM floats (device); f is updated in
+ * place as seen by the caller.  With the network on, the walk reads f^n as it
+ * is (a line's velocity neighbours included) and writes the new lines to a
+ * buffer of f's size that the library owns, then copies that buffer back
+ * into f on the context's stream; the buffer is allocated by the first
+ * learned sweep or step of the context (not inside a stream capture) and
+ * freed with it.  f_snap_dev is not read (kept in the signature; may be
+ * NULL).  At most 128 velocity cells on the sweep's velocity axis (one
+ * 128-row MMA operand per interface step; VP_ENOTSUP beyond, f unchanged).
+ * VP_ENOTSUP for use_net with kick = 1, VP_EINVAL for use_net outside 0..2. */
 int vp_learned_sweep(vp_ctx *ctx, int kick, int dim, double dt, const double *accel_dev,
                      const float *wts_dev, int use_net, const float *f_snap_dev);
 

@@ -283,3 +283,27 @@ def test_learned_step_replays_the_sweep_sequence():
     assert np.array_equal(from_gpu(a), from_gpu(b))
     a.close()
     b.close()
+
+
+def test_learned_sweep_velocity_axis_limit():
+    """One 128-row MMA operand per interface step: 128 velocity cells on the
+    sweep's velocity axis run (mass kept, f >= 0), 129 are refused with
+    VP_ENOTSUP and f is left as it was."""
+    import torch
+    w = _t(N.pack(_params(5, 0.3)), torch.float32)
+    for nv, ok in ((128, True), (129, False)):
+        g = dict(dims=1, nx=[16], nv=[nv], xlo=[0.0], xhi=[4.0], vlo=[-3.0], vhi=[3.0], order=7)
+        sim, og = both(g, V.VP_F32)
+        f0 = _f32(inputs.random_f(og.NX * og.NV, seed=nv))
+        to_gpu(sim, f0)
+        if ok:
+            V.vp_learned_sweep(sim.ctx, 0, 0, 0.3, None, w, 1)
+            f1 = from_gpu(sim)
+            assert f1.min() >= 0.0
+            assert abs(f1.sum() - f0.sum()) <= 1e-5 * f0.sum()
+        else:
+            with pytest.raises(V.VpError) as e:
+                V.vp_learned_sweep(sim.ctx, 0, 0, 0.3, None, w, 1)
+            assert e.value.code == V.VP_ENOTSUP
+            assert np.array_equal(from_gpu(sim), f0)
+        sim.close()
