@@ -58,6 +58,7 @@ struct RunDesc {
     long long NX, NV;
     double xlo[2], hx[2], vlo[2], hv[2];
     long long acc_off, rho_off;
+    long long dsh_off;  // drift shifts: axis 0 at [dsh_off, dsh_off + nv[0]), axis 1 after
     double coupling, rho_bg;
     int pois_order;
     int nstage;
@@ -120,9 +121,24 @@ __device__ __forceinline__ LineShift<float> ens_shift(double speed, double dth, 
     return sh;
 }
 
+// The drift shifts of every run for the step's dt (one entry per velocity
+// cell of each drift axis; the same decomposition as a tile would make of
+// its lines), computed once per dt outside the step: drift tiles read them
+// instead of spending the narrow FP64 pipe on every line of every tile.
+__global__ void k_ens_drift_table(const RunDesc *__restrict__ runs, LineShift<float> *__restrict__ tab,
+                                  EnsParams P) {
+    const RunDesc &r = runs[blockIdx.x];
+    for (int axis = 0; axis < r.dims; ++axis) {
+        const double dth = P.dt / r.hx[axis];  // drifts move by the full dt
+        const long long base = r.dsh_off + (axis ? r.nv[0] : 0);
+        for (int j = threadIdx.x; j < r.nv[axis]; j += blockDim.x)
+            tab[base + j] = ens_shift(vp_core::cell_centre(r.vlo[axis], r.hv[axis], j), dth, P);
+    }
+}
+
 template <int ORDER, bool PER>
 __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int tile,
-                          const double *acc_pool, const EnsParams &P, float *sm) {
+                          const double *acc_pool, const LineShift<float> *dsh, const EnsParams &P, float *sm) {
     // zero-inflow lines get VP_GHOST zero rows on each side (direct walks)
     constexpr int GP = PER ? 0 : VP_GHOST;
     const int L = s.L;
@@ -133,10 +149,13 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
     const int wc = (int)((s.inner - c0) < W ? (s.inner - c0) : W);
     float *base = pool + r.f_off + o * L * s.inner + c0;
     float *data = sm + GP * W;  // row 0
-    __shared__ double s_dth;
-    if (threadIdx.x == 0) {
+    // a kick tile holds one spatial point: its shift, made once (thread 0,
+    // while the tile is staged) and shared; drift tiles read the table
+    __shared__ LineShift<float> s_sh;
+    if (threadIdx.x == 0 && s.kick) {
         const double dt = s.half ? 0.5 * P.dt : P.dt;
-        s_dth = dt / (s.kick ? r.hv[s.axis] : r.hx[s.axis]);
+        const unsigned cls = (unsigned)(o / s.cdiv);
+        s_sh = ens_shift(ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls), dt / r.hv[s.axis], P);
     }
     for (int c = threadIdx.x; c < GP * W; c += blockDim.x) {
         sm[c] = 0.f;
@@ -188,12 +207,7 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
     const int cc = threadIdx.x % W, seg = threadIdx.x / W;
     if (cc < wc && seg < nseg) {
         const unsigned cls = s.cls_from_inner ? (unsigned)(((c0 + cc) / s.cdiv) % s.cmod) : (unsigned)(o / s.cdiv);
-        double speed;
-        if (s.kick)
-            speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
-        else
-            speed = vp_core::cell_centre(r.vlo[s.axis], r.hv[s.axis], (int)cls);
-        const LineShift<float> sh = ens_shift(speed, s_dth, P);
+        const LineShift<float> sh = s.kick ? s_sh : dsh[r.dsh_off + (s.axis ? r.nv[0] : 0) + cls];
         const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         struct St {
@@ -220,8 +234,16 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
     const long long l0 = (long long)tile * R;
     const int nl = (int)((s.outer - l0) < R ? (s.outer - l0) : R);
     float *base = pool + r.f_off + l0 * L;
+    // lines of one spatial point (a 2D run's v2 kick): one shift, made once by
+    // thread 0 while the tile is staged; otherwise one per line
+    const long long cfirst = l0 / s.cdiv;
+    const bool uniform = cfirst == (l0 + nl - 1) / s.cdiv;
     __shared__ double s_dth;
-    if (threadIdx.x == 0) s_dth = (s.half ? 0.5 * P.dt : P.dt) / r.hv[s.axis];
+    __shared__ LineShift<float> s_sh;
+    if (threadIdx.x == 0) {
+        s_dth = (s.half ? 0.5 * P.dt : P.dt) / r.hv[s.axis];
+        if (uniform) s_sh = ens_shift(ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cfirst), s_dth, P);
+    }
     for (int k = threadIdx.x; k < nl * GP; k += blockDim.x) {
         const int ln = k / GP, g = k - ln * GP;
         in[ln * Pp + g] = 0.f;
@@ -256,8 +278,8 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
     const int line = threadIdx.x % R, seg = threadIdx.x / R;
     if (line < nl && seg < nseg) {
         const unsigned cls = (unsigned)((l0 + line) / s.cdiv);
-        const double speed = ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls);
-        const LineShift<float> sh = ens_shift(speed, s_dth, P);
+        const LineShift<float> sh =
+            uniform ? s_sh : ens_shift(ldcg(acc_pool + r.acc_off + (long long)s.axis * r.NX + cls), s_dth, P);
         const int r0 = seg * L / nseg, r1 = (seg + 1) * L / nseg;
         const int i0 = sh.sigma > 0 ? r0 : r1 - 1;
         struct St {
@@ -432,7 +454,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
                                                        unsigned *__restrict__ ctr, double *acc_pool,
                                                        double *rho_pool, EnsParams P,
                                                        int *__restrict__ status, const double2 *__restrict__ tw,
-                                                       const double *__restrict__ green, double2 *fftbuf) {
+                                                       const double *__restrict__ green, double2 *fftbuf,
+                                                       const LineShift<float> *__restrict__ dsh) {
     extern __shared__ __align__(16) unsigned char ens_smem[];
     __shared__ int s_item;
     __shared__ int s_ok;
@@ -460,9 +483,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
         if (!s_ok) return;
         if (s.kind == ST_COLS) {
             if (s.periodic)
-                tile_cols<ORDER, true>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
+                tile_cols<ORDER, true>(pool, r, s, e.tile, acc_pool, dsh, P, reinterpret_cast<float *>(ens_smem));
             else
-                tile_cols<ORDER, false>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
+                tile_cols<ORDER, false>(pool, r, s, e.tile, acc_pool, dsh, P, reinterpret_cast<float *>(ens_smem));
         } else if (s.kind == ST_ROWS) {
             tile_rows<ORDER>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
         } else if (s.kind == ST_MOMENT) {
@@ -520,6 +543,10 @@ struct vp_ens {
     double2 *d_tw;     // FFT twiddles (kTwN / 2 entries)
     double *d_green;   // per run: S / lambda(k) / NX at every Fourier mode (rho layout)
     double2 *d_fft;    // per run: transform scratch of runs too large for shared memory (rho layout)
+    LineShift<float> *d_dsh;  // drift shifts of every run for dsh_dt (see k_ens_drift_table)
+    long long dsh_total;
+    double dsh_dt;
+    int dsh_valid;
     long long acc_total, rho_total;
     RunDesc *d_runs;
     EnsItem *d_items_step, *d_items_field;
@@ -659,6 +686,20 @@ static int upload_plan(vp_ens *e) {
 
 // the field pass waits on stage - 1 of the full list; give it its own view in
 // which the density stage (2D) precedes Poisson and nothing precedes density
+// the drift shift table for dt (before a step graph is captured; never inside one)
+static int ensure_drift_table(vp_ens *e, double dt) {
+    if (e->dsh_valid && e->dsh_dt == dt) return VP_OK;
+    EnsParams P = e->P;
+    P.dt = dt;
+    k_ens_drift_table<<<(unsigned)e->runs.size(), 128, 0, e->stream>>>(e->d_runs, e->d_dsh, P);
+    e->launches++;
+    const cudaError_t er = cudaGetLastError();
+    if (er != cudaSuccess) return ens_fail(e, VP_ECUDA, cudaGetErrorString(er));
+    e->dsh_valid = 1;
+    e->dsh_dt = dt;
+    return VP_OK;
+}
+
 static int launch_pass(vp_ens *e, const EnsItem *items, int nitems, double dt) {
     EnsParams P = e->P;
     P.dt = dt;
@@ -668,11 +709,11 @@ static int launch_pass(vp_ens *e, const EnsItem *items, int nitems, double dt) {
     if (e->P.order == 7)
         k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
                                                              e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
-                                                             e->d_green, e->d_fft);
+                                                             e->d_green, e->d_fft, e->d_dsh);
     else
         k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
                                                              e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
-                                                             e->d_green, e->d_fft);
+                                                             e->d_green, e->d_fft, e->d_dsh);
     e->launches++;
     const cudaError_t er = cudaGetLastError();
     if (er != cudaSuccess) return ens_fail(e, VP_ECUDA, cudaGetErrorString(er));
@@ -701,7 +742,7 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
     e->P.wp = vp_csl_weight_polys(order);
     for (int j = 0; j < 7; ++j)
         for (int k = 0; k < 7; ++k) e->P.wpf[j][k] = (float)e->P.wp.c[j][k];
-    long long off = 0, aoff = 0, roff = 0;
+    long long off = 0, aoff = 0, roff = 0, soff = 0;
     int slot = 0;
     for (int i = 0; i < nruns; ++i) {
         const vp_run_desc &d = runs[i];
@@ -734,23 +775,27 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
         r.f_off = off;
         r.acc_off = aoff;
         r.rho_off = roff;
+        r.dsh_off = soff;
         r.coupling = d.coupling;
         r.rho_bg = d.rho_bg;
         r.pois_order = d.pois_order == 2 || d.pois_order == 4 ? d.pois_order : 6;
         off += ((r.NX * r.NV + 31) / 32) * 32;  // 128-byte aligned runs
         aoff += r.dims * r.NX;
         roff += r.NX;
+        soff += r.nv[0] + (r.dims > 1 ? r.nv[1] : 0);
         e->runs.push_back(r);
     }
     e->pool_cells = off;
     e->acc_total = aoff;
     e->rho_total = roff;
+    e->dsh_total = soff;
     for (RunDesc &r : e->runs) build_stages(r, e->P.W, e->P.R, e->P.xpt, slot);
     e->nslots = slot;
     build_items(e);
     if (cudaMalloc(&e->d_acc, sizeof(double) * aoff) != cudaSuccess ||
         cudaMalloc(&e->d_rho, sizeof(double) * roff) != cudaSuccess ||
         cudaMalloc(&e->d_fft, sizeof(double2) * roff) != cudaSuccess ||
+        cudaMalloc(&e->d_dsh, sizeof(LineShift<float>) * soff) != cudaSuccess ||
         cudaMalloc(&e->d_ctr, sizeof(unsigned) * (slot + 1)) != cudaSuccess ||
         cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess) {
         vp_ensemble_destroy(e);
@@ -821,6 +866,7 @@ void vp_ensemble_destroy(vp_ens *e) {
     cudaFree(e->d_acc);
     cudaFree(e->d_rho);
     cudaFree(e->d_fft);
+    cudaFree(e->d_dsh);
     cudaFree(e->d_tw);
     cudaFree(e->d_green);
     cudaFree(e->d_ctr);
@@ -889,11 +935,13 @@ int vp_ensemble_field(vp_ens *e) {
         if (e->P.order == 7)
             k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
                                                                  (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft);
+                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft,
+                                                                 e->d_dsh);
         else
             k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
                                                                  (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft);
+                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft,
+                                                                 e->d_dsh);
         e->launches++;
         if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "field pass failed");
     }
@@ -982,8 +1030,9 @@ int vp_ensemble_autotune(vp_ens *e, double dt) {
                cudaMemcpyAsync(e->d_acc, snap_acc, sizeof(double) * e->acc_total, cudaMemcpyDeviceToDevice,
                                e->stream) == cudaSuccess;
     };
-    int rc = VP_OK;
-    if (cudaMemcpyAsync(snap_f, e->pool, sizeof(float) * e->pool_cells, cudaMemcpyDeviceToDevice, e->stream) !=
+    int rc = ensure_drift_table(e, dt);
+    if (rc == VP_OK &&
+        cudaMemcpyAsync(snap_f, e->pool, sizeof(float) * e->pool_cells, cudaMemcpyDeviceToDevice, e->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(snap_acc, e->d_acc, sizeof(double) * e->acc_total, cudaMemcpyDeviceToDevice, e->stream) !=
             cudaSuccess)
@@ -1038,6 +1087,9 @@ int vp_ensemble_autotune(vp_ens *e, double dt) {
 
 int vp_ensemble_step(vp_ens *e, double dt, int nsteps) {
     if (!e || !e->pool || nsteps < 0 || !std::isfinite(dt)) return VP_EINVAL;
+    if (nsteps == 0) return VP_OK;
+    const int trc = ensure_drift_table(e, dt);
+    if (trc) return trc;
     const bool use_graph = e->stream != nullptr && e->stream != cudaStreamLegacy;
     if (use_graph && !(e->graph_valid && e->graph_dt == dt)) {
         if (e->graph_valid) {
