@@ -3,18 +3,23 @@
 // kernel launch, the step captured in a CUDA graph.
 //
 // Work queue: one step of every run is a list of items (run, stage, tile)
-// sorted by stage.  Each CTA of a persistent grid pops the next item with an
-// atomic counter, waits (bounded) until the previous stage of that run has
-// finished all its tiles, processes the tile and counts it done.  Items are
-// popped in queue order by running CTAs only, so every wait is on work that a
-// running CTA already holds: no deadlock, whatever the residency.
+// sorted by stage.  Each CTA of a persistent grid pops items with an atomic
+// counter (the next one while it works on the current one), waits (bounded)
+// until the previous stage of that run has finished all its tiles, processes
+// the tile and counts it done.  Items are popped in queue order by running
+// CTAs only, and a CTA takes up its popped item right after its current one,
+// which comes earlier in the queue; every item's dependencies come earlier
+// still, so the earliest unfinished item is always being worked on: no
+// deadlock, whatever the residency.
 //
 // Stages of a KDK step (Eq. 55), per run:
 //   1D1V: kick v (dt/2) | drift x (dt) | density + Poisson | kick v (dt/2)
 //   2D2V: kick v1, kick v2 (dt/2) | drift x2, drift x1 (dt) | density |
 //         Poisson | kick v1, kick v2 (dt/2)
-// Sweeps reuse the line walker of the single-run kernels; the shift of every
-// line is decomposed in FP64 on the fly.  Data written by other CTAs inside
+// Sweeps reuse the line walker of the single-run kernels.  A kick tile's
+// lines share one spatial point, so thread 0 decomposes its shift in FP64
+// once per tile; drift shifts depend only on dt and come from a table made
+// once per dt (k_ens_drift_table).  Data written by other CTAs inside
 // the launch (f of the previous stage, density, field) is read with L1-bypass
 // loads (ld.global.cg).
 #include <cmath>
@@ -461,9 +466,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
     __shared__ int s_ok;
     unsigned *head = ctr;
     unsigned *done = ctr + 1;
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+    __syncthreads();
     while (true) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
-        __syncthreads();
         const int it = s_item;
         if (it >= nitems) break;
         const EnsItem e = items[it];
@@ -481,6 +486,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
         }
         __syncthreads();
         if (!s_ok) return;
+        // every thread has read s_item: the next item is popped now (by a thread
+        // of the second warp), its latency hidden behind this item's work; the
+        // barrier that ends this item publishes it
+        if (threadIdx.x == 32) s_item = (int)atomicAdd(head, 1u);
         if (s.kind == ST_COLS) {
             if (s.periodic)
                 tile_cols<ORDER, true>(pool, r, s, e.tile, acc_pool, dsh, P, reinterpret_cast<float *>(ens_smem));
