@@ -468,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
     unsigned *done = ctr + 1;
     if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
     __syncthreads();
+    int met_run = -1, met_stage = -1;  // thread 0: the last dependency seen met (counters only grow)
     while (true) {
         const int it = s_item;
         if (it >= nitems) break;
@@ -476,11 +477,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
         const StageDesc &s = r.st[e.stage];
         if (threadIdx.x == 0) {
             s_ok = 1;
-            if (e.stage > 0) {
+            if (e.stage > 0 && (e.run != met_run || e.stage != met_stage)) {
                 const StageDesc &prev = r.st[e.stage - 1];
                 if (!wait_count(done + prev.done_slot, (unsigned)prev.tiles, P.wait_limit)) {
                     atomicExch(status, VP_ETIMEOUT);
                     s_ok = 0;
+                } else {
+                    met_run = e.run;
+                    met_stage = e.stage;
                 }
             }
         }

@@ -132,3 +132,32 @@ def test_autotune_leaves_f_unchanged_and_graph_matches_direct():
     assert rel_l1(pool2[:n].double().cpu().numpy(), pool[:n].double().cpu().numpy()) <= 1e-6
     V.vp_ensemble_destroy(ens)
     V.vp_ensemble_destroy(ens2)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_ensemble_follows_a_change_of_dt(graph):
+    """Steps at one dt, then at another, then back (the drift shifts come from
+    a table made once per dt; a stale one would move every drift by the old
+    shift): every member against the single-run path after the same
+    sequence, with the step graph (a stream of its own) and with direct
+    launches (the legacy stream)."""
+    import torch
+    specs = _runs()
+    stream = torch.cuda.Stream() if graph else None
+    ens, pool = _ensemble(specs, stream)
+    seq = [(0.05, 4), (0.03, 3), (0.05, 2)]
+    for dt, n in seq:
+        V.vp_ensemble_step(ens, dt, n)
+    V.vp_ensemble_sync(ens)
+    for i, s in enumerate(specs):
+        sim = V.Simulation(_grid(s), precision=V.VP_F32)
+        V.vp_init_f(sim.ctx, *_ic(s))
+        sim.field()
+        for dt, n in seq:
+            sim.step(dt, n, split=V.VP_SPLIT_KDK)
+        sim.sync()
+        ref = sim.f.double().cpu().numpy()
+        got = _run_slice(ens, pool, i, s)
+        assert rel_l1(got, ref) <= 1e-6, (i, rel_l1(got, ref))
+        sim.close()
+    V.vp_ensemble_destroy(ens)
