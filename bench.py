@@ -61,6 +61,10 @@ def parse():
     p.add_argument("--learned-draws", type=int, default=256, help="seeded fine-run draws for the training set")
     p.add_argument("--ensemble-steps", type=int, default=500, help="timed ensemble steps (the configured run length)")
     p.add_argument("--no-schemes", action="store_true", help="skip the SL-MPP5 / RK-MPP5 sweep comparison")
+    p.add_argument("--profile-leg", default=None, choices=["ensemble", "unsplit"],
+                   help="run only that leg's profiled launches (for ncu --profile-from-start off) and exit")
+    p.add_argument("--profile-n", type=int, default=4096, help="unsplit profile: cells per axis")
+    p.add_argument("--profile-nv", type=int, default=2, help="unsplit profile: velocity cells per axis")
     p.add_argument("--no-unsplit", action="store_true", help="skip the split / unsplit Test-1d step comparison")
     p.add_argument("--collapse", action="store_true",
                    help="add the Sec. 3.4 uniform-sphere collapse (64^3 x 32^3 to t = 8T)")
@@ -226,10 +230,12 @@ def job_rate(t_local: float, units_local: int, world: int, device=None):
     return tmax, world * units_local / tmax
 
 
-def ensemble_bench(steps: int, warmup: int = 3):
+def ensemble_bench(steps: int, warmup: int = 3, profile: bool = False):
     """Batched-ensemble workload (512 uneven 1D1V runs + 8 2D2V 64^2 x 64^2
     Landau runs from PCG64(1702)), FP32 MP7+PP, dt = 0.05, KDK: one persistent
-    launch per step of all runs, graph-captured, autotuned tiles."""
+    launch per step of all runs, graph-captured, autotuned tiles.  profile:
+    after the warm-up, one step inside torch.cuda.profiler.start() / stop()
+    (for a profiler started with profiling off), nothing timed."""
     import torch
     from paper_1702_08521_gb300 import inputs
     from paper_1702_08521_gb300 import vlasov as V
@@ -257,6 +263,13 @@ def ensemble_bench(steps: int, warmup: int = 3):
     V.vp_ensemble_autotune(ens, 0.05)
     V.vp_ensemble_step(ens, 0.05, warmup)
     V.vp_ensemble_sync(ens)
+    if profile:
+        torch.cuda.profiler.start()
+        V.vp_ensemble_step(ens, 0.05, 1)
+        V.vp_ensemble_sync(ens)
+        torch.cuda.profiler.stop()
+        V.vp_ensemble_destroy(ens)
+        return {"profiled": "one ensemble step"}
     l0 = V.vp_ensemble_launch_count(ens)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -364,6 +377,29 @@ def scheme_compare_bench(sim, cfg, reps: int = 2):
     out["all_kinds"] = {"sl_mpp5_ms": round(tot["sl_mpp5"], 4), "rk_mpp5_ms": round(tot["rk_mpp5"], 4),
                         "ratio": round(tot["rk_mpp5"] / tot["sl_mpp5"], 3)}
     return out
+
+
+def unsplit_profile(n: int, nv: int):
+    """The unsplit Test-1d step of unsplit_bench's case (n, nv) for a profiler
+    started with profiling off: the tuning call and two steps, then three
+    single steps inside torch.cuda.profiler.start() / stop()."""
+    import torch
+    from paper_1702_08521_gb300 import inputs
+    from paper_1702_08521_gb300 import vlasov as V
+    cfg = inputs.advect_2d(n, 1, nv=nv)
+    sim = V.Simulation(cfg["grid"], precision=V.VP_F32)
+    V.vp_init_f(sim.ctx, *cfg["ic"])
+    sc = torch.empty_like(sim.f)
+    dt = 0.02 / n
+    V.vp_drift_unsplit(sim.ctx, dt, 2, sc)
+    sim.sync()
+    torch.cuda.profiler.start()
+    for _ in range(3):
+        V.vp_drift_unsplit(sim.ctx, dt, 1, sc)
+    sim.sync()
+    torch.cuda.profiler.stop()
+    sim.close()
+    return {"profiled": f"three unsplit steps, {n}^2 x {nv}^2"}
 
 
 def unsplit_bench(cases=((512, 1, 400), (4096, 1, 100), (4096, 2, 40)), reps: int = 3):
@@ -740,6 +776,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_leg:
+        out = ensemble_bench(0, profile=True) if args.profile_leg == "ensemble" else \
+            unsplit_profile(args.profile_n, args.profile_nv)
+        print(json.dumps(out))
+        return 0
     import torch
     import torch.distributed as dist
     from paper_1702_08521_gb300 import vlasov as V
