@@ -147,6 +147,24 @@ int vp_upload_f(vp_ctx *ctx, const void *host, size_t bytes);
 int vp_download_f(vp_ctx *ctx, void *host, size_t bytes);
 
 /*
+ * vp_host_alloc -- page-locked host memory for the copies above, backed by
+ * transparent huge pages where the kernel provides them: an anonymous
+ * mapping aligned to the huge-page size, advised for huge pages and
+ * registered with the CUDA driver (cudaHostRegister).  Copies from and to
+ * it need one address translation per huge page instead of one per base
+ * page; with f of tens of GB and the sweeps touching all of device memory
+ * between copies, a cudaHostAlloc buffer of base pages was seen to copy at
+ * half the rate.  The paper has no counterpart (its runs stay on the
+ * machine).  *out receives the pointer (host-readable and writable, zero
+ * filled); VP_EINVAL for bytes == 0 or out == NULL, VP_ENOMEM if the mapping
+ * fails, VP_ECUDA if registration fails (nothing is left allocated).
+ * vp_host_free unregisters and unmaps a pointer vp_host_alloc returned
+ * (VP_EINVAL for any other pointer).  Both synchronise with the device.
+ */
+int vp_host_alloc(size_t bytes, void **out);
+int vp_host_free(void *p);
+
+/*
  * vp_drift_sweep -- advance f by the 1D advection along spatial axis `dim`
  * (0-based) at speed v_dim for a time dt (Eq. 4): every line along x_dim is
  * shifted by s = v dt / dx_dim cells, split as s = N + zeta with N the

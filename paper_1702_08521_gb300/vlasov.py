@@ -15,6 +15,8 @@ import ctypes
 import os
 import threading
 
+import numpy as np
+
 from . import _build
 
 VP_OK, VP_EINVAL, VP_ECUDA, VP_ENOMEM, VP_ETIMEOUT, VP_ENONFINITE, VP_ENOTSUP, VP_ECFL = 0, -1, -2, -3, -4, -5, -6, -7
@@ -98,6 +100,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_init_f": (I, [P, I, P, I]),
             "vp_upload_f": (I, [P, P, ctypes.c_size_t]),
             "vp_download_f": (I, [P, P, ctypes.c_size_t]),
+            "vp_host_alloc": (I, [ctypes.c_size_t, ctypes.POINTER(P)]),
+            "vp_host_free": (I, [P]),
             "vp_drift_sweep": (I, [P, I, D]),
             "vp_drift_unsplit": (I, [P, D, I, P]),
             "vp_kick_sweep": (I, [P, I, D, P]),
@@ -150,6 +154,8 @@ def _ptr(t) -> ctypes.c_void_p:
         return None
     if isinstance(t, int):
         return ctypes.c_void_p(t)
+    if isinstance(t, HostBuffer):
+        return ctypes.c_void_p(t.ptr)
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -224,6 +230,34 @@ def vp_upload_f(ctx, host, nbytes: int) -> None:
 
 def vp_download_f(ctx, host, nbytes: int) -> None:
     _check(ctx, load().vp_download_f(ctx, _ptr(host), nbytes))
+
+
+class HostBuffer:
+    """Page-locked host memory on transparent huge pages (vp_host_alloc), for
+    vp_upload_f / vp_download_f; `ptr` is its address, `array(dtype)` a numpy
+    view of it.  Freed by close() or when collected."""
+
+    def __init__(self, nbytes: int):
+        p = ctypes.c_void_p()
+        rc = load().vp_host_alloc(nbytes, ctypes.byref(p))
+        if rc != VP_OK:
+            raise VpError(rc, f"vp_host_alloc({nbytes}) failed")
+        self.ptr, self.nbytes = p.value, nbytes
+
+    def array(self, dtype=np.float32) -> np.ndarray:
+        buf = (ctypes.c_char * self.nbytes).from_address(self.ptr)
+        return np.frombuffer(buf, dtype=dtype)
+
+    def close(self) -> None:
+        if self.ptr:
+            load().vp_host_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def vp_drift_sweep(ctx, dim: int, dt: float) -> None:
