@@ -256,7 +256,27 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
     }
     const int tot = nl * L;
     const int dr = blockDim.x / L, dp = blockDim.x - dr * L;
-    {
+    // whole rows of 16-byte pieces (f_off is 128-byte aligned): 16-byte loads and stores
+    const bool vec = (L & 3) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0;
+    if (vec) {
+        const int st4 = 4 * (int)blockDim.x;
+        const int vr = st4 / L, vp = st4 - vr * L;
+        int row = (4 * (int)threadIdx.x) / L, pos = 4 * (int)threadIdx.x - row * L;
+        for (int e = 4 * (int)threadIdx.x; e < tot; e += st4) {
+            const float4 v = __ldcg(reinterpret_cast<const float4 *>(base + e));
+            float *d = in + row * Pp + GP + pos;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
+            row += vr;
+            pos += vp;
+            if (pos >= L) {
+                pos -= L;
+                ++row;
+            }
+        }
+    } else {
         int row = threadIdx.x / L, pos = threadIdx.x - row * L;
         for (int e = threadIdx.x; e < tot; e += 4 * blockDim.x) {
             float v[4];
@@ -299,7 +319,21 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
                                                      P.pp, st);
     }
     __syncthreads();
-    {
+    if (vec) {
+        const int st4 = 4 * (int)blockDim.x;
+        const int vr = st4 / L, vp = st4 - vr * L;
+        int row = (4 * (int)threadIdx.x) / L, pos = 4 * (int)threadIdx.x - row * L;
+        for (int e = 4 * (int)threadIdx.x; e < tot; e += st4) {
+            const float *src = out + row * Q + pos;
+            *reinterpret_cast<float4 *>(base + e) = make_float4(src[0], src[1], src[2], src[3]);
+            row += vr;
+            pos += vp;
+            if (pos >= L) {
+                pos -= L;
+                ++row;
+            }
+        }
+    } else {
         int row = threadIdx.x / L, pos = threadIdx.x - row * L;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             base[e] = out[row * Q + pos];
