@@ -285,7 +285,7 @@ def ensemble_bench(steps: int, warmup: int = 3, profile: bool = False):
            "runs": len(draws), "cells": cells, "steps": steps, "ms_per_step": ms,
            "value": updates_per_step / (ms / 1e3), "unit": "cell-updates/s",
            "launches_per_step": (V.vp_ensemble_launch_count(ens) - l0) / steps,
-           "tiles": V.vp_ensemble_get_tiles(ens),
+           "tiles": V.vp_ensemble_get_tiles(ens) | {"flat_vote": V.vp_ensemble_get_flat_vote(ens)},
            "roofline": {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4), "algorithmic_bytes_per_step": alg,
                         "kernel": "k_ensemble (one persistent launch per step)",

@@ -317,10 +317,20 @@ int vp_ensemble_accel(const vp_ens *ens, const double **accel_dev);
  * dividing 256), CTAs per SM of the persistent grid (0 = occupancy maximum) */
 int vp_ensemble_set_tiles(vp_ens *ens, int W, int R, int ctas_per_sm);
 int vp_ensemble_get_tiles(const vp_ens *ens, int *out3);
-/* time candidate tile shapes (W, R, CTAs per SM) with whole steps at dt from
- * a snapshot of f and the field (allocated for the tuning, restored after
- * every timed step, freed: the ensemble's state is unchanged); keep the
- * fastest; synchronises.  VP_ENOMEM without room for the snapshot. */
+/* Whether the line walkers of the ensemble vote, warp by warp, on flat
+ * stencils (u_{-1} = u_0 = u_1 on every lane) and then skip the interpolant
+ * and the MP bounds (1, the default), or leave the vote out (0).  The results
+ * are the same bits either way (the constrained flux of a flat stencil is u_0
+ * exactly); the vote pays where f has flat (e.g. empty) regions and only
+ * costs where it has none.  set: VP_EINVAL for other values; forgets the
+ * captured step graph. */
+int vp_ensemble_set_flat_vote(vp_ens *ens, int on);
+int vp_ensemble_get_flat_vote(const vp_ens *ens, int *on);
+/* time candidate tile shapes (W, R, CTAs per SM), with and without the
+ * flat-stencil vote, with whole steps at dt from a snapshot of f and the
+ * field (allocated for the tuning, restored after every timed step, freed:
+ * the ensemble's state is unchanged); keep the fastest; synchronises.
+ * VP_ENOMEM without room for the snapshot. */
 int vp_ensemble_autotune(vp_ens *ens, double dt);
 /* nsteps KDK steps of every run (one persistent launch each, graph replay) */
 int vp_ensemble_step(vp_ens *ens, double dt, int nsteps);

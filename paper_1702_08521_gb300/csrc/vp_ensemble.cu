@@ -141,7 +141,7 @@ __global__ void k_ens_drift_table(const RunDesc *__restrict__ runs, LineShift<fl
     }
 }
 
-template <int ORDER, bool PER>
+template <int ORDER, bool PER, bool FLAT>
 __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int tile,
                           const double *acc_pool, const LineShift<float> *dsh, const EnsParams &P, float *sm) {
     // zero-inflow lines get VP_GHOST zero rows on each side (direct walks)
@@ -223,12 +223,13 @@ __device__ void tile_cols(float *pool, const RunDesc &r, const StageDesc &s, int
                 p += step;
             }
         } st{base + cc + (long long)i0 * s.inner, (long long)sh.sigma * s.inner};
-        vp_core::walk<float, ORDER, PER, true, PER ? 1 : VP_GHOST>(data + cc, W, L, sh, r0, r1, (float)P.alpha,
+        vp_core::walk<float, ORDER, PER, true, PER ? 1 : VP_GHOST, false, FLAT>(data + cc, W, L, sh, r0, r1,
+                                                                                (float)P.alpha,
                                                                     P.mp, P.pp, st);
     }
 }
 
-template <int ORDER>
+template <int ORDER, bool FLAT>
 __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int tile,
                           const double *acc_pool, const EnsParams &P, float *sm) {
     constexpr int GP = VP_GHOST;  // velocity lines: zero inflow
@@ -315,7 +316,8 @@ __device__ void tile_rows(float *pool, const RunDesc &r, const StageDesc &s, int
                 p += step;
             }
         } st{out + line * Q + i0, sh.sigma};
-        vp_core::walk<float, ORDER, false, true, GP>(in + line * Pp + GP, 1, L, sh, r0, r1, (float)P.alpha, P.mp,
+        vp_core::walk<float, ORDER, false, true, GP, false, FLAT>(in + line * Pp + GP, 1, L, sh, r0, r1,
+                                                                  (float)P.alpha, P.mp,
                                                      P.pp, st);
     }
     __syncthreads();
@@ -486,7 +488,7 @@ __device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *ac
     }
 }
 
-template <int ORDER>
+template <int ORDER, bool FLAT>
 __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ pool,
                                                        const RunDesc *__restrict__ runs,
                                                        const EnsItem *__restrict__ items, int nitems,
@@ -530,11 +532,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_ensemble(float *__restrict__ po
         if (threadIdx.x == 32) s_item = (int)atomicAdd(head, 1u);
         if (s.kind == ST_COLS) {
             if (s.periodic)
-                tile_cols<ORDER, true>(pool, r, s, e.tile, acc_pool, dsh, P, reinterpret_cast<float *>(ens_smem));
+                tile_cols<ORDER, true, FLAT>(pool, r, s, e.tile, acc_pool, dsh, P,
+                                             reinterpret_cast<float *>(ens_smem));
             else
-                tile_cols<ORDER, false>(pool, r, s, e.tile, acc_pool, dsh, P, reinterpret_cast<float *>(ens_smem));
+                tile_cols<ORDER, false, FLAT>(pool, r, s, e.tile, acc_pool, dsh, P,
+                                              reinterpret_cast<float *>(ens_smem));
         } else if (s.kind == ST_ROWS) {
-            tile_rows<ORDER>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
+            tile_rows<ORDER, FLAT>(pool, r, s, e.tile, acc_pool, P, reinterpret_cast<float *>(ens_smem));
         } else if (s.kind == ST_MOMENT) {
             const long long x0 = (long long)e.tile * P.xpt;
             const long long x1 = x0 + P.xpt < r.NX ? x0 + P.xpt : r.NX;
@@ -602,6 +606,7 @@ struct vp_ens {
     int *d_status;
     EnsParams P;
     int ctas_per_sm;
+    int flat;          // 1: the walkers vote on flat stencils (and skip them), 0: no vote
     size_t smem;
     int tuned;
     cudaGraphExec_t graph;
@@ -747,20 +752,34 @@ static int ensure_drift_table(vp_ens *e, double dt) {
     return VP_OK;
 }
 
+// the persistent kernel of the ensemble's order and flat-vote choice
+static const void *ens_kernel(int order, int flat) {
+    if (order == 7) return flat ? (const void *)k_ensemble<7, true> : (const void *)k_ensemble<7, false>;
+    return flat ? (const void *)k_ensemble<5, true> : (const void *)k_ensemble<5, false>;
+}
+
+static void launch_k(vp_ens *e, const EnsItem *items, int nitems, const EnsParams &P) {
+    const int grid = e->ctas_per_sm * e->sm_count;
+#define VP_ENS_LAUNCH(O, F)                                                                                 \
+    k_ensemble<O, F><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,   \
+                                                             e->d_acc, e->d_rho, P, e->d_status, e->d_tw,   \
+                                                             e->d_green, e->d_fft, e->d_dsh)
+    if (e->P.order == 7) {
+        if (e->flat) VP_ENS_LAUNCH(7, true);
+        else VP_ENS_LAUNCH(7, false);
+    } else {
+        if (e->flat) VP_ENS_LAUNCH(5, true);
+        else VP_ENS_LAUNCH(5, false);
+    }
+#undef VP_ENS_LAUNCH
+}
+
 static int launch_pass(vp_ens *e, const EnsItem *items, int nitems, double dt) {
     EnsParams P = e->P;
     P.dt = dt;
     if (cudaMemsetAsync(e->d_ctr, 0, sizeof(unsigned) * (e->nslots + 1), e->stream) != cudaSuccess)
         return ens_fail(e, VP_ECUDA, "counter reset failed");
-    const int grid = e->ctas_per_sm * e->sm_count;
-    if (e->P.order == 7)
-        k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
-                                                             e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
-                                                             e->d_green, e->d_fft, e->d_dsh);
-    else
-        k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, items, nitems, e->d_ctr,
-                                                             e->d_acc, e->d_rho, P, e->d_status, e->d_tw,
-                                                             e->d_green, e->d_fft, e->d_dsh);
+    launch_k(e, items, nitems, P);
     e->launches++;
     const cudaError_t er = cudaGetLastError();
     if (er != cudaSuccess) return ens_fail(e, VP_ECUDA, cudaGetErrorString(er));
@@ -896,12 +915,12 @@ int vp_ensemble_create(const vp_run_desc *runs, int nruns, int order, void *cuda
         return rc;
     }
     e->smem = smem_need(e->runs);
-    cudaFuncSetAttribute(k_ensemble<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_ensemble<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    for (int o = 5; o <= 7; o += 2)
+        for (int fl = 0; fl < 2; ++fl)
+            cudaFuncSetAttribute(ens_kernel(o, fl), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e->flat = 1;
     int per = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, order == 7 ? (const void *)k_ensemble<7>
-                                                                   : (const void *)k_ensemble<5>,
-                                                  kThreads, e->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_kernel(order, e->flat), kThreads, e->smem);
     e->ctas_per_sm = per < 1 ? 1 : per;
     *out = e;
     return VP_OK;
@@ -976,19 +995,9 @@ int vp_ensemble_field(vp_ens *e) {
         if (cudaMemcpyAsync(e->d_ctr, ctr.data(), sizeof(unsigned) * ctr.size(), cudaMemcpyHostToDevice,
                             e->stream) != cudaSuccess)
             return ens_fail(e, VP_ECUDA, "counter upload failed");
-        const int grid = e->ctas_per_sm * e->sm_count;
         EnsParams P = e->P;
         P.dt = 0.0;
-        if (e->P.order == 7)
-            k_ensemble<7><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
-                                                                 (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft,
-                                                                 e->d_dsh);
-        else
-            k_ensemble<5><<<grid, kThreads, e->smem, e->stream>>>(e->pool, e->d_runs, e->d_items_field,
-                                                                 (int)pass.size(), e->d_ctr, e->d_acc, e->d_rho,
-                                                                 P, e->d_status, e->d_tw, e->d_green, e->d_fft,
-                                                                 e->d_dsh);
+        launch_k(e, e->d_items_field, (int)pass.size(), P);
         e->launches++;
         if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ens_fail(e, VP_ECUDA, "field pass failed");
     }
@@ -1027,9 +1036,7 @@ int vp_ensemble_set_tiles(vp_ens *e, int W, int R, int ctas_per_sm) {
     if (rc) return rc;
     e->smem = smem_need(e->runs);
     int per = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, e->P.order == 7 ? (const void *)k_ensemble<7>
-                                                                        : (const void *)k_ensemble<5>,
-                                                  kThreads, e->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_kernel(e->P.order, e->flat), kThreads, e->smem);
     per = per < 1 ? 1 : per;
     e->ctas_per_sm = ctas_per_sm > 0 && ctas_per_sm < per ? ctas_per_sm : per;
     if (e->graph_valid) {
@@ -1046,6 +1053,22 @@ int vp_ensemble_set_wait_limit(vp_ens *e, long long iterations) {
         cudaGraphExecDestroy(e->graph);
         e->graph_valid = 0;
     }
+    return VP_OK;
+}
+
+int vp_ensemble_set_flat_vote(vp_ens *e, int on) {
+    if (!e || on < 0 || on > 1) return VP_EINVAL;
+    e->flat = on;
+    if (e->graph_valid) {  // the kernel is baked into the graph
+        cudaGraphExecDestroy(e->graph);
+        e->graph_valid = 0;
+    }
+    return VP_OK;
+}
+
+int vp_ensemble_get_flat_vote(const vp_ens *e, int *on) {
+    if (!e || !on) return VP_EINVAL;
+    *on = e->flat;
     return VP_OK;
 }
 
@@ -1087,12 +1110,15 @@ int vp_ensemble_autotune(vp_ens *e, double dt) {
     const int Ws[3] = {32, 64, 128};
     const int Rs[2] = {32, 64};
     float best = 1e30f;
-    int bw = e->P.W, br = e->P.R, bc = 0;
+    int bw = e->P.W, br = e->P.R, bc = 0, bf = e->flat;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
+    // the walkers with and without the flat-stencil vote (the same results)
+    for (int fl = 1; fl >= 0 && rc == VP_OK; --fl)
     for (int wi = 0; wi < 3 && rc == VP_OK; ++wi)
         for (int ri = 0; ri < 2 && rc == VP_OK; ++ri) {
+            e->flat = fl;
             if (vp_ensemble_set_tiles(e, Ws[wi], Rs[ri], 0)) continue;
             const int maxc = e->ctas_per_sm;
             for (int cps = maxc; cps >= 1 && cps >= maxc - 2 && rc == VP_OK; --cps) {
@@ -1119,6 +1145,7 @@ int vp_ensemble_autotune(vp_ens *e, double dt) {
                     bw = Ws[wi];
                     br = Rs[ri];
                     bc = cps;
+                    bf = fl;
                 }
             }
         }
@@ -1127,6 +1154,7 @@ int vp_ensemble_autotune(vp_ens *e, double dt) {
     cudaStreamSynchronize(e->stream);
     cudaFree(snap_f);
     cudaFree(snap_acc);
+    e->flat = bf;
     if (rc) return rc;
     e->tuned = 1;
     return vp_ensemble_set_tiles(e, bw, br, bc);

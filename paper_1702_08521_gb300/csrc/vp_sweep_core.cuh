@@ -314,9 +314,11 @@ __device__ __forceinline__ T flux_walk(const SH &sh, T um3, T um2, T um1, T u0, 
 // The update is the flux form of Eq. 49 in masses, f' = (u - M_out) + M_in.
 // store(i, v) writes the new value of cell i.  NEG: interfaces next to a
 // negative cell take the PP limiter's theta form (pp_theta_mass) instead of
-// the clamp (scalar T only).
+// the clamp (scalar T only).  FLAT = false leaves the flat-stencil vote out
+// (the same results; for data that is nowhere flat the vote only costs).
 
-template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, bool NEG = false, typename Store, typename SH>
+template <typename T, int ORDER, bool PERIODIC, bool FULL, int GP, bool NEG = false, bool FLAT = true,
+          typename Store, typename SH>
 __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, const SH &sh,
                                      int r0, int r1, T alpha, int mp, int pp, Store store) {
     if (r0 >= r1) return;
@@ -389,7 +391,7 @@ __device__ __forceinline__ void walk(const T *__restrict__ sm0, int ss, int L, c
         T phi;                                                                                    \
         if (FULL || mp) {                                                                         \
             const T dp = curv(u0_, u1_, w[(K + 6) & 7]);                                          \
-            if (FlatSkip<T>::on &&                                                                \
+            if (FLAT && FlatSkip<T>::on &&                                                        \
                 __all_sync(__activemask(), w[(K + 3) & 7] == u0_ && u0_ == u1_)) {                \
                 phi = u0_;                                                                        \
                 m4m = T(0);                                                                       \

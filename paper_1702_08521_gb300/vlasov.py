@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "vp_ensemble_accel": (I, [P, P]),
             "vp_ensemble_set_tiles": (I, [P, I, I, I]),
             "vp_ensemble_get_tiles": (I, [P, P]),
+            "vp_ensemble_set_flat_vote": (I, [P, I]),
+            "vp_ensemble_get_flat_vote": (I, [P, P]),
             "vp_ensemble_autotune": (I, [P, D]),
             "vp_ensemble_step": (I, [P, D, I]),
             "vp_ensemble_sync": (I, [P]),
@@ -385,6 +387,16 @@ def vp_ensemble_get_tiles(ens) -> dict:
     out = (ctypes.c_int * 3)()
     _echeck(ens, load().vp_ensemble_get_tiles(ens, ctypes.cast(out, ctypes.c_void_p)))
     return {"W": out[0], "R": out[1], "ctas_per_sm": out[2]}
+
+
+def vp_ensemble_set_flat_vote(ens, on: int) -> None:
+    _echeck(ens, load().vp_ensemble_set_flat_vote(ens, on))
+
+
+def vp_ensemble_get_flat_vote(ens) -> int:
+    out = ctypes.c_int()
+    _echeck(ens, load().vp_ensemble_get_flat_vote(ens, ctypes.byref(out)))
+    return out.value
 
 
 def vp_ensemble_autotune(ens, dt: float) -> None:

@@ -161,3 +161,26 @@ def test_ensemble_follows_a_change_of_dt(graph):
         assert rel_l1(got, ref) <= 1e-6, (i, rel_l1(got, ref))
         sim.close()
     V.vp_ensemble_destroy(ens)
+
+
+def test_flat_vote_does_not_change_the_bits():
+    """The walkers with and without the warp vote on flat stencils give the
+    same f, bit for bit (the flux of a flat stencil is its value exactly);
+    the setter checks its argument and the tuner leaves a valid choice."""
+    import torch
+    specs = _runs()
+    out = []
+    for on in (1, 0):
+        ens, pool = _ensemble(specs, torch.cuda.Stream())
+        V.vp_ensemble_set_flat_vote(ens, on)
+        assert V.vp_ensemble_get_flat_vote(ens) == on
+        V.vp_ensemble_step(ens, 0.05, 6)
+        V.vp_ensemble_sync(ens)
+        out.append(pool[:V.vp_ensemble_num_cells(ens)].clone())
+        if on == 0:
+            with pytest.raises(V.VpError):
+                V.vp_ensemble_set_flat_vote(ens, 2)
+            V.vp_ensemble_autotune(ens, 0.05)
+            assert V.vp_ensemble_get_flat_vote(ens) in (0, 1)
+        V.vp_ensemble_destroy(ens)
+    assert torch.equal(out[0], out[1])
