@@ -195,27 +195,43 @@ int enqueue_step(vp_ctx *c, double dt, int split, double *acc, const float *wts)
     const vp_grid &g = c->g;
     const long long NX = c->NX;
     int rc;
-    auto drift = [&](int d, double h) {
-        return wts ? vp_learned_sweep(c, 0, d, h, nullptr, wts, 1, nullptr) : sweep_all(c, 0, d, h, nullptr);
+    // the drifts x_D ... x_1 of a stage; learned drifts alternate between f
+    // and the library's second array (each reads f^n whole and writes the
+    // new lines apart), with the network operands made once per stage and
+    // one copy back into f only after an odd number of drifts
+    auto drifts = [&](double h) {
+        if (!wts) {
+            for (int d = g.dx - 1; d >= 0; --d)
+                if ((rc = sweep_all(c, 0, d, h, nullptr))) return rc;
+            return VP_OK;
+        }
+        float *src = static_cast<float *>(c->f), *dst = static_cast<float *>(c->d_learn_out);
+        for (int d = g.dx - 1; d >= 0; --d) {
+            if ((rc = vp_learned_drift_io(c, d, h, wts, 1, src, dst, d == g.dx - 1))) return rc;
+            float *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != c->f)
+            VP_CUDA_TRY(c, cudaMemcpyAsync(c->f, src, (size_t)c->ncell * sizeof(float), cudaMemcpyDeviceToDevice,
+                                           c->stream));
+        return VP_OK;
     };
     if (split == VP_SPLIT_KDK) {
         for (int d = 0; d < g.dv; ++d)
             if ((rc = sweep_all(c, 1, d, 0.5 * dt, acc + d * NX))) return rc;
-        for (int d = g.dx - 1; d >= 0; --d)
-            if ((rc = drift(d, dt))) return rc;
+        if ((rc = drifts(dt))) return rc;
         if ((rc = vp_launch_moment(c, c->d_rho_s))) return rc;
         if ((rc = vp_launch_poisson(c, c->d_rho_s, c->d_phi_s, acc))) return rc;
         for (int d = 0; d < g.dv; ++d)
             if ((rc = sweep_all(c, 1, d, 0.5 * dt, acc + d * NX))) return rc;
     } else {
-        for (int d = g.dx - 1; d >= 0; --d)
-            if ((rc = drift(d, 0.5 * dt))) return rc;
+        if ((rc = drifts(0.5 * dt))) return rc;
         if ((rc = vp_launch_moment(c, c->d_rho_s))) return rc;
         if ((rc = vp_launch_poisson(c, c->d_rho_s, c->d_phi_s, acc))) return rc;
         for (int d = 0; d < g.dv; ++d)
             if ((rc = sweep_all(c, 1, d, dt, acc + d * NX))) return rc;
-        for (int d = g.dx - 1; d >= 0; --d)
-            if ((rc = drift(d, 0.5 * dt))) return rc;
+        if ((rc = drifts(0.5 * dt))) return rc;
     }
     return VP_OK;
 }

@@ -901,22 +901,12 @@ int vp_learned_prepare(vp_ctx *c) {
     return VP_OK;
 }
 
-extern "C" {
-
-int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
-                     int use_net, const float *f_snap) {
-    (void)f_snap;  // the walk reads f^n as it is and writes the new lines to a buffer of its own
-    if (!c || !c->f) return VP_EINVAL;
-    if (c->g.precision != VP_F32 || c->g.order != 7)
-        return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
-    if (use_net < 0 || use_net > 2) return vp_fail(c, VP_EINVAL, "use_net must be 0, 1 or 2");
-    if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
-    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
-        return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
-    if (!use_net) return kick ? vp_kick_sweep(c, dim, dt, accel_dev) : vp_drift_sweep(c, dim, dt);
-    int rc = vp_learned_prepare(c);
-    if (rc != VP_OK) return rc;
-    const LineGeo q = line_geo(c->g, c->NX, c->NV, kick, dim);
+// one learned drift along dim from fin (f^n, not written) to fout; with
+// net = true the network operands are made from wts first (a stage of
+// several drifts with one network makes them once)
+int vp_learned_drift_io(vp_ctx *c, int dim, double dt, const float *wts, int use_net, const float *fin,
+                        float *fout, bool net) {
+    const LineGeo q = line_geo(c->g, c->NX, c->NV, 0, dim);
     // tile: every class j of its lines times a block of the other indices,
     // about 128 lines (columns)
     LTile tl{};
@@ -949,14 +939,14 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
     const size_t smem = (size_t)kLC * kABytes + kOpAlloc;
     const long long blocks = q.outer * tl.tpo;
     if (blocks >= (1LL << 31)) return vp_fail(c, VP_ENOTSUP, "learned sweep has too many tiles");
-    rc = vp_launch_shift_table(c, kick, dim, dt, accel_dev);
+    int rc = vp_launch_shift_table(c, 0, dim, dt, nullptr);
     if (rc != VP_OK) return rc;
-    k_net_umma<<<1, 256, 0, c->stream>>>(wts, static_cast<unsigned char *>(c->d_netfrag));
-    c->launches++;
+    if (net) {
+        k_net_umma<<<1, 256, 0, c->stream>>>(wts, static_cast<unsigned char *>(c->d_netfrag));
+        c->launches++;
+    }
     const LineShift<float> *tab = static_cast<const LineShift<float> *>(c->d_shift);
     const uint4 *ops = static_cast<const uint4 *>(c->d_netfrag);
-    const float *fin = static_cast<const float *>(c->f);
-    float *fout = static_cast<float *>(c->d_learn_out);
     if (q.periodic)
         k_learned_walk<true, kLC><<<(unsigned)blocks, threads, smem, c->stream>>>(
             fin, fout, tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
@@ -965,6 +955,27 @@ int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *acce
             fin, fout, tl, tab, ops, q.lo, q.dvel, (float)c->g.alpha, use_net, c->d_status);
     c->launches++;
     VP_CUDA_TRY(c, cudaGetLastError());
+    return VP_OK;
+}
+
+extern "C" {
+
+int vp_learned_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel_dev, const float *wts,
+                     int use_net, const float *f_snap) {
+    (void)f_snap;  // the walk reads f^n as it is and writes the new lines to a buffer of its own
+    if (!c || !c->f) return VP_EINVAL;
+    if (c->g.precision != VP_F32 || c->g.order != 7)
+        return vp_fail(c, VP_ENOTSUP, "the learned sweep runs on FP32 CSL7 grids");
+    if (use_net < 0 || use_net > 2) return vp_fail(c, VP_EINVAL, "use_net must be 0, 1 or 2");
+    if (use_net && kick) return vp_fail(c, VP_ENOTSUP, "the learned correction applies to spatial sweeps");
+    if (dim < 0 || dim >= c->g.dx || (kick && !accel_dev) || (use_net && !wts) || !std::isfinite(dt))
+        return vp_fail(c, VP_EINVAL, "bad learned-sweep arguments");
+    if (!use_net) return kick ? vp_kick_sweep(c, dim, dt, accel_dev) : vp_drift_sweep(c, dim, dt);
+    int rc = vp_learned_prepare(c);
+    if (rc != VP_OK) return rc;
+    float *fout = static_cast<float *>(c->d_learn_out);
+    if ((rc = vp_learned_drift_io(c, dim, dt, wts, use_net, static_cast<const float *>(c->f), fout, true)))
+        return rc;
     VP_CUDA_TRY(c, cudaMemcpyAsync(c->f, fout, (size_t)c->ncell * sizeof(float), cudaMemcpyDeviceToDevice,
                                    c->stream));
     return VP_OK;

@@ -193,6 +193,10 @@ int vp_launch_shift_table(vp_ctx *c, int kick, int dim, double dt, const double 
 bool vp_capturing(const vp_ctx *c);
 // buffers and kernel attributes of the learned sweep (outside any stream capture)
 int vp_learned_prepare(vp_ctx *c);
+// one learned drift along dim from fin to fout (distinct arrays of f's size);
+// net: make the network operands from wts first
+int vp_learned_drift_io(vp_ctx *c, int dim, double dt, const float *wts, int use_net, const float *fin,
+                        float *fout, bool net);
 // RK-MPP5 sweeps: kernel attributes once per process, one sweep (table + fused stages)
 int vp_rk_setup();
 int vp_launch_rk_sweep(vp_ctx *c, int kick, int dim, double dt, const double *accel);
