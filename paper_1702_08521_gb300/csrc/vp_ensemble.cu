@@ -34,9 +34,10 @@
 
 namespace {
 
-// threads of a CTA: 128, up to 8 CTAs per SM at the 64-register budget, so
-// that many independent items are in flight per SM (256-thread CTAs, 4 per
-// SM, left their staging waits exposed: 3.47 against 3.07 ms per step)
+// threads of a CTA: 128, so that many independent items are in flight per
+// SM (256-thread CTAs, 4 per SM, left their staging waits exposed: 3.47
+// against 3.07 ms per step); launch bounds for 6 CTAs per SM, which the
+// staged tiles' shared memory allows anyway, leave 80 registers (no spills)
 constexpr int kThreads = 128;
 constexpr int kMaxStages = 8;
 // shared-memory budget of one staged sweep tile (wider tiles are halved)
@@ -492,7 +493,7 @@ __device__ void poisson_run(const RunDesc &r, const double *rho_pool, double *ac
 }
 
 template <int ORDER, bool FLAT>
-__global__ void __launch_bounds__(kThreads, 8) k_ensemble(float *__restrict__ pool,
+__global__ void __launch_bounds__(kThreads, 6) k_ensemble(float *__restrict__ pool,
                                                        const RunDesc *__restrict__ runs,
                                                        const EnsItem *__restrict__ items, int nitems,
                                                        unsigned *__restrict__ ctr, double *acc_pool,
