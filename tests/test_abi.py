@@ -93,3 +93,20 @@ def test_grid_struct_matches_the_header():
         for part in decl.split(None, 1)[1].split(","):
             names.append(re.sub(r"\[.*\]", "", part).strip())
     assert [f[0] for f in vlasov.vp_grid._fields_] == names
+
+
+def test_host_buffer_and_ensemble_calls_check_their_arguments_without_gpu_work(lib):
+    """Argument checks that return before any CUDA call: a zero-byte or
+    output-less host allocation, freeing a pointer the library did not hand
+    out, and the ensemble's flat-vote calls on a null ensemble."""
+    L = vlasov.load()
+    p = ctypes.c_void_p()
+    assert L.vp_host_alloc(0, ctypes.byref(p)) == vlasov.VP_EINVAL
+    assert p.value is None
+    assert L.vp_host_alloc(64, None) == vlasov.VP_EINVAL
+    assert L.vp_host_free(ctypes.c_void_p(4096)) == vlasov.VP_EINVAL
+    assert L.vp_host_free(None) == vlasov.VP_EINVAL
+    on = ctypes.c_int(7)
+    assert L.vp_ensemble_set_flat_vote(None, 1) == vlasov.VP_EINVAL
+    assert L.vp_ensemble_get_flat_vote(None, ctypes.byref(on)) == vlasov.VP_EINVAL
+    assert on.value == 7
